@@ -458,8 +458,11 @@ void orc_hist(const orc_params *p, const double *x, int nbins, double *bond_h, d
  *    removed bonds are <= 1.3 sigma (so the reverse move is admissible too).
  *  - Proposal: draw one of the N_ch (N-1) bonds uniformly; P(b) is the list of
  *    admissible moves that remove b, ordered by the particle id of the monomer
- *    that would bond to b's lower-index end (then alpha before beta); one entry
- *    is drawn uniformly.  q(x->x') = [1/|P(b1)| + 1/|P(b2)|] / N_bonds, and the
+ *    that would bond to b's lower-index end; one entry
+ *    is drawn uniformly.  Ties (the same monomer offering both kinds) are
+ *    broken by the particle id of the partner bond's other monomer; both keys
+ *    follow the monomers, not the slots, so earlier swaps in a sweep that only
+ *    relabel slots leave the order unchanged.  q(x->x') = [1/|P(b1)| + 1/|P(b2)|] / N_bonds, and the
  *    move is accepted with probability
  *        min(1, exp(-dE/T) q(x'->x)/q(x->x')),
  *    dE = change of FENE log terms and bending energy of the two chains (the
@@ -471,13 +474,13 @@ void orc_hist(const orc_params *p, const double *x, int nbins, double *bond_h, d
  *    during the sweep and added to the positions once, at its end.
  */
 
-typedef struct { int key, kind, d, q; } orc_cand;
+typedef struct { int key, key2, kind, d, q; } orc_cand;
 
 static int cmp_cand(const void *a, const void *b)
 {
     const orc_cand *x = (const orc_cand *)a, *y = (const orc_cand *)b;
     if (x->key != y->key) return (x->key > y->key) - (x->key < y->key);
-    return (x->kind > y->kind) - (x->kind < y->kind);
+    return (x->key2 > y->key2) - (x->key2 < y->key2);
 }
 
 /* Admissible partners of bond (chain c, index b), by testing every slot. */
@@ -495,13 +498,13 @@ static int enum_partners(const orc_params *p, const double *x, const int *pid, i
         if (i == b + 1) {                       /* alpha: t = D_{b+1} */
             int up = d * N + b;                 /*        D_b         */
             if (dist2(x, M, L, up, w) <= lim2 && dist2(x, M, L, up, t) <= lim2) {
-                if (out) { out[cnt].key = pid[t]; out[cnt].kind = 0; out[cnt].d = d; out[cnt].q = b; }
+                if (out) { out[cnt].key = pid[t]; out[cnt].key2 = pid[up]; out[cnt].kind = 0; out[cnt].d = d; out[cnt].q = b; }
                 ++cnt;
             }
         }
         if (i == N - 2 - b) {                   /* beta: t = D_q, q = N-2-b */
             if (dist2(x, M, L, t + 1, w) <= lim2 && dist2(x, M, L, t, t + 1) <= lim2) {
-                if (out) { out[cnt].key = pid[t]; out[cnt].kind = 1; out[cnt].d = d; out[cnt].q = i; }
+                if (out) { out[cnt].key = pid[t]; out[cnt].key2 = pid[t + 1]; out[cnt].kind = 1; out[cnt].d = d; out[cnt].q = i; }
                 ++cnt;
             }
         }
