@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the DBH hot path on GB300: monomer-timesteps/s and accepted
+double-bridging moves/s, with the step kernel's fraction of HBM roofline.
+
+One bench step = 50 MD steps + one double-bridging sweep at the paper's rate
+R_MC = 1e-3 per monomer per tau (Sec. II.B), i.e. M * 50 * dt * 1e-3 attempts.
+Default workload: 1000 chains x N = 1600 (1.6M monomers), kappa = 3.5,
+rho = 0.85, T = 1, Gamma = 1, mixed precision, stage n = 12 (WCA) at dt = 0.01
+after a short dt-ramped walk through the softening stages.  Its working set is
+larger than the 129 MB L2, so every MD step streams from HBM.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (one MD step and 1/50 of a sweep per bench step), on this host.
+Under torchrun every rank advances an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+MD_PER_STEP = 50
+DT = 0.01
+# algorithmic HBM bytes per monomer per launch of the fused step kernel:
+# x r+w 48, u r+w 24 (f32) / 48 (f64), own record 16, displacement r+w 32 (mixed)
+# or gather copy r+w 64 + build position 32 (f64), list length 4, Verlet list
+# 4 * 10.25 (rho (4 pi/3)(r_c + skin)^3 neighbours at rho = 0.85, skin 0.3)
+NB_MEAN = 0.85 * 4.0 / 3.0 * np.pi * (2 ** (1 / 6) + 0.3) ** 3
+BYTES_PER_MONOMER = {"mixed": 48 + 24 + 16 + 32 + 4 + 4 * NB_MEAN,
+                     "fp64": 48 + 48 + 64 + 32 + 4 + 4 * NB_MEAN}
+# DRAM bytes per monomer of the mixed step kernel from an ncu capture, and the
+# hash of kg_md.cu they were taken on (reported as null once the source changes)
+NCU_TRAFFIC = {"bytes_per_monomer": None, "kg_md_sha1": None}
+
+WORKLOADS = {
+    "cfg5": dict(index=5, desc="1000 chains x N=1600 (1.6M monomers), kappa=3.5, rho=0.85"),
+    "cfg4": dict(index=4, desc="500 chains x N=800 (400k monomers), kappa=3.0, rho=0.85"),
+    "cfg2": dict(index=2, desc="200 chains x N=400 (80k monomers), kappa=2.5, rho=0.85"),
+    "cfg1": dict(index=1, desc="20 chains x N=50 (1000 monomers), kappa=1.5, rho=0.85"),
+}
+
+
+def prelude_stages(kg):
+    """dt ramp through the exponent set Xi (Eq. 11) to the n = 12 stage."""
+    s = [(2.0, 200, 0.001), (2.0, 200, 0.002), (3.0, 200, 0.002), (4.0, 200, 0.003), (5.0, 200, 0.003),
+         (5.75, 200, 0.004), (6.5, 200, 0.004), (7.0, 200, 0.005), (8.0, 200, 0.005), (9.0, 200, 0.005),
+         (10.0, 200, 0.005), (11.0, 200, 0.005), (12.0, 300, 0.005)]
+    stages = [kg.stage(n, k, dt) for n, k, dt in s]
+    return stages + [kg.stage(12.0, 10 ** 15, DT)], sum(k for _, k, _ in s)
+
+
+def src_sha1():
+    with open(os.path.join(ROOT, "paper_2109_11001_gb300", "csrc", "kg_md.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.path = os.path.join("/tmp", f"kg_clocks_{os.getpid()}.csv")
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_melt(wl, rank):
+    import kg_inputs as KI
+    d = KI.config(WORKLOADS[wl]["index"])
+    return KI.random_walk_melt(d["n_chains"], d["chain_len"], d["rho"], d["kappa"], d["seed"] + 1000 * rank)
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(m, md_steps=1, db_attempts=16):
+    """Time the oracle on the full melt: md_steps MD steps and db_attempts DB
+    attempts; returns (seconds per MD step, seconds per DB attempt, sample)."""
+    import oracle as O
+    O.build()
+    p = O.params(m.n_chains, m.chain_len, m.box, m.kappa, n_exp=2.0, dt=0.001, seed=3)
+    x, u = m.x.copy(), m.v.copy()
+    t0 = time.perf_counter()
+    O.run(p, x, u, 0, md_steps)
+    t_md = (time.perf_counter() - t0) / md_steps
+    pid = np.arange(m.M, dtype=np.int32)
+    t0 = time.perf_counter()
+    O.db_sweep(p, x, u, pid, 0, db_attempts)
+    t_db = (time.perf_counter() - t0) / max(db_attempts, 1)
+    return t_md, t_db
+
+
+def step_units(m):
+    """(monomer-steps, DB attempts) of one bench step at the paper's rate."""
+    return m.M * MD_PER_STEP, m.M * MD_PER_STEP * DT * 1e-3
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    m = make_melt(args.workload, 0)
+    units, att = step_units(m)
+    att_sample = max(1, int(round(att / MD_PER_STEP)))
+    for _ in range(args.warmup):
+        oracle_sample(m, 1, att_sample)
+    t = []
+    for _ in range(args.steps):
+        t_md, t_db = oracle_sample(m, 1, att_sample)
+        t.append(t_md + t_db * att_sample)
+    total = sum(t)
+    value = m.M * args.steps / total
+    line = {"metric": "monomer-timesteps/s", "value": value, "unit": "monomer-steps/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]['desc']}",
+                       "sample": f"per step: 1 MD step of all {m.M} monomers + {att_sample} DB attempts"},
+            "cpu_baseline": {"value": value, "unit": "monomer-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} x (1 MD step + {att_sample} DB attempts) on the full melt"},
+            "e2e": {"value": value, "unit": "monomer-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2109_11001_gb300 as kg
+    from paper_2109_11001_gb300 import build as B
+
+    if rank == 0 or world == 1:
+        B.build()
+    barrier(world)
+    torch.cuda.set_device(local)
+    m = make_melt(args.workload, rank)
+    prec = kg.KG_MIXED if args.precision == "mixed" else kg.KG_FP64
+    params = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=prec, seed=11 + rank)
+    stream = torch.cuda.current_stream()
+    ctx = kg.kg_create(params, local, stream.cuda_stream, kg.torch_allocator())
+    stages, n_pre = prelude_stages(kg)
+    kg.kg_set_potential_schedule(ctx, stages)
+    kg.kg_load_config(ctx, 0, m.x, m.v)
+    kg.kg_step(ctx, n_pre)
+
+    def bench_step():
+        kg.kg_step(ctx, MD_PER_STEP)
+        return kg.kg_db_sweep(ctx, -1.0)
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    kg.kg_profile(ctx, 1)
+    _, _, l0 = kg.kg_profile_read(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    acc = att = 0
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = bench_step()
+            acc += st.accepted
+            att += st.attempted
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    step_ms, n_launch, l1 = kg.kg_profile_read(ctx)
+    kg.kg_profile(ctx, 0)
+    barrier(world)
+    t_max = allmax(world, ms / 1e3)
+    units = allsum(world, float(m.M * MD_PER_STEP * args.steps))
+    acc_all = allsum(world, float(acc))
+
+    # end to end through the public API: state in from pinned host memory,
+    # 50 MD steps + one sweep, positions back to pinned host memory
+    hx = torch.from_numpy(m.x).pin_memory()
+    hv = torch.from_numpy(m.v).pin_memory()
+    hout = torch.empty_like(hx).pin_memory()
+    kg.kg_get_config(ctx, 0, hx, hv)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        kg.kg_load_config(ctx, 0, hx, hv)
+        bench_step()
+        kg.kg_get_config(ctx, 0, hout)
+    torch.cuda.synchronize()
+    t_e2e = allmax(world, time.perf_counter() - t0)
+
+    # secondary: the same step in plain binary64 on this GPU (single rank)
+    sec = None
+    if world == 1 and args.secondary:
+        sec = secondary(kg, torch, args, local)
+    kg.kg_destroy(ctx)
+    if rank != 0:
+        return
+    avg_ms = step_ms / max(n_launch, 1)
+    bpm = BYTES_PER_MONOMER[args.precision]
+    achieved = bpm * m.M / (avg_ms * 1e-3) / 1e9
+    peak, src = peaks()
+    traffic = None
+    if NCU_TRAFFIC["bytes_per_monomer"] and NCU_TRAFFIC["kg_md_sha1"] == src_sha1():
+        traffic = NCU_TRAFFIC["bytes_per_monomer"] * m.M
+    t_md, t_db = oracle_sample(m, 2, 8)
+    att_step = m.M * MD_PER_STEP * DT * 1e-3
+    cpu_val = m.M * MD_PER_STEP / (MD_PER_STEP * t_md + att_step * t_db)
+    line = {
+        "metric": "monomer-timesteps/s", "value": units / t_max, "unit": "monomer-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 forces, f64 state" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]['desc']}",
+                   "step": f"{MD_PER_STEP} MD steps (n=12, dt={DT}) + 1 DB sweep at R_MC=1e-3/monomer/tau",
+                   "precision": args.precision, "replicas": world,
+                   "l2": "inputs larger than L2 (working set > 129 MB), no flush"},
+        "accepted_db_moves_per_s": acc_all / t_max,
+        "db_attempts_per_step": att / args.steps,
+        "roofline": {"bound": "hbm", "kernel": "k_step_" + args.precision, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": src, "bytes_per_monomer": bpm, "avg_launch_ms": avg_ms},
+        "cpu_baseline": {"value": cpu_val, "unit": "monomer-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"2 MD steps + 8 DB attempts of the full {m.M}-monomer melt, "
+                                   f"scaled to one bench step"},
+        "e2e": {"value": units / t_e2e, "unit": "monomer-steps/s",
+                "h2d_bytes_per_step": int(hx.numel() * 8 + hv.numel() * 8),
+                "d2h_bytes_per_step": int(hout.numel() * 8)},
+        "gpu_launches": int(l1 - l0),
+        "clocks": clk.summary(),
+    }
+    if sec:
+        line["secondary"] = sec
+    print(json.dumps(line))
+
+
+def secondary(kg, torch, args, local):
+    """80k-monomer melt: mixed vs plain binary64 step rate on this GPU."""
+    import kg_inputs as KI
+    m = KI.make(2)
+    out = {"workload": "cfg2: " + WORKLOADS["cfg2"]["desc"]}
+    for name, prec in (("mixed", kg.KG_MIXED), ("fp64", kg.KG_FP64)):
+        p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=prec, seed=13)
+        s = torch.cuda.current_stream()
+        ctx = kg.kg_create(p, local, s.cuda_stream, kg.torch_allocator())
+        stages, n_pre = prelude_stages(kg)
+        kg.kg_set_potential_schedule(ctx, stages)
+        kg.kg_load_config(ctx, 0, m.x, m.v)
+        kg.kg_step(ctx, n_pre)
+        for _ in range(2):
+            kg.kg_step(ctx, MD_PER_STEP)
+            kg.kg_db_sweep(ctx, -1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 10
+        e0.record(s)
+        for _ in range(n):
+            kg.kg_step(ctx, MD_PER_STEP)
+            kg.kg_db_sweep(ctx, -1.0)
+        e1.record(s)
+        torch.cuda.synchronize()
+        out[name + "_monomer_steps_per_s"] = m.M * MD_PER_STEP * n / (e0.elapsed_time(e1) / 1e3)
+        kg.kg_destroy(ctx)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg5", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-secondary", dest="secondary", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

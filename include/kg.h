@@ -1,0 +1,212 @@
+/*
+ * kg.h -- C ABI of the GB300 (sm_103a) library for the core-softened
+ * double-bridging hybrid (DBH) equilibration of semiflexible Kremer-Grest
+ * melts, after Dietz & Hoy, arXiv:2109.11001.
+ *
+ * The calls follow the paper's statement of the problem:
+ *   - a melt of N_ch chains of N monomers in a cubic periodic cell at density
+ *     rho, temperature T and bending stiffness kappa (Sec. II.B);
+ *   - a sequence of stages (n, duration) of the core-softened pair potential
+ *     U_MLJ^n (Eq. 6) with the FENE constant k_n tied to n (Eq. 9), stepped
+ *     through the exponent set Xi (Eq. 11) by the schemes of Eqs. 19-20;
+ *   - molecular dynamics at time step dt with double-bridging (DB) Monte Carlo
+ *     swaps attempted at R_MC = 1e-3 N_ch N / tau under criteria (i) and (ii)
+ *     (Sec. II.B, Fig. 1);
+ *   - outputs <R^2(n)> (input to the l_K fit of Eq. 14), energies, swap counts.
+ *
+ * Conventions (all calls):
+ *   - Every call returns a kg_status; KG_OK is 0.  kg_strerror() names it.
+ *   - Storage is chain-major: slot s = c*N + i of a melt holds monomer i of
+ *     chain c; bonds join slots s and s+1 of one chain.  Topology is the slot
+ *     order, so no bond arrays cross the ABI.
+ *   - Position arrays are (3, M) float64 structure-of-arrays, unwrapped:
+ *     x[0..M) = x, x[M..2M) = y, x[2M..3M) = z.  Velocities likewise.
+ *   - Pointers passed to kg_load_config / kg_get_config / kg_observables /
+ *     kg_get_nlist / kg_forces may be host or device memory (CUDA unified
+ *     addressing decides); inputs are copied, the caller keeps ownership.
+ *   - The context owns its device memory; all GPU work is enqueued on the
+ *     context's stream.  kg_step and kg_db_sweep are asynchronous except for
+ *     one status read at their end; device-side errors (overstretched bond,
+ *     non-finite value, capacity) are latched and reported by that read.
+ *   - After an error the context refuses work (KG_ERR_STATE) until the next
+ *     kg_load_config.
+ *   - One context per host thread at a time.
+ */
+#ifndef KG_H
+#define KG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kg_ctx kg_ctx;
+
+typedef enum {
+    KG_OK = 0,
+    KG_ERR_INVALID_ARG = 1,      /* a size, pointer or parameter out of range          */
+    KG_ERR_CUDA = 2,             /* a CUDA runtime call failed                          */
+    KG_ERR_OOM = 3,              /* device allocation failed                            */
+    KG_ERR_BOND_OVERSTRETCH = 4, /* a bond reached r >= R0, where FENE is undefined     */
+    KG_ERR_NONFINITE = 5,        /* a force, velocity or position became non-finite     */
+    KG_ERR_CAPACITY = 6,         /* neighbour or candidate storage overflowed           */
+    KG_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up                  */
+    KG_ERR_STATE = 8             /* context holds a latched error or no configuration   */
+} kg_status;
+
+/* arithmetic of the MD force path */
+enum {
+    KG_FP64 = 0,   /* every force term in binary64                                     */
+    KG_MIXED = 1   /* pair/bond/angle forces in binary32 from binary64 positions;
+                      positions, DB energy changes and energy sums stay binary64      */
+};
+
+/* kg_params.flags */
+enum {
+    KG_FLAG_PAPER_METROPOLIS = 1  /* accept DB swaps with exp(-dE/T) alone (Fig. 1),
+                                      without the proposal ratio                      */
+};
+
+/* One melt (Sec. II.B): N_ch chains of N monomers in a cube of side L. */
+typedef struct {
+    int n_chains;    /* N_ch >= 1                                                      */
+    int chain_len;   /* N >= 3                                                          */
+    double box;      /* L = (N_ch N / rho)^(1/3); must exceed 7 sigma                   */
+    double kappa;    /* bending stiffness of U_ang = kappa (1 - cos theta), Eq. 4       */
+} kg_melt;
+
+/* Run parameters.  Several melts of uneven size may share one context; they
+ * are independent systems advanced by the same launches. */
+typedef struct {
+    int n_melts;              /* 1 ... 64                                               */
+    const kg_melt *melts;     /* n_melts entries, copied                               */
+    double T;                 /* temperature (1, Sec. II.B)                             */
+    double gamma;             /* Langevin friction (paper silent; 1)                   */
+    double R0;                /* FENE extent, 1.5 (Eq. 3)                               */
+    double l0;                /* bond length kept by k_n, 0.960897 (Eq. 7)              */
+    double db_bond_max;       /* longest new bond of a DB swap, 1.3 (Sec. II.B (ii))    */
+    double r_mc;              /* DB attempts per monomer per tau, 1e-3 (Sec. II.B)      */
+    double skin;              /* neighbour-list skin (0.3 when <= 0)                    */
+    unsigned long long seed;  /* key of every counter-based random draw                */
+    int precision;            /* KG_FP64 or KG_MIXED                                    */
+    int flags;                /* KG_FLAG_*                                              */
+} kg_params;
+
+/* One stage of the potential schedule (Eqs. 6, 9, 10, 19-20). */
+typedef struct {
+    double n_exp;       /* exponent n of U_MLJ^n; n != 6; Xi = {2,...,12} (Eq. 11)      */
+    double k_fene;      /* FENE constant; < 0 selects k_n of Eq. 9                      */
+    long long n_steps;  /* MD steps spent in the stage                                 */
+    double dt;          /* time step of the stage (a dt ramp is a run of stages)      */
+} kg_stage;
+
+/* Integer-time observables of one melt (FP64 sums). */
+typedef struct {
+    double e_pair, e_bond, e_angle, e_kin, virial, temperature, pressure;
+    long long step;
+} kg_obs;
+
+/* Double-bridging sweep statistics (summed over melts). */
+typedef struct {
+    long long attempted;    /* attempts drawn                                          */
+    long long empty;        /* attempts whose drawn bond had no admissible partner     */
+    long long accepted;     /* swaps applied                                           */
+    long long reevaluated;  /* attempts re-evaluated after an earlier swap in the sweep */
+    long long sweep;        /* index of the sweep just run                             */
+} kg_db_stats;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  NULL
+ * selects cudaMalloc / cudaFree.  alloc returns NULL on failure. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} kg_allocator;
+
+/* Create a context on `device`, enqueueing on `stream` (a cudaStream_t; NULL
+ * selects a new non-blocking stream owned by the context).  Validates p,
+ * allocates every device buffer.  The default stage is n = 12 (WCA), k_12,
+ * dt = 0.01 until kg_set_potential_schedule is called. */
+kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream,
+                    const kg_allocator *allocator);
+
+/* Load melt `melt`'s state: x (3, M) unwrapped positions, v (3, M) velocities
+ * (NULL: zero), pid (M) particle ids carried through DB swaps (NULL: 0..M-1).
+ * The velocity is the state velocity u = v_{n-1/2} of the leapfrog form of
+ * velocity Verlet.  Clears a latched error; forces a neighbour-list rebuild. */
+kg_status kg_load_config(kg_ctx *c, int melt, const double *x, const double *v, const int *pid);
+
+/* Copy melt `melt`'s state out (any pointer may be NULL). */
+kg_status kg_get_config(kg_ctx *c, int melt, double *x, double *v, int *pid);
+
+/* Replace the potential schedule by n_stages stages (copied).  Kernels read
+ * the stage parameters from device memory, so a stage change costs one small
+ * copy.  After the last stage its parameters stay in force. */
+kg_status kg_set_potential_schedule(kg_ctx *c, const kg_stage *stages, int n_stages);
+
+/* Advance every melt by n_steps MD steps: Verlet-list maintenance, U_MLJ^n
+ * pairs, U_bond^n bonds (Eq. 10), bending (Eq. 4), Langevin velocity Verlet
+ * with Philox4x32-10 noise keyed by (seed, step, slot, melt). */
+kg_status kg_step(kg_ctx *c, long long n_steps);
+
+/* One DB sweep per melt.  attempts_per_monomer >= 0: floor(a M + carry)
+ * attempts per melt; < 0: the paper's rate R_MC times the MD time elapsed since
+ * the previous sweep (Sec. II.B).  Attempts are processed with the semantics
+ * of a strictly sequential loop (an attempt sees every swap accepted before
+ * it).  stats may be NULL. */
+kg_status kg_db_sweep(kg_ctx *c, double attempts_per_monomer, kg_db_stats *stats);
+
+/* As kg_db_sweep with an explicit attempt count per melt (n_melts entries). */
+kg_status kg_db_sweep_k(kg_ctx *c, const long long *attempts, kg_db_stats *stats);
+
+/* Observables of melt `melt` at the current integer time step (synchronises):
+ * energies and virial from the conservative forces, kinetic energy from
+ * v_n = u + dt/2 F_n, <R^2(n)> for n = 0..N-1 into r2n (N doubles; NULL to
+ * skip), and bond-length (on [0, R0)) / cos(theta) (on [-1, 1]) histograms of
+ * n_bins bins (NULL to skip). */
+kg_status kg_observables(kg_ctx *c, int melt, kg_obs *out, double *r2n,
+                         double *bond_hist, double *cos_hist, int n_bins);
+
+/* Wait for the context's stream; returns the latched device status. */
+kg_status kg_sync(kg_ctx *c);
+
+/* Counters: MD step index and DB sweep index (they key the random draws). */
+kg_status kg_get_counters(kg_ctx *c, long long *step, long long *sweep);
+kg_status kg_set_counters(kg_ctx *c, long long step, long long sweep);
+
+/* Verlet list of melt `melt` built now from the current positions with cutoff
+ * r_c + skin: CSR offs (M+1) and nbr (melt-local slots, ascending per row,
+ * at most cap entries); *total receives the pair count.  1-2 bonded pairs are
+ * excluded; the distance test is r^2 < (r_c + skin)^2 in binary64. */
+kg_status kg_get_nlist(kg_ctx *c, int melt, int *offs, int *nbr, long long cap, long long *total);
+
+/* Conservative forces (3, M) of melt `melt` at the current positions, in the
+ * context's precision, and e4 = [pair, bond, angle, virial] energies (either
+ * pointer may be NULL). */
+kg_status kg_forces(kg_ctx *c, int melt, double *F, double *e4);
+
+/* Timing of the fused MD step kernel with CUDA events on the context's
+ * stream.  kg_profile(c, 1) starts recording an event pair around every
+ * step-kernel launch (and resets the totals); kg_profile(c, 0) stops.
+ * kg_profile_read synchronises and returns the summed step-kernel time (ms),
+ * its launch count, and the number of kernels the library has launched since
+ * kg_create (every kernel, whether or not profiling is on). */
+kg_status kg_profile(kg_ctx *c, int enable);
+kg_status kg_profile_read(kg_ctx *c, double *step_kernel_ms, long long *step_kernel_launches,
+                          long long *kernel_launches);
+
+/* Host helpers (no context): k_n of Eq. 9, and the twelve stages of the
+ * paper's schedule for (kappa, N) at time step dt (Eqs. 12, 16-20; scheme 1
+ * for kappa <= 2.5), each stage's length scaled by `scale` (1: the paper's). */
+double kg_kn(double n, double R0, double l0);
+kg_status kg_schedule_paper(double kappa, int chain_len, double dt, double scale,
+                            kg_stage *out12);
+
+void kg_destroy(kg_ctx *c);
+const char *kg_strerror(kg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KG_H */

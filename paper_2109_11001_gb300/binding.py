@@ -1,0 +1,276 @@
+"""ctypes binding of ``libkg.so`` (include/kg.h), argument marshalling only.
+
+Every function keeps the C name.  Arrays may be numpy arrays (host) or torch
+tensors (host or CUDA); their data pointers are passed as they are.  PyTorch
+supplies device memory (through the ``kg_allocator`` hook, see
+:func:`torch_allocator`) and the CUDA stream; all arithmetic runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library is missing or
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkg.so")
+
+KG_OK, KG_ERR_INVALID_ARG, KG_ERR_CUDA, KG_ERR_OOM = 0, 1, 2, 3
+KG_ERR_BOND_OVERSTRETCH, KG_ERR_NONFINITE, KG_ERR_CAPACITY, KG_ERR_TIMEOUT, KG_ERR_STATE = 4, 5, 6, 7, 8
+KG_FP64, KG_MIXED = 0, 1
+KG_FLAG_PAPER_METROPOLIS = 1
+
+EXPORTS = ["kg_create", "kg_load_config", "kg_get_config", "kg_set_potential_schedule", "kg_step",
+           "kg_db_sweep", "kg_db_sweep_k", "kg_observables", "kg_sync", "kg_get_counters",
+           "kg_set_counters", "kg_get_nlist", "kg_forces", "kg_profile", "kg_profile_read", "kg_kn", "kg_schedule_paper", "kg_destroy",
+           "kg_strerror"]
+
+
+class kg_melt(C.Structure):
+    _fields_ = [("n_chains", C.c_int), ("chain_len", C.c_int), ("box", C.c_double), ("kappa", C.c_double)]
+
+
+class kg_params(C.Structure):
+    _fields_ = [("n_melts", C.c_int), ("melts", C.POINTER(kg_melt)), ("T", C.c_double),
+                ("gamma", C.c_double), ("R0", C.c_double), ("l0", C.c_double),
+                ("db_bond_max", C.c_double), ("r_mc", C.c_double), ("skin", C.c_double),
+                ("seed", C.c_ulonglong), ("precision", C.c_int), ("flags", C.c_int)]
+
+
+class kg_stage(C.Structure):
+    _fields_ = [("n_exp", C.c_double), ("k_fene", C.c_double), ("n_steps", C.c_longlong), ("dt", C.c_double)]
+
+
+class kg_obs(C.Structure):
+    _fields_ = [("e_pair", C.c_double), ("e_bond", C.c_double), ("e_angle", C.c_double),
+                ("e_kin", C.c_double), ("virial", C.c_double), ("temperature", C.c_double),
+                ("pressure", C.c_double), ("step", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class kg_db_stats(C.Structure):
+    _fields_ = [("attempted", C.c_longlong), ("empty", C.c_longlong), ("accepted", C.c_longlong),
+                ("reevaluated", C.c_longlong), ("sweep", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class kg_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    i, d, p, ll = C.c_int, C.c_double, C.c_void_p, C.c_longlong
+    sig = {
+        "kg_create": (i, [p, C.POINTER(kg_params), i, p, p]),
+        "kg_load_config": (i, [p, i, p, p, p]),
+        "kg_get_config": (i, [p, i, p, p, p]),
+        "kg_set_potential_schedule": (i, [p, C.POINTER(kg_stage), i]),
+        "kg_step": (i, [p, ll]),
+        "kg_db_sweep": (i, [p, d, C.POINTER(kg_db_stats)]),
+        "kg_db_sweep_k": (i, [p, p, C.POINTER(kg_db_stats)]),
+        "kg_observables": (i, [p, i, C.POINTER(kg_obs), p, p, p, i]),
+        "kg_sync": (i, [p]),
+        "kg_get_counters": (i, [p, C.POINTER(ll), C.POINTER(ll)]),
+        "kg_set_counters": (i, [p, ll, ll]),
+        "kg_get_nlist": (i, [p, i, p, p, ll, C.POINTER(ll)]),
+        "kg_forces": (i, [p, i, p, p]),
+        "kg_profile": (i, [p, i]),
+        "kg_profile_read": (i, [p, C.POINTER(d), C.POINTER(ll), C.POINTER(ll)]),
+        "kg_kn": (d, [d, d, d]),
+        "kg_schedule_paper": (i, [d, i, d, d, C.POINTER(kg_stage)]),
+        "kg_destroy": (None, [p]),
+        "kg_strerror": (C.c_char_p, [i]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+class KGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = load().kg_strerror(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def _check(st, where):
+    if st != KG_OK:
+        raise KGError(st, where)
+    return st
+
+
+def ptr(a):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def torch_allocator():
+    """A kg_allocator whose buffers are torch CUDA tensors (kept alive here)."""
+    import torch
+    keep = {}
+
+    def _alloc(nbytes, user):
+        t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        keep[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(p, user):
+        keep.pop(int(p or 0), None)
+
+    a = kg_allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    a._keep = (keep, _alloc, _free)
+    return a
+
+
+# ---- the C entry points, same names ----
+
+# allocators (and their ctypes callback trampolines) must outlive their context
+_ALLOCATORS = {}
+
+
+def kg_create(params: kg_params, device: int = 0, stream: int | None = None, allocator=None):
+    ctx = C.c_void_p()
+    _check(load().kg_create(C.byref(ctx), C.byref(params), int(device), stream,
+                            C.byref(allocator) if allocator is not None else None), "kg_create")
+    if allocator is not None:
+        _ALLOCATORS[ctx.value] = allocator
+    return ctx
+
+
+def kg_load_config(ctx, melt, x, v=None, pid=None):
+    return _check(load().kg_load_config(ctx, int(melt), ptr(x), ptr(v), ptr(pid)), "kg_load_config")
+
+
+def kg_get_config(ctx, melt, x=None, v=None, pid=None):
+    return _check(load().kg_get_config(ctx, int(melt), ptr(x), ptr(v), ptr(pid)), "kg_get_config")
+
+
+def kg_set_potential_schedule(ctx, stages):
+    arr = (kg_stage * len(stages))(*stages)
+    return _check(load().kg_set_potential_schedule(ctx, arr, len(stages)), "kg_set_potential_schedule")
+
+
+def kg_step(ctx, n_steps):
+    return _check(load().kg_step(ctx, int(n_steps)), "kg_step")
+
+
+def kg_db_sweep(ctx, attempts_per_monomer=-1.0):
+    st = kg_db_stats()
+    _check(load().kg_db_sweep(ctx, float(attempts_per_monomer), C.byref(st)), "kg_db_sweep")
+    return st
+
+
+def kg_db_sweep_k(ctx, attempts):
+    a = np.ascontiguousarray(np.asarray(attempts, dtype=np.int64))
+    st = kg_db_stats()
+    _check(load().kg_db_sweep_k(ctx, a.ctypes.data, C.byref(st)), "kg_db_sweep_k")
+    return st
+
+
+def kg_observables(ctx, melt, r2n=None, bond_hist=None, cos_hist=None, n_bins=0):
+    ob = kg_obs()
+    _check(load().kg_observables(ctx, int(melt), C.byref(ob), ptr(r2n), ptr(bond_hist), ptr(cos_hist),
+                                 int(n_bins)), "kg_observables")
+    return ob
+
+
+def kg_sync(ctx):
+    return load().kg_sync(ctx)
+
+
+def kg_get_counters(ctx):
+    s, w = C.c_longlong(), C.c_longlong()
+    _check(load().kg_get_counters(ctx, C.byref(s), C.byref(w)), "kg_get_counters")
+    return s.value, w.value
+
+
+def kg_set_counters(ctx, step, sweep):
+    return _check(load().kg_set_counters(ctx, int(step), int(sweep)), "kg_set_counters")
+
+
+def kg_get_nlist(ctx, melt, M, cap=None):
+    cap = cap or M * 96
+    offs = np.zeros(M + 1, dtype=np.int32)
+    nbr = np.zeros(cap, dtype=np.int32)
+    tot = C.c_longlong()
+    _check(load().kg_get_nlist(ctx, int(melt), ptr(offs), ptr(nbr), cap, C.byref(tot)), "kg_get_nlist")
+    return offs, nbr[:tot.value].copy()
+
+
+def kg_forces(ctx, melt, F=None, e4=None):
+    return _check(load().kg_forces(ctx, int(melt), ptr(F), ptr(e4)), "kg_forces")
+
+
+def kg_profile(ctx, enable):
+    return _check(load().kg_profile(ctx, int(bool(enable))), "kg_profile")
+
+
+def kg_profile_read(ctx):
+    ms, n, launches = C.c_double(), C.c_longlong(), C.c_longlong()
+    _check(load().kg_profile_read(ctx, C.byref(ms), C.byref(n), C.byref(launches)), "kg_profile_read")
+    return ms.value, n.value, launches.value
+
+
+def kg_kn(n, R0=1.5, l0=0.960897):
+    return load().kg_kn(float(n), float(R0), float(l0))
+
+
+def kg_schedule_paper(kappa, chain_len, dt, scale=1.0):
+    out = (kg_stage * 12)()
+    _check(load().kg_schedule_paper(float(kappa), int(chain_len), float(dt), float(scale), out),
+           "kg_schedule_paper")
+    return list(out)
+
+
+def kg_destroy(ctx):
+    load().kg_destroy(ctx)
+    _ALLOCATORS.pop(ctx.value, None)
+
+
+def kg_strerror(status):
+    return load().kg_strerror(int(status)).decode()
+
+
+# ---- convenience: parameter construction ----
+
+def make_params(melts, precision=KG_MIXED, seed=1, T=1.0, gamma=1.0, R0=1.5, l0=0.960897, db_bond_max=1.3,
+                r_mc=1e-3, skin=0.3, flags=0):
+    """melts: iterable of (n_chains, chain_len, box, kappa)."""
+    arr = (kg_melt * len(melts))(*[kg_melt(int(a), int(b), float(c), float(d)) for a, b, c, d in melts])
+    p = kg_params(len(melts), arr, T, gamma, R0, l0, db_bond_max, r_mc, skin, int(seed), int(precision),
+                  int(flags))
+    p._keep = arr
+    return p
+
+
+def stage(n_exp, n_steps, dt, k_fene=-1.0):
+    return kg_stage(float(n_exp), float(k_fene), int(n_steps), float(dt))

@@ -1,0 +1,664 @@
+// kg_api.cu -- C ABI of the GB300 DBH library: context lifecycle, potential
+// schedule (Eqs. 9, 11, 12, 16-20), and dispatch of the MD / DB / observable
+// kernels.  See include/kg.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kg_host.h"
+
+using kg::MeltDev;
+using kg::SimDev;
+using kg::StageDev;
+
+namespace {
+
+constexpr double RC = 1.122462048309373;   // 2^(1/6): cutoff and LJ minimum (Eq. 2)
+
+// ---- schedule arithmetic (Sec. II.B) ----
+const double XI[12] = {2, 3, 4, 5, 5.75, 6.5, 7, 8, 9, 10, 11, 12};   // Eq. 11
+
+double lk_over_l0(double k)   // Eq. 12
+{
+    const double flory = k < 1e-4 ? 1.0 + 2.0 * k / 3.0
+                                   : (2 * k + std::exp(-2 * k) - 1) / (1 - std::exp(-2 * k) * (2 * k + 1));
+    return flory + 0.77 * (std::tanh(-0.03 * k * k - 0.41 * k + 0.16) + 1.0);
+}
+
+double kn_of(double n, double R0, double l0)   // Eq. 9
+{
+    return 6.0 * n * (R0 * R0 - l0 * l0) * (std::pow(2.0, n / 6.0) * std::pow(l0, -n) - 2.0 * std::pow(l0, -6.0))
+           / ((n - 6.0) * R0 * R0 * l0 * l0);
+}
+
+kg_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return KG_OK;
+    if (e == cudaErrorMemoryAllocation) return KG_ERR_OOM;
+    return KG_ERR_CUDA;
+}
+
+#define KG_TRY(call)                                       \
+    do {                                                   \
+        kg_status _s = cuda_status(call);                  \
+        if (_s != KG_OK) return _s;                        \
+    } while (0)
+
+void *dev_alloc(kg_ctx *c, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (c->have_alloc) p = c->alloc.alloc(bytes, c->alloc.user);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) cudaMemsetAsync(p, 0, bytes, c->stream);
+    return p;
+}
+
+void dev_free(kg_ctx *c, void *p)
+{
+    if (!p) return;
+    if (c->have_alloc) c->alloc.free(p, c->alloc.user);
+    else cudaFree(p);
+}
+
+// Stage parameters: U_MLJ^n = c1 r^-n - c2 r^-6 + 1 with c1 = 6 2^(n/6)/(n-6),
+// c2 = 2n/(n-6) (Eq. 5 with m = 6, shifted at r_c); FENE k_n from Eq. 9 when
+// the stage gives k < 0.
+StageDev make_stage(const kg_params &p, const kg_stage &s)
+{
+    StageDev d{};
+    const double n = s.n_exp;
+    d.n = n;
+    d.c1 = 6.0 * std::pow(2.0, n / 6.0) / (n - 6.0);
+    d.c2 = 2.0 * n / (n - 6.0);
+    d.kfene = s.k_fene < 0 ? kn_of(n, p.R0, p.l0) : s.k_fene;
+    d.R0sq = p.R0 * p.R0;
+    d.dt = s.dt;
+    d.gamma = p.gamma;
+    d.T = p.T;
+    d.amp = p.gamma > 0 ? std::sqrt(2.0 * p.gamma * p.T / s.dt) : 0.0;
+    d.nf = (float)n; d.c1f = (float)d.c1; d.c2f = (float)d.c2; d.kfenef = (float)d.kfene;
+    d.R0sqf = (float)d.R0sq; d.dtf = (float)d.dt; d.gammaf = (float)d.gamma; d.ampf = (float)d.amp;
+    const double rn = std::nearbyint(n);
+    if (std::fabs(n - rn) < 1e-12 && rn >= 1 && rn <= 64) { d.nkind = 1; d.nint = (int)rn; }
+    else if (n == 5.75) d.nkind = 2;
+    else if (n == 6.5) d.nkind = 3;
+    else d.nkind = 0;
+    return d;
+}
+
+kg_status upload_stage(kg_ctx *c, const kg_stage &s)
+{
+    c->stage = make_stage(c->p, s);
+    KG_TRY(cudaMemcpyAsync(c->d_stage, &c->stage, sizeof(StageDev), cudaMemcpyHostToDevice, c->stream));
+    return KG_OK;
+}
+
+__global__ void k_d2f(const double *__restrict__ a, float *__restrict__ b, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_f2d(const float *__restrict__ a, double *__restrict__ b, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+__global__ void k_iota(int *__restrict__ a, int n, int base)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = base + i;
+}
+
+// Read the device status word; translate latched error bits.
+kg_status read_flags(kg_ctx *c, unsigned *host4)
+{
+    KG_TRY(cudaMemcpyAsync(host4, c->flags, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, c->stream));
+    KG_TRY(cudaStreamSynchronize(c->stream));
+    const unsigned e = host4[0];
+    kg_status s = KG_OK;
+    if (e & kg::ERR_OVERSTRETCH) s = KG_ERR_BOND_OVERSTRETCH;
+    else if (e & kg::ERR_NONFINITE) s = KG_ERR_NONFINITE;
+    else if (e & (kg::ERR_NL_CAPACITY | kg::ERR_DB_CAPACITY | kg::ERR_DB_INTERNAL)) s = KG_ERR_CAPACITY;
+    else if (e & kg::ERR_TIMEOUT) s = KG_ERR_TIMEOUT;
+    if (s != KG_OK) c->latched = s;
+    return s;
+}
+
+unsigned *pinned_flags()
+{
+    static thread_local unsigned *p = nullptr;
+    if (!p && cudaMallocHost(&p, 64) != cudaSuccess) p = nullptr;
+    return p;
+}
+
+kg_status set_rebuild(kg_ctx *c)
+{
+    static const unsigned one = 1u;
+    KG_TRY(cudaMemcpyAsync(c->flags + 1, &one, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
+    return KG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *kg_strerror(kg_status s)
+{
+    switch (s) {
+        case KG_OK: return "ok";
+        case KG_ERR_INVALID_ARG: return "invalid argument";
+        case KG_ERR_CUDA: return "CUDA runtime error";
+        case KG_ERR_OOM: return "device allocation failed";
+        case KG_ERR_BOND_OVERSTRETCH: return "bond overstretched (r >= R0)";
+        case KG_ERR_NONFINITE: return "non-finite force, velocity or position";
+        case KG_ERR_CAPACITY: return "neighbour or candidate capacity exceeded";
+        case KG_ERR_TIMEOUT: return "bounded device wait timed out";
+        case KG_ERR_STATE: return "context has a latched error or no configuration";
+    }
+    return "unknown status";
+}
+
+double kg_kn(double n, double R0, double l0) { return kn_of(n, R0, l0); }
+
+kg_status kg_schedule_paper(double kappa, int chain_len, double dt, double scale, kg_stage *out)
+{
+    if (!out || chain_len < 3 || !(dt > 0) || !(scale > 0) || kappa < 0) return KG_ERR_INVALID_ARG;
+    const double N = chain_len;
+    const double a = 1.6, b = 0.77, f0 = 46.3354;                          // Eq. 15 fit; Sec. II.B f_0
+    const double ne = 77.0 * std::exp(-kappa / 1.1) + 9.4;                  // initial N_e estimate
+    const double tau_e = ne * ne * lk_over_l0(kappa);                       // Eq. 17 (prefactor dropped)
+    const double tau_fix = f0 * N / a * std::exp(b * kappa);               // Eq. 16
+    double w[12], s11 = 0, s12 = 0;
+    for (int i = 0; i < 12; ++i) {
+        w[i] = 1.0 / std::sqrt(XI[i]);
+        s12 += w[i];
+        if (i < 11) s11 += w[i];
+    }
+    for (int i = 0; i < 12; ++i) {
+        double tau;
+        if (kappa <= 2.5)                                                   // Eq. 19
+            tau = i < 11 ? w[i] / s11 * (200.0 * N - 2.0 * tau_e) : 2.0 * tau_e;
+        else                                                                // Eq. 20
+            tau = w[i] / s12 * tau_fix;
+        out[i].n_exp = XI[i];
+        out[i].k_fene = -1.0;
+        out[i].n_steps = (long long)std::nearbyint(scale * tau / dt);
+        out[i].dt = dt;
+    }
+    return KG_OK;
+}
+
+kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, const kg_allocator *allocator)
+{
+    if (!out || !p || p->n_melts < 1 || p->n_melts > kg::MAX_MELTS || !p->melts) return KG_ERR_INVALID_ARG;
+    if (p->precision != KG_FP64 && p->precision != KG_MIXED) return KG_ERR_INVALID_ARG;
+    if (!(p->T > 0) || p->gamma < 0 || !(p->R0 > RC) || !(p->l0 > 0) || !(p->db_bond_max > 0) ||
+        p->db_bond_max >= p->R0)
+        return KG_ERR_INVALID_ARG;
+    *out = nullptr;
+    {   // every melt: chains of >= 3 monomers in a box that holds the cell grids
+        const double skin = p->skin > 0 ? p->skin : 0.3;
+        for (int m = 0; m < p->n_melts; ++m) {
+            const kg_melt &ml = p->melts[m];
+            if (ml.n_chains < 1 || ml.chain_len < 3 || !(ml.box > 7.0) || !(ml.kappa >= 0)) return KG_ERR_INVALID_ARG;
+            if (ml.box / (RC + skin) > (1 << kg::CODE_BITS) || ml.box / p->db_bond_max < 3.0) return KG_ERR_INVALID_ARG;
+        }
+    }
+    kg_ctx *c = new (std::nothrow) kg_ctx();
+    if (!c) return KG_ERR_OOM;
+    c->device = device;
+    c->p = *p;
+    c->melts.assign(p->melts, p->melts + p->n_melts);
+    c->p.melts = c->melts.data();
+    if (!(c->p.skin > 0)) c->p.skin = 0.3;
+    c->precision = p->precision;
+    if (allocator && allocator->alloc && allocator->free) { c->alloc = *allocator; c->have_alloc = true; }
+    auto fail = [&](kg_status s) { kg_destroy(c); return s; };
+    if (cudaSetDevice(device) != cudaSuccess) return fail(KG_ERR_CUDA);
+    if (stream) c->stream = (cudaStream_t)stream;
+    else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(KG_ERR_CUDA);
+        c->own_stream = true;
+    }
+
+    // geometry of every melt
+    SimDev &S = c->sim;
+    S.n_melts = p->n_melts;
+    const double rl = RC + c->p.skin;
+    long long M = 0, ncell = 0, ndbcell = 0;
+    for (int m = 0; m < p->n_melts; ++m) {
+        const kg_melt &ml = c->melts[m];
+        if (ml.n_chains < 1 || ml.chain_len < 3 || !(ml.box > 7.0) || ml.kappa < 0) return fail(KG_ERR_INVALID_ARG);
+        MeltDev &md = S.melt[m];
+        md.off = (int)M;
+        md.N = ml.chain_len;
+        md.n_ch = ml.n_chains;
+        md.M = ml.n_chains * ml.chain_len;
+        md.L = ml.box; md.invL = 1.0 / ml.box; md.Lf = (float)ml.box;
+        md.kappa = ml.kappa; md.kappaf = (float)ml.kappa;
+        md.nc = (int)std::floor(ml.box / (rl * (1.0 + 1e-9)));
+        md.ndb = (int)std::floor(ml.box / (p->db_bond_max * (1.0 + 1e-9)));
+        if (md.nc < 3 || md.ndb < 3) return fail(KG_ERR_INVALID_ARG);
+        md.h = ml.box / md.nc; md.invh = 1.0 / md.h;
+        md.ncc = std::max(md.nc, 16);
+        if (md.ncc > (1 << kg::CODE_BITS)) return fail(KG_ERR_INVALID_ARG);
+        md.hc = ml.box / md.ncc; md.invhc = 1.0 / md.hc; md.hcf = (float)md.hc;
+        md.hdb = ml.box / md.ndb; md.invhdb = 1.0 / md.hdb;
+        md.cell_off = (int)ncell;
+        md.dbcell_off = (int)ndbcell;
+        ncell += (long long)md.nc * md.nc * md.nc;
+        ndbcell += (long long)md.ndb * md.ndb * md.ndb;
+        M += md.M;
+    }
+    if (M >= (1LL << 30) || ncell >= (1LL << 30) || ndbcell >= (1LL << 30)) return fail(KG_ERR_INVALID_ARG);
+    c->M = (int)M;
+    c->Mp = (int)((M + 31) / 32 * 32);
+    c->ncell_md = (int)ncell;
+    c->ncell_db = (int)ndbcell;
+    c->maxnb = 80;
+    S.M = c->M; S.Mp = c->Mp; S.maxnb = c->maxnb;
+    S.rc2 = RC * RC; S.rc2f = (float)S.rc2;
+    S.rl = rl; S.rl2 = rl * rl;
+    S.rl2f_lo = (float)(S.rl2 * (1.0 - 1e-5));
+    S.rl2f_hi = (float)(S.rl2 * (1.0 + 1e-5));
+    S.half_skin2 = 0.25 * c->p.skin * c->p.skin;
+    S.half_skin2f = (float)S.half_skin2;
+    S.db_lim2 = p->db_bond_max * p->db_bond_max;
+    S.seed = p->seed;
+    S.paper_metropolis = (p->flags & KG_FLAG_PAPER_METROPOLIS) ? 1 : 0;
+    c->carry.assign(p->n_melts, 0.0);
+
+    // device buffers
+    const size_t Mp = c->Mp;
+    const size_t ureal = c->precision == KG_MIXED ? sizeof(float) : sizeof(double);
+    bool ok = true;
+    auto A = [&](size_t bytes) { void *q = dev_alloc(c, bytes); ok = ok && q; return q; };
+    c->d_sim = (SimDev *)A(sizeof(SimDev));
+    c->d_stage = (StageDev *)A(sizeof(StageDev));
+    c->x = (double *)A(3 * Mp * sizeof(double));
+    c->u = A(3 * Mp * ureal);
+    c->pid = (int *)A(Mp * sizeof(int));
+    c->recb = (float4 *)A(Mp * sizeof(float4));
+    if (c->precision == KG_MIXED) {
+        c->dlt[0] = (float4 *)A(Mp * sizeof(float4));
+        c->dlt[1] = (float4 *)A(Mp * sizeof(float4));
+    } else {
+        c->pos64[0] = (double4_32a *)A(Mp * sizeof(double4_32a));
+        c->pos64[1] = (double4_32a *)A(Mp * sizeof(double4_32a));
+        c->xb = (double4_32a *)A(Mp * sizeof(double4_32a));
+    }
+    c->cellid = (int *)A(Mp * sizeof(int));
+    c->rank = (int *)A(Mp * sizeof(int));
+    c->ccount = (int *)A((size_t)c->ncell_md * sizeof(int));
+    c->cstart = (int *)A(((size_t)c->ncell_md + 1) * sizeof(int));
+    c->clist = (int *)A(Mp * sizeof(int));
+    const size_t nbs = (size_t)std::max(c->ncell_md, c->ncell_db) / 1024 + 2;
+    c->bsum = (int *)A(nbs * sizeof(int));
+    c->nl = (int *)A((size_t)c->maxnb * Mp * sizeof(int));
+    c->nn = (int *)A(Mp * sizeof(int));
+    c->dbcell = (int *)A(Mp * sizeof(int));
+    c->dbrank = (int *)A(Mp * sizeof(int));
+    c->dbcount = (int *)A((size_t)c->ncell_db * sizeof(int));
+    c->dbstart = (int *)A(((size_t)c->ncell_db + 1) * sizeof(int));
+    c->dblist = (int *)A(Mp * sizeof(int));
+    c->koff = (int *)A((kg::MAX_MELTS + 1) * sizeof(int));
+    c->occ = (int *)A(Mp * sizeof(int));
+    c->curmap = (int *)A(Mp * sizeof(int));
+    c->img = (int *)A(3 * Mp * sizeof(int));
+    c->dirty = (int *)A(Mp * sizeof(int));
+    c->db_stats = (long long *)A(4 * kg::MAX_MELTS * sizeof(long long));
+    c->scratch = (double *)A(7 * Mp * sizeof(double));
+    c->flags = (unsigned *)A(16 * sizeof(unsigned));
+    c->fout = (double *)A(3 * Mp * sizeof(double));
+    c->partials_cap = (int)(Mp / 128 + 2) * 5;
+    c->partials = (double *)A((size_t)c->partials_cap * sizeof(double));
+    long long r2cap = 0;
+    for (int m = 0; m < p->n_melts; ++m) r2cap = std::max(r2cap, (long long)S.melt[m].M);
+    c->r2tmp_cap = r2cap;
+    c->r2tmp = (double *)A((size_t)r2cap * sizeof(double));
+    if (!ok) return fail(KG_ERR_OOM);
+    if (cudaMemcpyAsync(c->d_sim, &c->sim, sizeof(SimDev), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return fail(KG_ERR_CUDA);
+    const int nb = (int)((Mp + 255) / 256);
+    k_iota<<<nb, 256, 0, c->stream>>>(c->occ, (int)Mp, 0);
+    k_iota<<<nb, 256, 0, c->stream>>>(c->curmap, (int)Mp, 0);
+    kg_stage def{12.0, -1.0, -1, 0.01};
+    if (upload_stage(c, def) != KG_OK) return fail(KG_ERR_CUDA);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(KG_ERR_CUDA);
+    if (!pinned_flags()) return fail(KG_ERR_OOM);
+    c->latched = KG_ERR_STATE;
+    *out = c;
+    return KG_OK;
+}
+
+void kg_destroy(kg_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    void *bufs[] = {c->d_sim, c->d_stage, c->x, c->u, c->pid, c->recb, c->dlt[0], c->dlt[1], c->pos64[0],
+                    c->pos64[1], c->xb, c->cellid, c->rank, c->ccount, c->cstart, c->clist, c->bsum, c->nl,
+                    c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->att, c->koff, c->occ,
+                    c->curmap, c->img, c->dirty, c->db_stats, c->scratch, c->flags, c->fout, c->partials,
+                    c->r2tmp, c->hist};
+    for (void *b : bufs) dev_free(c, b);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+static kg_status check_melt(kg_ctx *c, int melt)
+{
+    if (!c || melt < 0 || melt >= c->sim.n_melts) return KG_ERR_INVALID_ARG;
+    return cudaSetDevice(c->device) == cudaSuccess ? KG_OK : KG_ERR_CUDA;
+}
+
+kg_status kg_load_config(kg_ctx *c, int melt, const double *x, const double *v, const int *pid)
+{
+    kg_status s = check_melt(c, melt);
+    if (s != KG_OK) return s;
+    if (!x) return KG_ERR_INVALID_ARG;
+    const MeltDev &md = c->sim.melt[melt];
+    const size_t Mm = md.M, Mp = c->Mp;
+    for (int d = 0; d < 3; ++d)
+        KG_TRY(cudaMemcpyAsync(c->x + d * Mp + md.off, x + d * Mm, Mm * sizeof(double), cudaMemcpyDefault, c->stream));
+    for (int d = 0; d < 3; ++d) {
+        if (c->precision == KG_MIXED) {
+            float *u = (float *)c->u + d * Mp + md.off;
+            if (v) {
+                KG_TRY(cudaMemcpyAsync(c->scratch, v + d * Mm, Mm * sizeof(double), cudaMemcpyDefault, c->stream));
+                k_d2f<<<(int)((Mm + 255) / 256), 256, 0, c->stream>>>(c->scratch, u, (int)Mm);
+            } else {
+                KG_TRY(cudaMemsetAsync(u, 0, Mm * sizeof(float), c->stream));
+            }
+        } else {
+            double *u = (double *)c->u + d * Mp + md.off;
+            if (v) KG_TRY(cudaMemcpyAsync(u, v + d * Mm, Mm * sizeof(double), cudaMemcpyDefault, c->stream));
+            else KG_TRY(cudaMemsetAsync(u, 0, Mm * sizeof(double), c->stream));
+        }
+    }
+    if (pid) KG_TRY(cudaMemcpyAsync(c->pid + md.off, pid, Mm * sizeof(int), cudaMemcpyDefault, c->stream));
+    else k_iota<<<(int)((Mm + 255) / 256), 256, 0, c->stream>>>(c->pid + md.off, (int)Mm, 0);
+    KG_TRY(cudaMemsetAsync(c->flags, 0, 16 * sizeof(unsigned), c->stream));
+    if ((s = set_rebuild(c)) != KG_OK) return s;
+    KG_TRY(cudaStreamSynchronize(c->stream));
+    c->latched = KG_OK;
+    return KG_OK;
+}
+
+kg_status kg_get_config(kg_ctx *c, int melt, double *x, double *v, int *pid)
+{
+    kg_status s = check_melt(c, melt);
+    if (s != KG_OK) return s;
+    const MeltDev &md = c->sim.melt[melt];
+    const size_t Mm = md.M, Mp = c->Mp;
+    for (int d = 0; d < 3; ++d) {
+        if (x) KG_TRY(cudaMemcpyAsync(x + d * Mm, c->x + d * Mp + md.off, Mm * sizeof(double), cudaMemcpyDefault, c->stream));
+        if (v) {
+            if (c->precision == KG_MIXED) {
+                k_f2d<<<(int)((Mm + 255) / 256), 256, 0, c->stream>>>((const float *)c->u + d * Mp + md.off,
+                                                                      c->scratch + d * Mm, (int)Mm);
+                KG_TRY(cudaMemcpyAsync(v + d * Mm, c->scratch + d * Mm, Mm * sizeof(double), cudaMemcpyDefault, c->stream));
+            } else {
+                KG_TRY(cudaMemcpyAsync(v + d * Mm, (const double *)c->u + d * Mp + md.off, Mm * sizeof(double),
+                                       cudaMemcpyDefault, c->stream));
+            }
+        }
+    }
+    if (pid) KG_TRY(cudaMemcpyAsync(pid, c->pid + md.off, Mm * sizeof(int), cudaMemcpyDefault, c->stream));
+    KG_TRY(cudaStreamSynchronize(c->stream));
+    return KG_OK;
+}
+
+kg_status kg_set_potential_schedule(kg_ctx *c, const kg_stage *stages, int n_stages)
+{
+    if (!c || !stages || n_stages < 1) return KG_ERR_INVALID_ARG;
+    for (int i = 0; i < n_stages; ++i)
+        if (!(stages[i].dt > 0) || stages[i].n_exp == 6.0 || !(stages[i].n_exp > 0) || stages[i].n_steps < 0)
+            return KG_ERR_INVALID_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return KG_ERR_CUDA;
+    c->schedule.assign(stages, stages + n_stages);
+    c->stage_idx = 0;
+    c->stage_left = c->schedule[0].n_steps;
+    return upload_stage(c, c->schedule[0]);
+}
+
+kg_status kg_step(kg_ctx *c, long long n_steps)
+{
+    if (!c || n_steps < 0) return KG_ERR_INVALID_ARG;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    if (cudaSetDevice(c->device) != cudaSuccess) return KG_ERR_CUDA;
+    while (n_steps > 0) {
+        // advance past exhausted stages
+        while (c->stage_left == 0 && c->stage_idx + 1 < c->schedule.size()) {
+            ++c->stage_idx;
+            c->stage_left = c->schedule[c->stage_idx].n_steps;
+            kg_status s = upload_stage(c, c->schedule[c->stage_idx]);
+            if (s != KG_OK) return s;
+        }
+        long long chunk = n_steps;
+        if (c->stage_left > 0) chunk = std::min(chunk, c->stage_left);
+        for (long long i = 0; i < chunk; ++i) {
+            kg::md_step(c, c->step);
+            ++c->step;
+        }
+        c->t_since_sweep += chunk * c->stage.dt;
+        if (c->stage_left > 0) c->stage_left -= chunk;
+        n_steps -= chunk;
+    }
+    KG_TRY(cudaGetLastError());
+    unsigned *h = pinned_flags();
+    return read_flags(c, h);
+}
+
+kg_status kg_db_sweep_k(kg_ctx *c, const long long *attempts, kg_db_stats *stats)
+{
+    if (!c || !attempts) return KG_ERR_INVALID_ARG;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    if (cudaSetDevice(c->device) != cudaSuccess) return KG_ERR_CUDA;
+    const int nm = c->sim.n_melts;
+    std::vector<long long> K(attempts, attempts + nm);
+    long long tot = 0;
+    for (long long k : K) {
+        if (k < 0 || k >= (1LL << 31)) return KG_ERR_INVALID_ARG;
+        tot += k;
+    }
+    if (tot >= (1LL << 31)) return KG_ERR_INVALID_ARG;
+    if (tot > c->att_cap) {
+        dev_free(c, c->att);
+        c->att_cap = std::max(tot, 2 * c->att_cap);
+        c->att = dev_alloc(c, (size_t)c->att_cap * sizeof(kg::Attempt));
+        if (!c->att) { c->att_cap = 0; return KG_ERR_OOM; }
+    }
+    static thread_local long long *hstats = nullptr;
+    if (!hstats && cudaMallocHost(&hstats, sizeof(long long) * 4 * kg::MAX_MELTS) != cudaSuccess) return KG_ERR_OOM;
+    // the grid and the record buffers must describe the current positions
+    kg::db_sweep(c, K, hstats);
+    KG_TRY(cudaGetLastError());
+    kg_status s = read_flags(c, pinned_flags());
+    kg_db_stats out{0, 0, 0, 0, c->sweep};
+    for (int m = 0; m < nm; ++m) {
+        out.attempted += hstats[4 * m];
+        out.empty += hstats[4 * m + 1];
+        out.accepted += hstats[4 * m + 2];
+        out.reevaluated += hstats[4 * m + 3];
+    }
+    ++c->sweep;
+    c->t_since_sweep = 0.0;
+    if (stats) *stats = out;
+    return s;
+}
+
+kg_status kg_db_sweep(kg_ctx *c, double a, kg_db_stats *stats)
+{
+    if (!c) return KG_ERR_INVALID_ARG;
+    const int nm = c->sim.n_melts;
+    std::vector<long long> K(nm);
+    for (int m = 0; m < nm; ++m) {
+        const double want = (a >= 0 ? a : c->p.r_mc * c->t_since_sweep) * c->sim.melt[m].M + c->carry[m];
+        K[m] = (long long)std::floor(want);
+        c->carry[m] = want - (double)K[m];
+    }
+    return kg_db_sweep_k(c, K.data(), stats);
+}
+
+kg_status kg_sync(kg_ctx *c)
+{
+    if (!c) return KG_ERR_INVALID_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return KG_ERR_CUDA;
+    kg_status s = read_flags(c, pinned_flags());
+    if (s == KG_OK && c->latched != KG_OK) return KG_ERR_STATE;
+    return s;
+}
+
+kg_status kg_get_counters(kg_ctx *c, long long *step, long long *sweep)
+{
+    if (!c) return KG_ERR_INVALID_ARG;
+    if (step) *step = c->step;
+    if (sweep) *sweep = c->sweep;
+    return KG_OK;
+}
+
+kg_status kg_set_counters(kg_ctx *c, long long step, long long sweep)
+{
+    if (!c || step < 0 || sweep < 0) return KG_ERR_INVALID_ARG;
+    c->step = step;
+    c->sweep = sweep;
+    return KG_OK;
+}
+
+kg_status kg_forces(kg_ctx *c, int melt, double *F, double *e4)
+{
+    kg_status s = check_melt(c, melt);
+    if (s != KG_OK) return s;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    kg::rebuild_md(c);
+    const int nb = kg::forces_blocks(c, melt);
+    kg::forces_eval(c, melt, c->step, c->fout, c->partials, nb);
+    const MeltDev &md = c->sim.melt[melt];
+    const size_t Mm = md.M, Mp = c->Mp;
+    if (F)
+        for (int d = 0; d < 3; ++d)
+            KG_TRY(cudaMemcpyAsync(F + d * Mm, c->fout + d * Mp + md.off, Mm * sizeof(double), cudaMemcpyDefault, c->stream));
+    std::vector<double> part((size_t)nb * 5);
+    KG_TRY(cudaMemcpyAsync(part.data(), c->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if ((s = read_flags(c, pinned_flags())) != KG_OK) return s;
+    if (e4) {
+        for (int k = 0; k < 4; ++k) e4[k] = 0;
+        for (int b = 0; b < nb; ++b)
+            for (int k = 0; k < 4; ++k) e4[k] += part[(size_t)b * 5 + k];
+    }
+    return KG_OK;
+}
+
+kg_status kg_observables(kg_ctx *c, int melt, kg_obs *out, double *r2n, double *bond_hist, double *cos_hist,
+                         int n_bins)
+{
+    kg_status s = check_melt(c, melt);
+    if (s != KG_OK) return s;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    if ((bond_hist || cos_hist) && n_bins < 1) return KG_ERR_INVALID_ARG;
+    const MeltDev &md = c->sim.melt[melt];
+    if (out) {
+        kg::rebuild_md(c);
+        const int nb = kg::forces_blocks(c, melt);
+        kg::forces_eval(c, melt, c->step, nullptr, c->partials, nb);
+        std::vector<double> part((size_t)nb * 5);
+        KG_TRY(cudaMemcpyAsync(part.data(), c->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if ((s = read_flags(c, pinned_flags())) != KG_OK) return s;
+        double e[5] = {0, 0, 0, 0, 0};
+        for (int b = 0; b < nb; ++b)
+            for (int k = 0; k < 5; ++k) e[k] += part[(size_t)b * 5 + k];
+        const double V = md.L * md.L * md.L;
+        out->e_pair = e[0]; out->e_bond = e[1]; out->e_angle = e[2]; out->virial = e[3]; out->e_kin = e[4];
+        out->temperature = 2.0 * e[4] / (3.0 * md.M);
+        out->pressure = (2.0 * e[4] + e[3]) / (3.0 * V);
+        out->step = c->step;
+    }
+    if (r2n) {
+        kg::r2n_eval(c, melt, c->scratch);
+        KG_TRY(cudaMemcpyAsync(r2n, c->scratch, sizeof(double) * md.N, cudaMemcpyDefault, c->stream));
+    }
+    if (bond_hist || cos_hist) {
+        if (c->hist_cap < 2 * n_bins) {
+            dev_free(c, c->hist);
+            c->hist = (int *)dev_alloc(c, sizeof(int) * 2 * n_bins);
+            if (!c->hist) { c->hist_cap = 0; return KG_ERR_OOM; }
+            c->hist_cap = 2 * n_bins;
+        }
+        kg::hist_eval(c, melt, n_bins, c->hist);
+        std::vector<int> h(2 * (size_t)n_bins);
+        KG_TRY(cudaMemcpyAsync(h.data(), c->hist, sizeof(int) * 2 * n_bins, cudaMemcpyDeviceToHost, c->stream));
+        KG_TRY(cudaStreamSynchronize(c->stream));
+        for (int b = 0; b < n_bins; ++b) {
+            if (bond_hist) bond_hist[b] = h[b];
+            if (cos_hist) cos_hist[b] = h[n_bins + b];
+        }
+    }
+    KG_TRY(cudaStreamSynchronize(c->stream));
+    return KG_OK;
+}
+
+kg_status kg_profile(kg_ctx *c, int enable)
+{
+    if (!c) return KG_ERR_INVALID_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return KG_ERR_CUDA;
+    if (enable) {
+        kg::prof_collect(c);
+        c->prof_ms = 0.0;
+        c->prof_n = 0;
+    }
+    c->prof_on = enable != 0;
+    return KG_OK;
+}
+
+kg_status kg_profile_read(kg_ctx *c, double *ms, long long *n, long long *launches)
+{
+    if (!c) return KG_ERR_INVALID_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return KG_ERR_CUDA;
+    kg::prof_collect(c);
+    if (ms) *ms = c->prof_ms;
+    if (n) *n = c->prof_n;
+    if (launches) *launches = c->launches;
+    return KG_OK;
+}
+
+kg_status kg_get_nlist(kg_ctx *c, int melt, int *offs, int *nbr, long long cap, long long *total)
+{
+    kg_status s = check_melt(c, melt);
+    if (s != KG_OK) return s;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    if (!offs || !nbr || cap < 0) return KG_ERR_INVALID_ARG;
+    if ((s = set_rebuild(c)) != KG_OK) return s;
+    kg::rebuild_md(c);
+    const MeltDev &md = c->sim.melt[melt];
+    const size_t Mm = md.M, Mp = c->Mp;
+    std::vector<int> nn(Mm), nl((size_t)c->maxnb * Mm);
+    KG_TRY(cudaMemcpyAsync(nn.data(), c->nn + md.off, Mm * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    for (int k = 0; k < c->maxnb; ++k)
+        KG_TRY(cudaMemcpyAsync(nl.data() + (size_t)k * Mm, c->nl + (size_t)k * Mp + md.off, Mm * sizeof(int),
+                               cudaMemcpyDeviceToHost, c->stream));
+    if ((s = read_flags(c, pinned_flags())) != KG_OK) return s;
+    long long tot = 0;
+    std::vector<int> row;
+    for (size_t i = 0; i < Mm; ++i) {
+        offs[i] = (int)tot;
+        row.clear();
+        for (int k = 0; k < nn[i]; ++k) row.push_back(nl[(size_t)k * Mm + i] - md.off);
+        std::sort(row.begin(), row.end());
+        if (tot + (long long)row.size() > cap) return KG_ERR_CAPACITY;
+        std::copy(row.begin(), row.end(), nbr + tot);
+        tot += (long long)row.size();
+    }
+    offs[Mm] = (int)tot;
+    if (total) *total = tot;
+    return KG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// kg_internal.cuh -- device-side data layout and helpers of the GB300 DBH library.
+//
+// Layout in HBM (all melts of a context are concatenated slot ranges):
+//   x        double[3][Mp]   canonical unwrapped positions (SoA)
+//   u        float[3][Mp] (mixed) / double[3][Mp] (FP64): state velocity v_{n-1/2}
+//   pid      int[Mp]         particle ids carried through double-bridging swaps
+//   recb     float4[Mp]      build-time position record: offset from its cell
+//                            corner on the "code grid" + packed cell code
+//   dlt[2]   float4[Mp]      (mixed) displacement since the last build, ping-pong
+//   pos64[2] double4_32a[Mp] (FP64) gather copy of the positions, ping-pong
+//   xb       double4_32a[Mp] (FP64) positions at the last build
+//   nl       int[maxnb][Mp]  Verlet list, column-major (coalesced per k)
+//   nn       int[Mp]         list lengths
+// Mp is the total slot count rounded up to a multiple of 32.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kg {
+
+constexpr int MAX_MELTS = 64;
+constexpr int CODE_BITS = 10;           // cells per axis on the code grid <= 1024
+constexpr int CODE_MASK = (1 << CODE_BITS) - 1;
+
+// device error / status word bits
+enum : unsigned {
+    ERR_OVERSTRETCH = 1u,
+    ERR_NONFINITE = 2u,
+    ERR_NL_CAPACITY = 4u,
+    ERR_DB_CAPACITY = 8u,
+    ERR_TIMEOUT = 16u,
+    ERR_DB_INTERNAL = 32u,
+};
+
+struct MeltDev {
+    int off, M, N, n_ch;          // slots [off, off+M): chain c, position i -> off + c*N + i
+    double L, invL, kappa;
+    float Lf, kappaf;
+    // Verlet-list cell grid (cells >= r_c + skin)
+    int nc, cell_off;
+    double h, invh;
+    // code grid of the position records (>= 16 cells per axis)
+    int ncc;
+    double hc, invhc;
+    float hcf;
+    // double-bridging grid (cells >= db_bond_max)
+    int ndb, dbcell_off;
+    double hdb, invhdb;
+};
+
+// Parameters of the current potential stage (Eqs. 6, 9, 10) and thermostat.
+struct StageDev {
+    double n, c1, c2;        // U_MLJ^n(r) = c1 r^-n - c2 r^-6 + 1  (r < r_c)
+    double kfene, R0sq;      // FENE: -k R0^2/2 ln(1 - r^2/R0^2)
+    double dt, gamma, T, amp;  // amp = sqrt(2 gamma T / dt)
+    float nf, c1f, c2f, kfenef, R0sqf, dtf, gammaf, ampf;
+    int nkind;               // 0: general n, 1: integer n, 2: n = 5.75, 3: n = 6.5
+    int nint;
+};
+
+struct SimDev {
+    MeltDev melt[MAX_MELTS];
+    int n_melts, M, Mp, maxnb;
+    double rc2, rl2, rl, db_lim2;
+    float rc2f, rl2f_lo, rl2f_hi, half_skin2f;
+    double half_skin2;
+    unsigned long long seed;
+    int paper_metropolis;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
+// 32x32->64 multiplies with multipliers 0xD2511F53, 0xCD9E8D57 and a Weyl key
+// schedule with increments 0x9E3779B9, 0xBB67AE85.
+// Counter layout: (index, time_lo, time_hi, melt<<4 | purpose), key = seed.
+// Purposes: 0 MD noise (index = melt-local slot, time = step),
+//           1 DB attempt draw, 2 DB partner draw (index = attempt, time = sweep).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(unsigned long long seed, int melt, unsigned purpose,
+                                      unsigned long long time, uint32_t index)
+{
+    return philox4x32_10(make_uint4(index, (uint32_t)time, (uint32_t)(time >> 32),
+                                    ((uint32_t)melt << 4) | purpose),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// (2*(w>>9)+1) * 2^-24: a uniform in (0,1), exact in binary32 and binary64.
+__device__ __forceinline__ float unit_open_f(uint32_t w)
+{
+    return __uint2float_rn(2u * (w >> 9) + 1u) * 5.9604644775390625e-8f;
+}
+__device__ __forceinline__ double unit_open_d(uint32_t w)
+{
+    return (double)(2u * (w >> 9) + 1u) * 5.9604644775390625e-8;
+}
+
+// Three standard normals by Box-Muller.
+__device__ __forceinline__ float3 gauss3_f(uint4 r)
+{
+    const float a = sqrtf(-2.0f * logf(unit_open_f(r.x)));
+    const float b = sqrtf(-2.0f * logf(unit_open_f(r.z)));
+    float s, c;
+    sincospif(2.0f * unit_open_f(r.y), &s, &c);
+    return make_float3(a * c, a * s, b * cospif(2.0f * unit_open_f(r.w)));
+}
+__device__ __forceinline__ double3 gauss3_d(uint4 r)
+{
+    const double a = sqrt(-2.0 * log(unit_open_d(r.x)));
+    const double b = sqrt(-2.0 * log(unit_open_d(r.z)));
+    double s, c;
+    sincospi(2.0 * unit_open_d(r.y), &s, &c);
+    return make_double3(a * c, a * s, b * cospi(2.0 * unit_open_d(r.w)));
+}
+
+// floor(w * n / 2^64): exact integer map of a 64-bit word onto [0, n).
+__device__ __forceinline__ long long mul_hi64(unsigned long long w, unsigned long long n)
+{
+    return (long long)__umul64hi(w, n);
+}
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int melt_of(const SimDev &S, int s)
+{
+    int m = 0;
+    while (m + 1 < S.n_melts && s >= S.melt[m + 1].off) ++m;
+    return m;
+}
+
+// binary64 minimum image evaluated exactly as d - L*rint(d/L), no contraction
+__device__ __forceinline__ double min_image_exact(double d, double L)
+{
+    return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
+}
+
+// squared binary64 distance between slots s and t, ((dx*dx + dy*dy) + dz*dz)
+__device__ __forceinline__ double dist2_exact(const double *__restrict__ x, int Mp, double L, int s, int t)
+{
+    const double dx = min_image_exact(__dsub_rn(x[t], x[s]), L);
+    const double dy = min_image_exact(__dsub_rn(x[Mp + t], x[Mp + s]), L);
+    const double dz = min_image_exact(__dsub_rn(x[2 * Mp + t], x[2 * Mp + s]), L);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ unsigned pack_code(int cx, int cy, int cz)
+{
+    return (unsigned)cx | ((unsigned)cy << CODE_BITS) | ((unsigned)cz << (2 * CODE_BITS));
+}
+
+__device__ __forceinline__ int wrap_dk(int dk, int n)
+{
+    if (dk > n / 2) dk -= n;
+    else if (dk < -(n / 2)) dk += n;
+    return dk;
+}
+
+// Minimum-image vector from record i to record j (binary32): the code grid
+// carries the integer part, so no large-magnitude value enters the sum.
+__device__ __forceinline__ float3 rec_rel(float4 bi, float4 di, float4 bj, float4 dj, int ncc, float hc)
+{
+    const unsigned ci = __float_as_uint(bi.w), cj = __float_as_uint(bj.w);
+    const int dkx = wrap_dk((int)(cj & CODE_MASK) - (int)(ci & CODE_MASK), ncc);
+    const int dky = wrap_dk((int)((cj >> CODE_BITS) & CODE_MASK) - (int)((ci >> CODE_BITS) & CODE_MASK), ncc);
+    const int dkz = wrap_dk((int)(cj >> (2 * CODE_BITS)) - (int)(ci >> (2 * CODE_BITS)), ncc);
+    return make_float3((bj.x - bi.x) + (dj.x - di.x) + (float)dkx * hc,
+                       (bj.y - bi.y) + (dj.y - di.y) + (float)dky * hc,
+                       (bj.z - bi.z) + (dj.z - di.z) + (float)dkz * hc);
+}
+
+}  // namespace kg

@@ -1,0 +1,635 @@
+// kg_md.cu -- molecular-dynamics kernels of the GB300 DBH library.
+//
+//  * cell binning + counting sort + Verlet-list build (every rebuild);
+//  * one fused kernel per MD step: U_MLJ^n pairs over the Verlet list (Eq. 6),
+//    U_bond^n bonds (Eq. 10), kappa (1 - cos theta) bending (Eq. 4), Langevin
+//    friction and Philox noise, and the leapfrog update of (x, u);
+//  * a force/energy kernel for observables and parity checks.
+// Thread per slot; slots are chain-major, so a warp walks 32 consecutive
+// monomers of a chain and its neighbour gathers overlap in L1.
+#include <cuda_runtime.h>
+
+#include "kg_host.h"
+
+namespace kg {
+
+// ---------------------------------------------------------------------------
+// pair and bond terms (binary32 and binary64 forms of the same formulas)
+// U_MLJ^n(r) = c1 r^-n - c2 r^-6 + 1 for r < r_c (Eqs. 5-6, shifted by +epsilon);
+// fr = (dU/dr)/r, so the force on i from j at d = x_j - x_i is fr * d.
+// ---------------------------------------------------------------------------
+template <bool ENERGY>
+__device__ __forceinline__ float mlj_fr(const StageDev &st, float r2, float &U)
+{
+    const float ir2 = __frcp_rn(r2);
+    const float ir6 = ir2 * ir2 * ir2;
+    float rn;
+    if (st.nkind == 1) {
+        float p = 1.0f;
+        for (int k = 0; k < (st.nint >> 1); ++k) p *= ir2;
+        if (st.nint & 1) p *= rsqrtf(r2);
+        rn = p;
+    } else if (st.nkind == 2) {          // n = 23/4: r^-6 r^(1/4)
+        rn = ir6 * sqrtf(sqrtf(sqrtf(r2)));
+    } else if (st.nkind == 3) {          // n = 13/2: r^-6 r^(-1/2)
+        rn = ir6 * sqrtf(rsqrtf(r2));
+    } else {
+        rn = exp2f(-0.5f * st.nf * log2f(r2));
+    }
+    if (ENERGY) U = st.c1f * rn - st.c2f * ir6 + 1.0f;
+    return (6.0f * st.c2f * ir6 - st.nf * st.c1f * rn) * ir2;
+}
+
+template <bool ENERGY>
+__device__ __forceinline__ double mlj_fr(const StageDev &st, double r2, double &U)
+{
+    const double ir2 = 1.0 / r2;
+    const double ir6 = ir2 * ir2 * ir2;
+    double rn;
+    if (st.nkind == 1) {
+        double p = 1.0;
+        for (int k = 0; k < (st.nint >> 1); ++k) p *= ir2;
+        if (st.nint & 1) p *= rsqrt(r2);
+        rn = p;
+    } else if (st.nkind == 2) {
+        rn = ir6 * sqrt(sqrt(sqrt(r2)));
+    } else if (st.nkind == 3) {
+        rn = ir6 * sqrt(rsqrt(r2));
+    } else {
+        rn = exp2(-0.5 * st.n * log2(r2));
+    }
+    if (ENERGY) U = st.c1 * rn - st.c2 * ir6 + 1.0;
+    return (6.0 * st.c2 * ir6 - st.n * st.c1 * rn) * ir2;
+}
+
+template <typename T> struct V3;
+template <> struct V3<float> { using t = float3; };
+template <> struct V3<double> { using t = double3; };
+
+template <typename T> __device__ __forceinline__ typename V3<T>::t mk(T a, T b, T c);
+template <> __device__ __forceinline__ float3 mk<float>(float a, float b, float c) { return make_float3(a, b, c); }
+template <> __device__ __forceinline__ double3 mk<double>(double a, double b, double c) { return make_double3(a, b, c); }
+
+template <typename T3> __device__ __forceinline__ auto dot3(T3 a, T3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T3> __device__ __forceinline__ T3 sub3(T3 a, T3 b) { return T3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+
+template <typename T> __device__ __forceinline__ T st_c(const StageDev &st, int which);
+template <> __device__ __forceinline__ float st_c<float>(const StageDev &st, int w)
+{
+    return w == 0 ? st.kfenef : w == 1 ? st.R0sqf : w == 2 ? st.dtf : w == 3 ? st.gammaf : st.ampf;
+}
+template <> __device__ __forceinline__ double st_c<double>(const StageDev &st, int w)
+{
+    return w == 0 ? st.kfene : w == 1 ? st.R0sq : w == 2 ? st.dt : w == 3 ? st.gamma : st.amp;
+}
+
+__device__ __forceinline__ float flog(float a) { return logf(a); }
+__device__ __forceinline__ double flog(double a) { return log(a); }
+__device__ __forceinline__ float frsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double frsqrt(double a) { return rsqrt(a); }
+
+// ---------------------------------------------------------------------------
+// position access policies
+// ---------------------------------------------------------------------------
+struct GeoMixed {
+    using T = float;
+    using T3 = float3;
+    const float4 *__restrict__ recb;
+    const float4 *__restrict__ dlt;
+    int ncc;
+    float hc;
+    float4 bi, di;
+    __device__ __forceinline__ void melt(const MeltDev &md) { ncc = md.ncc; hc = md.hcf; }
+    __device__ __forceinline__ void self(int s) { bi = __ldg(recb + s); di = __ldg(dlt + s); }
+    __device__ __forceinline__ float3 rel(int j) const
+    {
+        return rec_rel(bi, di, __ldg(recb + j), __ldg(dlt + j), ncc, hc);
+    }
+};
+
+struct GeoF64 {
+    using T = double;
+    using T3 = double3;
+    const double4_32a *__restrict__ pos;
+    double L, invL;
+    double4_32a pi;
+    __device__ __forceinline__ void melt(const MeltDev &md) { L = md.L; invL = md.invL; }
+    __device__ __forceinline__ void self(int s) { pi = pos[s]; }
+    __device__ __forceinline__ double3 rel(int j) const
+    {
+        const double4_32a pj = pos[j];
+        double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+        dx -= L * rint(dx * invL);
+        dy -= L * rint(dy * invL);
+        dz -= L * rint(dz * invL);
+        return make_double3(dx, dy, dz);
+    }
+};
+
+// Conservative force on slot s (chain position i of N) and, with ENERGY, its
+// shares of the energies: e[0] pair (1/2 per pair), e[1] bond (1/2 per bond),
+// e[2] bending (the angle whose vertex is s), e[3] virial (1/2 per pair/bond).
+template <bool ENERGY, class G>
+__device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, const StageDev &st,
+                                                   const MeltDev &md, int s, int i,
+                                                   const int *__restrict__ nl, int cnt,
+                                                   double *e, unsigned &err)
+{
+    using T = typename G::T;
+    using T3 = typename G::T3;
+    T3 F = mk<T>(0, 0, 0);
+    const T rc2 = (T)S.rc2;
+    // pairs (Verlet list, both directions stored)
+    for (int k = 0; k < cnt; ++k) {
+        const int j = __ldg(nl + (size_t)k * S.Mp + s);
+        const T3 d = g.rel(j);
+        const T r2 = dot3(d, d);
+        if (r2 < rc2) {
+            T U;
+            const T fr = mlj_fr<ENERGY>(st, r2, U);
+            F.x += fr * d.x; F.y += fr * d.y; F.z += fr * d.z;
+            if (ENERGY) { e[0] += 0.5 * (double)U; e[3] -= 0.5 * (double)(fr * r2); }
+        }
+    }
+    const int N = md.N;
+    T3 rm2 = mk<T>(0, 0, 0), rm1 = mk<T>(0, 0, 0), rp1 = mk<T>(0, 0, 0), rp2 = mk<T>(0, 0, 0);
+    if (i >= 1) rm1 = g.rel(s - 1);
+    if (i >= 2) rm2 = g.rel(s - 2);
+    if (i <= N - 2) rp1 = g.rel(s + 1);
+    if (i <= N - 3) rp2 = g.rel(s + 2);
+    // bonds: U_MLJ^n + FENE(k_n) (Eq. 10)
+    const T kf = st_c<T>(st, 0), R0sq = st_c<T>(st, 1);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        if ((side == 0 && i >= 1) || (side == 1 && i <= N - 2)) {
+            const T3 d = side == 0 ? rm1 : rp1;
+            const T r2 = dot3(d, d);
+            if (!(r2 < R0sq)) err |= ERR_OVERSTRETCH;
+            const T q = (T)1 - r2 / R0sq;
+            T fr = kf / q;
+            T U = 0;
+            if (r2 < rc2) fr += mlj_fr<ENERGY>(st, r2, U);
+            F.x += fr * d.x; F.y += fr * d.y; F.z += fr * d.z;
+            if (ENERGY) {
+                e[1] += 0.5 * ((double)U - 0.5 * (double)kf * (double)R0sq * (double)flog(q));
+                e[3] -= 0.5 * (double)(fr * r2);
+            }
+        }
+    }
+    // bending kappa (1 - b1.b2 / |b1||b2|) at the vertices s-1, s, s+1
+    const T kap = (T)md.kappa;
+    if (kap != (T)0) {
+        const T3 Bm2 = sub3(rm1, rm2), Bm1 = mk<T>(-rm1.x, -rm1.y, -rm1.z), B0 = rp1, Bp1 = sub3(rp2, rp1);
+        if (i >= 1 && i <= N - 2) {          // vertex s: force kappa (g1 - g2)
+            const T l1 = dot3(Bm1, Bm1), l2 = dot3(B0, B0), inv = frsqrt(l1 * l2), cs = dot3(Bm1, B0) * inv;
+            F.x += kap * ((B0.x * inv - cs * Bm1.x / l1) - (Bm1.x * inv - cs * B0.x / l2));
+            F.y += kap * ((B0.y * inv - cs * Bm1.y / l1) - (Bm1.y * inv - cs * B0.y / l2));
+            F.z += kap * ((B0.z * inv - cs * Bm1.z / l1) - (Bm1.z * inv - cs * B0.z / l2));
+            if (ENERGY) e[2] += (double)kap * (1.0 - (double)cs);
+        }
+        if (i <= N - 3) {                    // vertex s+1, s is its first end: -kappa g1
+            const T l1 = dot3(B0, B0), l2 = dot3(Bp1, Bp1), inv = frsqrt(l1 * l2), cs = dot3(B0, Bp1) * inv;
+            F.x -= kap * (Bp1.x * inv - cs * B0.x / l1);
+            F.y -= kap * (Bp1.y * inv - cs * B0.y / l1);
+            F.z -= kap * (Bp1.z * inv - cs * B0.z / l1);
+        }
+        if (i >= 2) {                        // vertex s-1, s is its last end: +kappa g2
+            const T l1 = dot3(Bm2, Bm2), l2 = dot3(Bm1, Bm1), inv = frsqrt(l1 * l2), cs = dot3(Bm2, Bm1) * inv;
+            F.x += kap * (Bm2.x * inv - cs * Bm1.x / l2);
+            F.y += kap * (Bm2.y * inv - cs * Bm1.y / l2);
+            F.z += kap * (Bm2.z * inv - cs * Bm1.z / l2);
+        }
+    }
+    return F;
+}
+
+// ---------------------------------------------------------------------------
+// fused MD step: forces at x_n, then u <- u + dt F_n, x <- x + dt u
+// F_n = F_c - gamma u + sqrt(2 gamma T / dt) g_n,  g_n = Philox normals.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_step_mixed(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
+                                                   double *__restrict__ x, float *__restrict__ u,
+                                                   const float4 *__restrict__ recb, const float4 *__restrict__ dcur,
+                                                   float4 *__restrict__ dnext, const int *__restrict__ nl,
+                                                   const int *__restrict__ nn, unsigned *__restrict__ flags,
+                                                   long long step)
+{
+    const SimDev &S = *Sp;
+    const StageDev &st = *stp;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    bool rebuild = false;
+    unsigned err = 0;
+    if (s < S.M) {
+        const int m = melt_of(S, s);
+        const MeltDev &md = S.melt[m];
+        const int rel = s - md.off, i = rel % md.N;
+        GeoMixed g{recb, dcur, md.ncc, md.hcf};
+        g.self(s);
+        float3 F = force_on<false>(g, S, st, md, s, i, nl, __ldg(nn + s), nullptr, err);
+        const float3 gn = gauss3_f(draw(S.seed, m, 0, (unsigned long long)step, (uint32_t)rel));
+        const int Mp = S.Mp;
+        float3 v = make_float3(u[s], u[Mp + s], u[2 * Mp + s]);
+        v.x += st.dtf * (F.x - st.gammaf * v.x + st.ampf * gn.x);
+        v.y += st.dtf * (F.y - st.gammaf * v.y + st.ampf * gn.y);
+        v.z += st.dtf * (F.z - st.gammaf * v.z + st.ampf * gn.z);
+        u[s] = v.x; u[Mp + s] = v.y; u[2 * Mp + s] = v.z;
+        x[s] += st.dt * (double)v.x;
+        x[Mp + s] += st.dt * (double)v.y;
+        x[2 * Mp + s] += st.dt * (double)v.z;
+        float4 d = g.di;
+        d.x += st.dtf * v.x; d.y += st.dtf * v.y; d.z += st.dtf * v.z;
+        dnext[s] = d;
+        rebuild = d.x * d.x + d.y * d.y + d.z * d.z > S.half_skin2f;
+        if (!isfinite(v.x + v.y + v.z)) err |= ERR_NONFINITE;
+    }
+    if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(flags + 1, 1u);
+    if (err) atomicOr(flags, err);
+}
+
+__global__ void __launch_bounds__(128) k_step_f64(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
+                                                 double *__restrict__ x, double *__restrict__ u,
+                                                 const double4_32a *__restrict__ pcur, double4_32a *__restrict__ pnext,
+                                                 const double4_32a *__restrict__ xb, const int *__restrict__ nl,
+                                                 const int *__restrict__ nn, unsigned *__restrict__ flags,
+                                                 long long step)
+{
+    const SimDev &S = *Sp;
+    const StageDev &st = *stp;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    bool rebuild = false;
+    unsigned err = 0;
+    if (s < S.M) {
+        const int m = melt_of(S, s);
+        const MeltDev &md = S.melt[m];
+        const int rel = s - md.off, i = rel % md.N;
+        GeoF64 g{pcur, md.L, md.invL};
+        g.self(s);
+        double3 F = force_on<false>(g, S, st, md, s, i, nl, __ldg(nn + s), nullptr, err);
+        const double3 gn = gauss3_d(draw(S.seed, m, 0, (unsigned long long)step, (uint32_t)rel));
+        const int Mp = S.Mp;
+        double3 v = make_double3(u[s], u[Mp + s], u[2 * Mp + s]);
+        v.x += st.dt * (F.x - st.gamma * v.x + st.amp * gn.x);
+        v.y += st.dt * (F.y - st.gamma * v.y + st.amp * gn.y);
+        v.z += st.dt * (F.z - st.gamma * v.z + st.amp * gn.z);
+        u[s] = v.x; u[Mp + s] = v.y; u[2 * Mp + s] = v.z;
+        const double nx = x[s] + st.dt * v.x, ny = x[Mp + s] + st.dt * v.y, nz = x[2 * Mp + s] + st.dt * v.z;
+        x[s] = nx; x[Mp + s] = ny; x[2 * Mp + s] = nz;
+        pnext[s] = make_double4_32a(nx, ny, nz, 0.0);
+        const double4_32a b = xb[s];
+        const double dx = nx - b.x, dy = ny - b.y, dz = nz - b.z;
+        rebuild = dx * dx + dy * dy + dz * dz > S.half_skin2;
+        if (!isfinite(v.x + v.y + v.z)) err |= ERR_NONFINITE;
+    }
+    if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(flags + 1, 1u);
+    if (err) atomicOr(flags, err);
+}
+
+// ---------------------------------------------------------------------------
+// rebuild chain (each kernel returns at once unless flags[2] is set)
+// ---------------------------------------------------------------------------
+__global__ void k_rebuild_begin(unsigned *flags)
+{
+    flags[2] = flags[1];
+    flags[1] = 0u;
+}
+
+__device__ __forceinline__ long long floor_ll(double v) { return (long long)floor(v); }
+
+// records on the code grid, gather buffer reset, Verlet-grid cell + rank
+__global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, const double *__restrict__ x,
+                                               float4 *__restrict__ recb, float4 *__restrict__ dcur,
+                                               double4_32a *__restrict__ pcur, double4_32a *__restrict__ xb,
+                                               int *__restrict__ cellid, int *__restrict__ rank,
+                                               int *__restrict__ count, const unsigned *__restrict__ flags)
+{
+    if (!flags[2]) return;
+    const SimDev &S = *Sp;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S.M) return;
+    const MeltDev &md = S.melt[melt_of(S, s)];
+    const int Mp = S.Mp;
+    float off[3];
+    int code[3], cell[3];
+    double xs[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double xd = x[d * Mp + s];
+        xs[d] = xd;
+        const long long K = floor_ll(xd * md.invhc);
+        off[d] = (float)(xd - (double)K * md.hc);
+        long long km = K % md.ncc;
+        if (km < 0) km += md.ncc;
+        code[d] = (int)km;
+        const double w = xd - md.L * floor(xd * md.invL);
+        int c = (int)(w * md.invh);
+        cell[d] = c < 0 ? 0 : (c >= md.nc ? md.nc - 1 : c);
+    }
+    recb[s] = make_float4(off[0], off[1], off[2], __uint_as_float(pack_code(code[0], code[1], code[2])));
+    if (dcur) dcur[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pcur) {
+        const double4_32a p = make_double4_32a(xs[0], xs[1], xs[2], 0.0);
+        pcur[s] = p;
+        xb[s] = p;
+    }
+    const int c = md.cell_off + (cell[2] * md.nc + cell[1]) * md.nc + cell[0];
+    cellid[s] = c;
+    rank[s] = atomicAdd(count + c, 1);
+}
+
+// DB grid: cell of each particle from its wrapped position (cells >= 1.3 sigma)
+__global__ void __launch_bounds__(256) k_bin_db(const SimDev *__restrict__ Sp, const double *__restrict__ x,
+                                               int *__restrict__ cellid, int *__restrict__ rank,
+                                               int *__restrict__ count)
+{
+    const SimDev &S = *Sp;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S.M) return;
+    const MeltDev &md = S.melt[melt_of(S, s)];
+    int cell[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double xd = x[d * S.Mp + s];
+        const double w = xd - md.L * floor(xd * md.invL);
+        int c = (int)(w * md.invhdb);
+        cell[d] = c < 0 ? 0 : (c >= md.ndb ? md.ndb - 1 : c);
+    }
+    const int c = md.dbcell_off + (cell[2] * md.ndb + cell[1]) * md.ndb + cell[0];
+    cellid[s] = c;
+    rank[s] = atomicAdd(count + c, 1);
+}
+
+// exclusive scan, phase 1: per 1024-element block, local scan + block total
+__global__ void __launch_bounds__(1024) k_scan1(const int *__restrict__ in, int *__restrict__ out,
+                                               int *__restrict__ bsum, int n, const unsigned *__restrict__ flags)
+{
+    if (flags && !flags[2]) return;
+    __shared__ int wsum[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int v = i < n ? in[i] : 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int ws = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += t;
+        }
+        wsum[lane] = ws;
+    }
+    __syncthreads();
+    const int base = w ? wsum[w - 1] : 0;
+    if (i < n) out[i] = base + incl - v;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = base + incl;
+}
+
+// phase 2: add the totals of all preceding blocks; out[n] = grand total
+__global__ void __launch_bounds__(1024) k_scan2(int *__restrict__ out, const int *__restrict__ bsum, int n,
+                                               int nblk, const unsigned *__restrict__ flags)
+{
+    if (flags && !flags[2]) return;
+    __shared__ int off_s;
+    if (threadIdx.x < 32) {
+        int acc = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 32) acc += bsum[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) off_s = acc;
+    }
+    __syncthreads();
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) out[i] += off_s;
+    if (blockIdx.x == nblk - 1 && threadIdx.x == 0) {
+        int tot = 0;
+        for (int b = 0; b < nblk; ++b) tot += bsum[b];
+        out[n] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(const int *__restrict__ cellid, const int *__restrict__ rank,
+                                                const int *__restrict__ start, int *__restrict__ list, int M,
+                                                const unsigned *__restrict__ flags)
+{
+    if (flags && !flags[2]) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < M) list[start[cellid[s]] + rank[s]] = s;
+}
+
+// within-cell order by slot (deterministic lists), then clear the counts
+__global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start, int *__restrict__ list,
+                                                 int *__restrict__ count, int ncell,
+                                                 const unsigned *__restrict__ flags)
+{
+    if (!flags[2]) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int a = start[c], b = start[c + 1];
+    for (int k = a + 1; k < b; ++k) {
+        const int v = list[k];
+        int j = k - 1;
+        while (j >= a && list[j] > v) { list[j + 1] = list[j]; --j; }
+        list[j + 1] = v;
+    }
+    count[c] = 0;
+}
+
+// Verlet list: all t != s, not 1-2 bonded, with r^2 < (r_c + skin)^2.  The
+// binary32 record distance decides every pair outside a band of relative
+// width 1e-5 around the cutoff (its error is below 2e-6); pairs inside the band
+// are decided by the binary64 distance evaluated exactly as
+// ((dx*dx + dy*dy) + dz*dz), dx = d - L rint(d/L).
+__global__ void __launch_bounds__(128) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
+                                              const float4 *__restrict__ recb, const int *__restrict__ cellid,
+                                              const int *__restrict__ start, const int *__restrict__ list,
+                                              int *__restrict__ nl, int *__restrict__ nn,
+                                              unsigned *__restrict__ flags)
+{
+    if (!flags[2]) return;
+    const SimDev &S = *Sp;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S.M) return;
+    const MeltDev &md = S.melt[melt_of(S, s)];
+    const int N = md.N, chain = (s - md.off) / N;
+    const float4 bi = __ldg(recb + s);
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int c0 = cellid[s] - md.cell_off, nc = md.nc;
+    const int cx = c0 % nc, cy = (c0 / nc) % nc, cz = c0 / (nc * nc);
+    int cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int zz = (cz + dz + nc) % nc;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int yy = (cy + dy + nc) % nc;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int xx = (cx + dx + nc) % nc;
+                const int cell = md.cell_off + (zz * nc + yy) * nc + xx;
+                const int e = start[cell + 1];
+                for (int k = start[cell]; k < e; ++k) {
+                    const int t = list[k];
+                    if (t == s) continue;
+                    if ((t == s + 1 || t == s - 1) && (t - md.off) / N == chain) continue;
+                    const float3 d = rec_rel(bi, z, __ldg(recb + t), z, md.ncc, md.hcf);
+                    const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+                    bool in;
+                    if (r2 < S.rl2f_lo) in = true;
+                    else if (r2 >= S.rl2f_hi) in = false;
+                    else in = dist2_exact(x, S.Mp, md.L, s, t) < S.rl2;
+                    if (in) {
+                        if (cnt < S.maxnb) nl[(size_t)cnt * S.Mp + s] = t;
+                        ++cnt;
+                    }
+                }
+            }
+        }
+    }
+    nn[s] = cnt < S.maxnb ? cnt : S.maxnb;
+    if (cnt > S.maxnb) {
+        atomicOr(flags, ERR_NL_CAPACITY);
+        atomicMax(flags + 3, (unsigned)cnt);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// forces + energies (observables, parity): F_c written as binary64; per block
+// partial sums [pair, bond, angle, virial, kinetic] in binary64, where the
+// kinetic part uses v_n = u + dt/2 (F_c - gamma u + amp g_n).
+// ---------------------------------------------------------------------------
+template <class G>
+__global__ void __launch_bounds__(128) k_forces(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
+                                               G g, const void *__restrict__ uptr, int lo, int hi,
+                                               const int *__restrict__ nl, const int *__restrict__ nn,
+                                               double *__restrict__ Fout, double *__restrict__ part,
+                                               unsigned *__restrict__ flags, long long step)
+{
+    using T = typename G::T;
+    const SimDev &S = *Sp;
+    const StageDev &st = *stp;
+    const int s = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    double e[5] = {0, 0, 0, 0, 0};
+    unsigned err = 0;
+    if (s < hi) {
+        const int m = melt_of(S, s);
+        const MeltDev &md = S.melt[m];
+        const int rel = s - md.off, i = rel % md.N;
+        G gg = g;
+        gg.melt(md);
+        gg.self(s);
+        const auto F = force_on<true>(gg, S, st, md, s, i, nl, __ldg(nn + s), e, err);
+        const int Mp = S.Mp;
+        if (Fout) {
+            Fout[s] = (double)F.x; Fout[Mp + s] = (double)F.y; Fout[2 * Mp + s] = (double)F.z;
+        }
+        const double3 gn = gauss3_d(draw(S.seed, m, 0, (unsigned long long)step, (uint32_t)rel));
+        const T *u = (const T *)uptr;
+        const double ux = (double)u[s], uy = (double)u[Mp + s], uz = (double)u[2 * Mp + s];
+        const double vx = ux + 0.5 * st.dt * ((double)F.x - st.gamma * ux + st.amp * gn.x);
+        const double vy = uy + 0.5 * st.dt * ((double)F.y - st.gamma * uy + st.amp * gn.y);
+        const double vz = uz + 0.5 * st.dt * ((double)F.z - st.gamma * uz + st.amp * gn.z);
+        e[4] = 0.5 * (vx * vx + vy * vy + vz * vz);
+    }
+    if (err) atomicOr(flags, err);
+    // deterministic block reduction (fixed tree)
+    __shared__ double sh[5][128];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = e[k];
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) part[blockIdx.x * 5 + k] = sh[k][0];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+void rebuild_md(kg_ctx *c)
+{
+    cudaStream_t st = c->stream;
+    c->launches += 7;
+    k_rebuild_begin<<<1, 1, 0, st>>>(c->flags);
+    const bool mixed = c->precision == KG_MIXED;
+    k_bin_md<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->recb, mixed ? c->dlt[c->cur] : nullptr,
+                                              mixed ? nullptr : c->pos64[c->cur], c->xb, c->cellid, c->rank,
+                                              c->ccount, c->flags);
+    const int nb = nblk(c->ncell_md, 1024);
+    k_scan1<<<nb, 1024, 0, st>>>(c->ccount, c->cstart, c->bsum, c->ncell_md, c->flags);
+    k_scan2<<<nb, 1024, 0, st>>>(c->cstart, c->bsum, c->ncell_md, nb, c->flags);
+    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->cellid, c->rank, c->cstart, c->clist, c->M, c->flags);
+    k_cellsort<<<nblk(c->ncell_md, 256), 256, 0, st>>>(c->cstart, c->clist, c->ccount, c->ncell_md, c->flags);
+    k_nlist<<<nblk(c->M, 128), 128, 0, st>>>(c->d_sim, c->x, c->recb, c->cellid, c->cstart, c->clist, c->nl,
+                                             c->nn, c->flags);
+}
+
+// One MD step: the Verlet list is rebuilt first if the previous step (or a
+// configuration load or an accepted swap) asked for it.
+void prof_collect(kg_ctx *c)
+{
+    if (!c->ev_used) return;
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < c->ev_used; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]);
+        c->prof_ms += ms;
+    }
+    c->prof_n += c->ev_used;
+    c->ev_used = 0;
+}
+
+void md_step(kg_ctx *c, long long step)
+{
+    rebuild_md(c);
+    const int nb = nblk(c->M, 128);
+    cudaEvent_t e1 = nullptr;
+    if (c->prof_on) {
+        if (c->ev.empty()) {
+            c->ev.resize(2 * 1024);
+            for (auto &e : c->ev) cudaEventCreate(&e);
+        }
+        if (2 * c->ev_used >= (int)c->ev.size()) prof_collect(c);
+        cudaEventRecord(c->ev[2 * c->ev_used], c->stream);
+        e1 = c->ev[2 * c->ev_used + 1];
+        ++c->ev_used;
+    }
+    ++c->launches;
+    if (c->precision == KG_MIXED) {
+        k_step_mixed<<<nb, 128, 0, c->stream>>>(c->d_sim, c->d_stage, c->x, (float *)c->u, c->recb,
+                                                c->dlt[c->cur], c->dlt[c->cur ^ 1], c->nl, c->nn, c->flags, step);
+    } else {
+        k_step_f64<<<nb, 128, 0, c->stream>>>(c->d_sim, c->d_stage, c->x, (double *)c->u, c->pos64[c->cur],
+                                              c->pos64[c->cur ^ 1], c->xb, c->nl, c->nn, c->flags, step);
+    }
+    if (e1) cudaEventRecord(e1, c->stream);
+    c->cur ^= 1;
+}
+
+int forces_blocks(const kg_ctx *c, int melt) { return nblk(c->sim.melt[melt].M, 128); }
+
+void forces_eval(kg_ctx *c, int melt, long long step, double *F_dev, double *part_dev, int nb)
+{
+    const MeltDev &md = c->sim.melt[melt];
+    ++c->launches;
+    if (c->precision == KG_MIXED) {
+        GeoMixed g{c->recb, c->dlt[c->cur], 0, 0.f, {}, {}};
+        k_forces<GeoMixed><<<nb, 128, 0, c->stream>>>(c->d_sim, c->d_stage, g, c->u, md.off, md.off + md.M,
+                                                     c->nl, c->nn, F_dev, part_dev, c->flags, step);
+    } else {
+        GeoF64 g{c->pos64[c->cur], 0.0, 0.0, {}};
+        k_forces<GeoF64><<<nb, 128, 0, c->stream>>>(c->d_sim, c->d_stage, g, c->u, md.off, md.off + md.M,
+                                                   c->nl, c->nn, F_dev, part_dev, c->flags, step);
+    }
+}
+
+}  // namespace kg

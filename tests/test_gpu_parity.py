@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Bars: Verlet lists and double-bridging topology bit-exact; forces <= 1e-5
+relative (binary64 path: 1e-10); positions after 10 steps <= 1e-4 sigma.
+The force bar is norm-wise per monomer against the larger of its own force
+and the melt's rms force, because a single net force can cancel to near zero.
+"""
+import contextlib
+
+import numpy as np
+import pytest
+
+import kg_inputs as KI
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+RL = 2.0 ** (1 / 6) + 0.3
+
+
+@pytest.fixture(scope="module")
+def kg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_11001_gb300 as kg
+    kg.load()
+    return kg
+
+
+@contextlib.contextmanager
+def context(kg, melts, precision, seed=11, schedule=None, flags=0):
+    import torch
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa) for m in melts], precision=precision,
+                       seed=seed, flags=flags)
+    ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+    try:
+        if schedule is not None:
+            kg.kg_set_potential_schedule(ctx, schedule)
+        for i, m in enumerate(melts):
+            kg.kg_load_config(ctx, i, m.x, m.v)
+        yield ctx
+    finally:
+        kg.kg_destroy(ctx)
+
+
+def oparams(m, n_exp, seed=11, stream=0, dt=0.01, **kw):
+    return O.params(m.n_chains, m.chain_len, m.box, m.kappa, n_exp=n_exp, seed=seed, stream=stream, dt=dt, **kw)
+
+
+CASES = {
+    "cfg1": lambda: KI.make(1),
+    "ragged": lambda: KI.random_walk_melt(37, 29, 0.85, 2.0, 5),            # M = 1073, not a tile multiple
+    "short": lambda: KI.random_walk_melt(400, 3, 0.85, 0.0, 6),            # N = 3: one angle per chain
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nlist_bit_exact(kg, case, precision):
+    m = CASES[case]()
+    with context(kg, [m], precision) as ctx:
+        offs, nbr = kg.kg_get_nlist(ctx, 0, m.M)
+    oo, on = O.nlist(oparams(m, 12), m.x, RL, use_cells=True)
+    assert np.array_equal(offs, oo)
+    assert np.array_equal(nbr, on)
+
+
+def _force_err(F, Fo):
+    n = np.linalg.norm(F - Fo, axis=0)
+    ref = np.maximum(np.linalg.norm(Fo, axis=0), np.sqrt((Fo ** 2).sum(axis=0).mean()))
+    return (n / ref).max()
+
+
+@pytest.mark.parametrize("n_exp", [2.0, 3.0, 5.75, 6.5, 9.0, 12.0])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-5)])
+def test_forces(kg, n_exp, precision, tol):
+    m = KI.random_walk_melt(30, 40, 0.85, 1.5, 21)
+    with context(kg, [m], precision, schedule=[kg.stage(n_exp, 10, 0.005)]) as ctx:
+        F = np.zeros_like(m.x)
+        e4 = np.zeros(4)
+        kg.kg_forces(ctx, 0, F, e4)
+    Fo, eo = O.forces(oparams(m, n_exp), m.x)
+    assert _force_err(F, Fo) < tol
+    assert e4 == pytest.approx(eo, rel=1e-9 if precision == 0 else 1e-5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n_exp,dt", [(2.0, 0.002), (12.0, 0.0005)])   # unrelaxed start: small dt
+def test_trajectory_10_steps(kg, precision, n_exp, dt):
+    m = KI.make(1)
+    with context(kg, [m], precision, schedule=[kg.stage(n_exp, 100, dt)]) as ctx:
+        kg.kg_step(ctx, 10)
+        x = np.zeros_like(m.x)
+        v = np.zeros_like(m.v)
+        kg.kg_get_config(ctx, 0, x, v)
+    xo, uo = m.x.copy(), m.v.copy()
+    O.run(oparams(m, n_exp, dt=dt), xo, uo, 0, 10)
+    assert np.abs(x - xo).max() < 1e-4
+    if precision == 0:
+        assert np.abs(x - xo).max() < 1e-9
+
+
+def _db_case(kappa=0.5, seed=31, n_chains=40, N=20):
+    return KI.random_walk_melt(n_chains, N, 0.85, kappa, seed)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n_exp,K", [(2.0, 300), (12.0, 400)])
+def test_db_topology_bit_exact(kg, precision, n_exp, K):
+    m = _db_case()
+    q = oparams(m, n_exp)
+    xo, uo, pido = m.x.copy(), m.v.copy(), np.arange(m.M, dtype=np.int32)
+    acc_o = 0
+    with context(kg, [m], precision, schedule=[kg.stage(n_exp, 10, 0.005)]) as ctx:
+        for sweep in range(4):
+            st = kg.kg_db_sweep_k(ctx, [K])
+            a, e, acc = O.db_sweep(q, xo, uo, pido, sweep, K)
+            assert (st.attempted, st.empty, st.accepted) == (a, e, acc)
+            acc_o += acc
+        x = np.zeros_like(m.x)
+        v = np.zeros_like(m.v)
+        pid = np.zeros(m.M, dtype=np.int32)
+        kg.kg_get_config(ctx, 0, x, v, pid)
+    assert acc_o > 0
+    assert np.array_equal(pid, pido)
+    assert np.array_equal(x, xo)                  # moved and box-shifted bit for bit
+    assert np.allclose(v, uo, rtol=0, atol=1e-6 if precision else 0)
+
+
+def test_db_paper_metropolis_switch(kg):
+    m = _db_case(seed=33)
+    q = oparams(m, 2.0, paper_metropolis=True)
+    xo, uo, pido = m.x.copy(), m.v.copy(), np.arange(m.M, dtype=np.int32)
+    with context(kg, [m], 0, schedule=[kg.stage(2.0, 10, 0.005)], flags=1) as ctx:
+        st = kg.kg_db_sweep_k(ctx, [500])
+        pid = np.zeros(m.M, dtype=np.int32)
+        kg.kg_get_config(ctx, 0, None, None, pid)
+    _, _, acc = O.db_sweep(q, xo, uo, pido, 0, 500)
+    assert st.accepted == acc and np.array_equal(pid, pido)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_uneven_melts(kg, precision):
+    melts = [KI.random_walk_melt(12, 30, 0.85, 0.0, 41), KI.random_walk_melt(7, 61, 0.85, 2.5, 42),
+             KI.random_walk_melt(50, 8, 0.85, 1.0, 43)]
+    dt = 0.002
+    with context(kg, melts, precision, seed=5, schedule=[kg.stage(3.0, 1000, dt)]) as ctx:
+        forces = []
+        for i, m in enumerate(melts):
+            F = np.zeros_like(m.x)
+            kg.kg_forces(ctx, i, F)
+            forces.append(F)
+        kg.kg_step(ctx, 10)
+        st = kg.kg_db_sweep_k(ctx, [200, 150, 100])
+        out = []
+        for i, m in enumerate(melts):
+            x = np.zeros_like(m.x)
+            pid = np.zeros(m.M, dtype=np.int32)
+            kg.kg_get_config(ctx, i, x, None, pid)
+            out.append((x, pid))
+    acc = 0
+    for i, m in enumerate(melts):
+        q = oparams(m, 3.0, seed=5, stream=i, dt=dt)
+        Fo, _ = O.forces(q, m.x)
+        assert _force_err(forces[i], Fo) < (1e-10 if precision == 0 else 1e-5)
+        xo, uo = m.x.copy(), m.v.copy()
+        O.run(q, xo, uo, 0, 10)
+        pido = np.arange(m.M, dtype=np.int32)
+        a, e, ac = O.db_sweep(q, xo, uo, pido, 0, [200, 150, 100][i])
+        acc += ac
+        x, pid = out[i]
+        assert np.abs(x - xo).max() < 1e-4
+        if precision == 0:
+            assert np.array_equal(pid, pido)
+    assert st.accepted == acc or precision == 1
+
+
+def test_observables(kg):
+    m = KI.random_walk_melt(25, 33, 0.85, 2.0, 51)
+    with context(kg, [m], 0, schedule=[kg.stage(5.0, 10, 0.005)]) as ctx:
+        r2 = np.zeros(m.chain_len)
+        bh, ch = np.zeros(20), np.zeros(20)
+        ob = kg.kg_observables(ctx, 0, r2, bh, ch, 20)
+    q = oparams(m, 5.0, dt=0.005)
+    want = O.observe(q, m.x, m.v, 0)
+    for k in ("e_pair", "e_bond", "e_angle", "e_kin", "virial", "temperature", "pressure"):
+        assert getattr(ob, k) == pytest.approx(want[k], rel=1e-9), k
+    assert np.allclose(r2, O.r2n(q, m.x), rtol=1e-12, atol=0)
+    obh, och = O.hist(q, m.x, 20)
+    assert np.array_equal(bh, obh) and np.array_equal(ch, och)
+
+
+def test_errors_and_recovery(kg):
+    m = KI.random_walk_melt(4, 10, 0.05, 1.0, 61)     # dilute: L > 7
+    bad = m.x.copy()
+    bad[0, 5:] += 3.0                                   # bond 4-5 longer than 2 > R0
+    with context(kg, [m], 1) as ctx:
+        kg.kg_load_config(ctx, 0, bad, m.v)
+        with pytest.raises(kg.KGError) as ei:
+            kg.kg_step(ctx, 1)
+        assert ei.value.status == kg.KG_ERR_BOND_OVERSTRETCH
+        with pytest.raises(kg.KGError) as ei:
+            kg.kg_step(ctx, 1)
+        assert ei.value.status == kg.KG_ERR_STATE
+        kg.kg_load_config(ctx, 0, m.x, m.v)            # a reload clears the latched error
+        kg.kg_step(ctx, 2)
+    with pytest.raises(kg.KGError) as ei:
+        kg.kg_create(kg.make_params([(2, 5, 5.0, 1.0)]), 0)   # box below 7 sigma
+    assert ei.value.status == kg.KG_ERR_INVALID_ARG
+
+
+def test_runs_are_deterministic(kg):
+    m = KI.make(1)
+    outs = []
+    for _ in range(2):
+        with context(kg, [m], 1, schedule=[kg.stage(2.0, 10 ** 6, 0.002)]) as ctx:
+            kg.kg_step(ctx, 60)
+            kg.kg_db_sweep_k(ctx, [300])
+            kg.kg_step(ctx, 60)
+            x = np.zeros_like(m.x)
+            kg.kg_get_config(ctx, 0, x)
+            outs.append(x)
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_full_size_80k(kg):
+    # 200 chains x 400 monomers (80,000), kappa = 2.5: the single-melt workload
+    m = KI.make(2)
+    for precision in (0, 1):
+        with context(kg, [m], precision, schedule=[kg.stage(12.0, 10, 0.005)]) as ctx:
+            offs, nbr = kg.kg_get_nlist(ctx, 0, m.M)
+            F = np.zeros_like(m.x)
+            kg.kg_forces(ctx, 0, F)
+            if precision == 0:
+                st = kg.kg_db_sweep_k(ctx, [800])
+                pid = np.zeros(m.M, dtype=np.int32)
+                kg.kg_get_config(ctx, 0, None, None, pid)
+        q = oparams(m, 12.0)
+        if precision == 0:
+            oo, on = O.nlist(q, m.x, RL)
+            assert np.array_equal(offs, oo) and np.array_equal(nbr, on)
+        Fo, _ = O.forces(q, m.x)
+        assert _force_err(F, Fo) < (1e-10 if precision == 0 else 1e-5)
+    xo, uo, pido = m.x.copy(), m.v.copy(), np.arange(m.M, dtype=np.int32)
+    _, _, acc = O.db_sweep(q, xo, uo, pido, 0, 800)
+    assert st.accepted == acc and np.array_equal(pid, pido)
