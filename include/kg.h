@@ -88,6 +88,11 @@ typedef struct {
     double db_bond_max;       /* longest new bond of a DB swap, 1.3 (Sec. II.B (ii))    */
     double r_mc;              /* DB attempts per monomer per tau, 1e-3 (Sec. II.B)      */
     double skin;              /* neighbour-list skin (0.3 when <= 0)                    */
+    double fene_qmin;         /* 0: FENE exactly as Eq. 3, r >= R0 is an error;
+                                 q in (0, 0.25): the FENE log term is continued beyond
+                                 r* = R0 sqrt(1 - q) by the quadratic in r^2 that
+                                 matches its value and slope there (finite past R0;
+                                 r >= 2 R0 is still an error)                          */
     unsigned long long seed;  /* key of every counter-based random draw                */
     int precision;            /* KG_FP64 or KG_MIXED                                    */
     int flags;                /* KG_FLAG_*                                              */
@@ -205,6 +210,7 @@ kg_status kg_schedule_paper(double kappa, int chain_len, double dt, double scale
 
 void kg_destroy(kg_ctx *c);
 const char *kg_strerror(kg_status s);
+
 
 #ifdef __cplusplus
 }

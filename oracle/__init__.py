@@ -41,7 +41,7 @@ class Params(C.Structure):
                 ("kappa", C.c_double), ("n_exp", C.c_double), ("k_fene", C.c_double),
                 ("R0", C.c_double), ("T", C.c_double), ("gamma", C.c_double),
                 ("dt", C.c_double), ("db_bond_max", C.c_double), ("seed", C.c_ulonglong),
-                ("stream", C.c_uint), ("paper_metropolis", C.c_int)]
+                ("stream", C.c_uint), ("paper_metropolis", C.c_int), ("fene_qmin", C.c_double)]
 
 
 def lib():
@@ -52,6 +52,7 @@ def lib():
         sig = {
             "orc_rc": (d, []), "orc_mlj_u": (d, [d, d]), "orc_mlj_du": (d, [d, d]),
             "orc_kn": (d, [d, d, d]), "orc_fene_u": (d, [d, d, d]), "orc_fene_du": (d, [d, d, d]),
+            "orc_fene_reg_u": (d, [d, d, d, d]), "orc_fene_reg_du": (d, [d, d, d, d]),
             "orc_philox4x32_10": (None, [p, p, p]),
             "orc_gauss3": (None, [C.c_ulonglong, C.c_uint, ll, C.c_uint, p]),
             "orc_nlist": (ll, [p, p, d, i, p, p, ll]),
@@ -76,12 +77,13 @@ def _ptr(a: np.ndarray):
 
 def params(n_chains, chain_len, box, kappa, n_exp=12.0, k_fene=None, R0=1.5, T=1.0,
            gamma=1.0, dt=0.01, db_bond_max=1.3, seed=0, stream=0, paper_metropolis=False,
-           l0=0.960897) -> Params:
+           l0=0.960897, fene_qmin=0.0) -> Params:
     if k_fene is None:
         k_fene = kn(n_exp, R0, l0)
     return Params(int(n_chains), int(chain_len), float(box), float(kappa), float(n_exp),
                   float(k_fene), float(R0), float(T), float(gamma), float(dt),
-                  float(db_bond_max), int(seed), int(stream), int(bool(paper_metropolis)))
+                  float(db_bond_max), int(seed), int(stream), int(bool(paper_metropolis)),
+                  float(fene_qmin))
 
 
 class OracleError(RuntimeError):
@@ -118,6 +120,14 @@ def fene_u(k, R0, r):
 
 def fene_du(k, R0, r):
     return lib().orc_fene_du(float(k), float(R0), float(r))
+
+
+def fene_reg_u(k, R0, qmin, r):
+    return lib().orc_fene_reg_u(float(k), float(R0), float(qmin), float(r))
+
+
+def fene_reg_du(k, R0, qmin, r):
+    return lib().orc_fene_reg_du(float(k), float(R0), float(qmin), float(r))
 
 
 def philox4x32_10(ctr, key):

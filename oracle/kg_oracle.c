@@ -62,6 +62,27 @@ double orc_fene_du(double k, double R0, double r)
     return k * r / (1.0 - (r / R0) * (r / R0));
 }
 
+/* READING: Eq. 3 is singular at r = R0 and the paper's engine (LAMMPS) does
+ * not stop there, it limits the force near R0.  With qmin > 0 the log term is
+ * kept for q = 1 - (r/R0)^2 >= qmin and continued beyond r* = R0 sqrt(1 - qmin)
+ * by the quadratic in r^2 that matches its value and slope at r*:
+ *     U = -(k R0^2 / 2) ln(qmin) + k (r^2 - r*^2) / (2 qmin).
+ * qmin = 0 is Eq. 3 unchanged. */
+double orc_fene_reg_u(double k, double R0, double qmin, double r)
+{
+    double q = 1.0 - (r / R0) * (r / R0);
+    if (qmin <= 0.0 || q >= qmin) return orc_fene_u(k, R0, r);
+    double rs2 = (1.0 - qmin) * R0 * R0;
+    return -0.5 * k * R0 * R0 * log(qmin) + k * (r * r - rs2) / (2.0 * qmin);
+}
+
+double orc_fene_reg_du(double k, double R0, double qmin, double r)
+{
+    double q = 1.0 - (r / R0) * (r / R0);
+    if (qmin <= 0.0 || q >= qmin) return orc_fene_du(k, R0, r);
+    return k * r / qmin;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from its       */
 /* published definition: 10 rounds of two 32x32->64 multiplies with the      */
@@ -295,9 +316,9 @@ int orc_forces(const orc_params *p, const double *x, double *F, double *e)
             double d[3] = {min_image(x[t] - x[s], L), min_image(x[M + t] - x[M + s], L),
                            min_image(x[2 * M + t] - x[2 * M + s], L)};
             double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            if (!(r < p->R0)) return ORC_OVERSTRETCH;
-            double du = orc_mlj_du(n, r) + orc_fene_du(p->k_fene, p->R0, r);
-            ebond += orc_mlj_u(n, r) + orc_fene_u(p->k_fene, p->R0, r);
+            if (p->fene_qmin <= 0.0 ? !(r < p->R0) : !(r < 2.0 * p->R0)) return ORC_OVERSTRETCH;
+            double du = orc_mlj_du(n, r) + orc_fene_reg_du(p->k_fene, p->R0, p->fene_qmin, r);
+            ebond += orc_mlj_u(n, r) + orc_fene_reg_u(p->k_fene, p->R0, p->fene_qmin, r);
             vir += -du * r;
             add_central(F, M, s, t, d, r, du);
         }
@@ -524,7 +545,7 @@ static double chain_topo_energy(const orc_params *p, const double *x, int c)
     double L = p->box, E = 0.0;
     for (int i = 0; i + 1 < N; ++i) {
         int s = c * N + i;
-        E += orc_fene_u(p->k_fene, p->R0, sqrt(dist2(x, M, L, s, s + 1)));
+        E += orc_fene_reg_u(p->k_fene, p->R0, p->fene_qmin, sqrt(dist2(x, M, L, s, s + 1)));
     }
     for (int i = 1; i + 1 < N; ++i) {
         int a = c * N + i - 1;

@@ -36,6 +36,9 @@ typedef struct {
     unsigned long long seed; /* Philox key                                  */
     unsigned int stream;     /* melt index: selects an independent stream  */
     int paper_metropolis;    /* 1: acceptance without the proposal ratio   */
+    double fene_qmin;        /* 0: Eq. 3 as printed (r >= R0 is an error);
+                                > 0: C1 harmonic continuation beyond
+                                r* = R0 sqrt(1 - fene_qmin)               */
 } orc_params;
 
 /* status codes */
@@ -52,6 +55,8 @@ double orc_mlj_du(double n, double r);                /* dU/dr               */
 double orc_kn(double n, double R0, double l0);        /* Eq. 9               */
 double orc_fene_u(double k, double R0, double r);     /* log term of Eq. 10  */
 double orc_fene_du(double k, double R0, double r);
+double orc_fene_reg_u(double k, double R0, double qmin, double r);   /* regularised */
+double orc_fene_reg_du(double k, double R0, double qmin, double r);
 
 /* ---- counter-based RNG ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -78,6 +78,10 @@ StageDev make_stage(const kg_params &p, const kg_stage &s)
     d.c2 = 2.0 * n / (n - 6.0);
     d.kfene = s.k_fene < 0 ? kn_of(n, p.R0, p.l0) : s.k_fene;
     d.R0sq = p.R0 * p.R0;
+    d.qmin = p.fene_qmin > 0 ? p.fene_qmin : 0.0;
+    d.r2star = (1.0 - d.qmin) * d.R0sq;
+    d.ustar = d.qmin > 0 ? -0.5 * d.kfene * d.R0sq * std::log(d.qmin) : 0.0;
+    d.qminf = (float)d.qmin; d.r2starf = (float)d.r2star; d.ustarf = (float)d.ustar;
     d.dt = s.dt;
     d.gamma = p.gamma;
     d.T = p.T;
@@ -199,7 +203,8 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     if (!out || !p || p->n_melts < 1 || p->n_melts > kg::MAX_MELTS || !p->melts) return KG_ERR_INVALID_ARG;
     if (p->precision != KG_FP64 && p->precision != KG_MIXED) return KG_ERR_INVALID_ARG;
     if (!(p->T > 0) || p->gamma < 0 || !(p->R0 > RC) || !(p->l0 > 0) || !(p->db_bond_max > 0) ||
-        p->db_bond_max >= p->R0)
+        p->db_bond_max >= p->R0 || p->fene_qmin < 0 || p->fene_qmin >= 0.25 ||
+        p->db_bond_max * p->db_bond_max > (1.0 - p->fene_qmin) * p->R0 * p->R0)
         return KG_ERR_INVALID_ARG;
     *out = nullptr;
     {   // every melt: chains of >= 3 monomers in a box that holds the cell grids
@@ -386,6 +391,8 @@ kg_status kg_load_config(kg_ctx *c, int melt, const double *x, const double *v, 
     if (pid) KG_TRY(cudaMemcpyAsync(c->pid + md.off, pid, Mm * sizeof(int), cudaMemcpyDefault, c->stream));
     else k_iota<<<(int)((Mm + 255) / 256), 256, 0, c->stream>>>(c->pid + md.off, (int)Mm, 0);
     KG_TRY(cudaMemsetAsync(c->flags, 0, 16 * sizeof(unsigned), c->stream));
+    // a rebuild cut short by an earlier error may have left cell counts behind
+    KG_TRY(cudaMemsetAsync(c->ccount, 0, sizeof(int) * (size_t)c->ncell_md, c->stream));
     if ((s = set_rebuild(c)) != KG_OK) return s;
     KG_TRY(cudaStreamSynchronize(c->stream));
     c->latched = KG_OK;

@@ -46,7 +46,7 @@ struct DBC {
     const int *__restrict__ list;
     MeltDev md;
     int melt;
-    double lim2, kfene, R0, T;
+    double lim2, kfene, R0, T, qmin;
 };
 
 // topology views: slot -> monomer (pre-sweep slot) and monomer -> slot
@@ -103,8 +103,9 @@ __device__ int count_partners(const DBC &C, const V &v, int c, int b, Cand *out)
         for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
                 const int cell = md.dbcell_off + (((cz + dz + n) % n) * n + (cy + dy + n) % n) * n + (cx + dx + n) % n;
-                const int e = C.start[cell + 1];
-                for (int k = C.start[cell]; k < e; ++k) {
+                const int b0 = C.start[cell], e = C.start[cell + 1];
+                if (e - b0 > MAX_CELL_OCC) return -1;                  // caller reports capacity
+                for (int k = b0; k < e; ++k) {
                     const int t = C.list[k];
                     const int ts = v.cur(t), r = ts - md.off, d = r / N, i = r - d * N;
                     if (d == c) continue;
@@ -133,7 +134,10 @@ __device__ double bond_fene(const DBC &C, const V &v, int chain, int idx)
 {
     const int s = C.md.off + chain * C.md.N + idx;
     const double r = sqrt(d2(C, v.occ(s), v.occ(s + 1)));
-    return -0.5 * C.kfene * C.R0 * C.R0 * log(1.0 - (r / C.R0) * (r / C.R0));
+    const double q = 1.0 - (r / C.R0) * (r / C.R0);
+    if (C.qmin > 0.0 && q < C.qmin)           // continuation beyond r* (kg_params.fene_qmin)
+        return -0.5 * C.kfene * C.R0 * C.R0 * log(C.qmin) + C.kfene * (r * r - (1.0 - C.qmin) * C.R0 * C.R0) / (2.0 * C.qmin);
+    return -0.5 * C.kfene * C.R0 * C.R0 * log(q);
 }
 
 template <class V>
@@ -179,7 +183,7 @@ __device__ Attempt evaluate(const DBC &C, const V &v, unsigned long long seed, l
     Cand list[CAND_CAP];
     const int n1 = count_partners(C, v, c, b, list);
     if (n1 == 0) return a;
-    if (n1 > CAND_CAP) { err |= ERR_DB_CAPACITY; return a; }
+    if (n1 < 0 || n1 > CAND_CAP) { err |= ERR_DB_CAPACITY; return a; }
     for (int i = 1; i < n1; ++i) {                      // order by (key, key2)
         const Cand t = list[i];
         int j = i - 1;
@@ -195,6 +199,7 @@ __device__ Attempt evaluate(const DBC &C, const V &v, unsigned long long seed, l
     a.jp[2] = v.occ(off + m.d * N + m.q);
     a.jp[3] = v.occ(off + m.d * N + m.q + 1);
     const int n2 = count_partners(C, v, m.d, m.q, (Cand *)nullptr);
+    if (n2 <= 0) { err |= n2 < 0 ? ERR_DB_CAPACITY : ERR_DB_INTERNAL; a.flags = 1; return a; }
     const int A = c < m.d ? c : m.d, B = c < m.d ? m.d : c;
     const int pA = A == c ? b : m.q, pB = A == c ? m.q : b;
     a.kind = m.kind; a.A = A; a.B = B; a.pA = pA; a.pB = pB;
@@ -204,7 +209,7 @@ __device__ Attempt evaluate(const DBC &C, const V &v, unsigned long long seed, l
     dE -= bend(C, v, A, pA) + bend(C, v, A, pA + 1) + bend(C, v, B, pB) + bend(C, v, B, pB + 1);
     const int r1 = count_partners(C, w, A, pA, (Cand *)nullptr);
     const int rr2 = count_partners(C, w, B, pB, (Cand *)nullptr);
-    if (r1 == 0 || rr2 == 0) { err |= ERR_DB_INTERNAL; a.flags = 1; return a; }
+    if (r1 <= 0 || rr2 <= 0) { err |= (r1 < 0 || rr2 < 0) ? ERR_DB_CAPACITY : ERR_DB_INTERNAL; a.flags = 1; return a; }
     const double ratio = (1.0 / r1 + 1.0 / rr2) / (1.0 / n1 + 1.0 / n2);
     double acc = exp(-dE / C.T);
     if (!paper) acc *= ratio;
@@ -218,7 +223,7 @@ __device__ __forceinline__ DBC make_dbc(const SimDev &S, const StageDev &st, int
 {
     DBC C;
     C.x = x; C.Mp = S.Mp; C.pid = pid; C.cell = cell; C.start = start; C.list = list;
-    C.md = S.melt[m]; C.melt = m; C.lim2 = S.db_lim2; C.kfene = st.kfene; C.R0 = sqrt(st.R0sq); C.T = T;
+    C.md = S.melt[m]; C.melt = m; C.lim2 = S.db_lim2; C.kfene = st.kfene; C.R0 = sqrt(st.R0sq); C.T = T; C.qmin = st.qmin;
     return C;
 }
 
@@ -228,6 +233,7 @@ __global__ void __launch_bounds__(128) k_db_eval(const SimDev *__restrict__ Sp, 
                                                 const int *__restrict__ list, const int *__restrict__ koff,
                                                 Attempt *__restrict__ att, long long sweep, unsigned *flags)
 {
+    if (flags[0]) return;                          // a latched error stops the sweep
     const SimDev &S = *Sp;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= koff[S.n_melts]) return;
@@ -267,6 +273,10 @@ __global__ void __launch_bounds__(256) k_db_commit(const SimDev *__restrict__ Sp
     __shared__ long long n_acc, n_empty, n_re;
     const SimDev &S = *Sp;
     const int m = blockIdx.x;
+    if (flags[0]) {                                // a latched error stops the sweep
+        if (threadIdx.x == 0) for (int k = 0; k < 4; ++k) stats[4 * m + k] = 0;
+        return;
+    }
     const MeltDev &md = S.melt[m];
     const int N = md.N, off = md.off, Mp = S.Mp, tid = threadIdx.x;
     const DBC C = make_dbc(S, *stp, m, x, pid, cell, start, list, stp->T);

@@ -60,7 +60,7 @@ struct kg_ctx {
 
     // scratch
     double *scratch = nullptr;   // [3][Mp] doubles + [3][Mp] + [Mp] ints (gather / staging)
-    unsigned *flags = nullptr;   // [0] error bits, [1] rebuild request, [2] rebuild active, [3] max list length
+    unsigned *flags = nullptr;   // [0] error bits, [1] rebuild request, [3] max list length, [4] blocks done
     double *partials = nullptr;  // block partial sums for observables
     int partials_cap = 0;
     double *r2tmp = nullptr;     // per-chain <R^2(n)> partial sums

@@ -21,6 +21,7 @@ namespace kg {
 constexpr int MAX_MELTS = 64;
 constexpr int CODE_BITS = 10;           // cells per axis on the code grid <= 1024
 constexpr int CODE_MASK = (1 << CODE_BITS) - 1;
+constexpr int MAX_CELL_OCC = 1024;      // a cell holding more monomers is reported, never scanned
 
 // device error / status word bits
 enum : unsigned {
@@ -52,8 +53,9 @@ struct MeltDev {
 struct StageDev {
     double n, c1, c2;        // U_MLJ^n(r) = c1 r^-n - c2 r^-6 + 1  (r < r_c)
     double kfene, R0sq;      // FENE: -k R0^2/2 ln(1 - r^2/R0^2)
+    double qmin, r2star, ustar;  // continuation beyond r*^2 = (1 - qmin) R0^2 (qmin > 0)
     double dt, gamma, T, amp;  // amp = sqrt(2 gamma T / dt)
-    float nf, c1f, c2f, kfenef, R0sqf, dtf, gammaf, ampf;
+    float nf, c1f, c2f, kfenef, R0sqf, dtf, gammaf, ampf, qminf, r2starf, ustarf;
     int nkind;               // 0: general n, 1: integer n, 2: n = 5.75, 3: n = 6.5
     int nint;
 };

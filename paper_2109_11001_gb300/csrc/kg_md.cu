@@ -76,11 +76,13 @@ template <typename T3> __device__ __forceinline__ T3 sub3(T3 a, T3 b) { return T
 template <typename T> __device__ __forceinline__ T st_c(const StageDev &st, int which);
 template <> __device__ __forceinline__ float st_c<float>(const StageDev &st, int w)
 {
-    return w == 0 ? st.kfenef : w == 1 ? st.R0sqf : w == 2 ? st.dtf : w == 3 ? st.gammaf : st.ampf;
+    return w == 0 ? st.kfenef : w == 1 ? st.R0sqf : w == 2 ? st.dtf : w == 3 ? st.gammaf : w == 4 ? st.ampf
+         : w == 5 ? st.qminf : w == 6 ? st.r2starf : st.ustarf;
 }
 template <> __device__ __forceinline__ double st_c<double>(const StageDev &st, int w)
 {
-    return w == 0 ? st.kfene : w == 1 ? st.R0sq : w == 2 ? st.dt : w == 3 ? st.gamma : st.amp;
+    return w == 0 ? st.kfene : w == 1 ? st.R0sq : w == 2 ? st.dt : w == 3 ? st.gamma : w == 4 ? st.amp
+         : w == 5 ? st.qmin : w == 6 ? st.r2star : st.ustar;
 }
 
 __device__ __forceinline__ float flog(float a) { return logf(a); }
@@ -164,14 +166,23 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
         if ((side == 0 && i >= 1) || (side == 1 && i <= N - 2)) {
             const T3 d = side == 0 ? rm1 : rp1;
             const T r2 = dot3(d, d);
-            if (!(r2 < R0sq)) err |= ERR_OVERSTRETCH;
-            const T q = (T)1 - r2 / R0sq;
-            T fr = kf / q;
+            const T qmin = st_c<T>(st, 5);
+            T q = (T)1 - r2 / R0sq, fr, Uf = 0;
+            if (qmin > (T)0 && q < qmin) {           // continuation beyond r* (kg_params.fene_qmin)
+                fr = kf / qmin;
+                if (!(r2 < (T)4 * R0sq)) err |= ERR_OVERSTRETCH;
+                if (ENERGY) Uf = st_c<T>(st, 7) + kf * (r2 - st_c<T>(st, 6)) / ((T)2 * qmin);
+            } else {
+                if (!(r2 < R0sq)) err |= ERR_OVERSTRETCH;
+                q = fmax(q, (T)1e-6);                    // finite even when flagged
+                fr = kf / q;
+                if (ENERGY) Uf = (T)-0.5 * kf * R0sq * flog(q);
+            }
             T U = 0;
             if (r2 < rc2) fr += mlj_fr<ENERGY>(st, r2, U);
             F.x += fr * d.x; F.y += fr * d.y; F.z += fr * d.z;
             if (ENERGY) {
-                e[1] += 0.5 * ((double)U - 0.5 * (double)kf * (double)R0sq * (double)flog(q));
+                e[1] += 0.5 * ((double)U + (double)Uf);
                 e[3] -= 0.5 * (double)(fr * r2);
             }
         }
@@ -214,6 +225,7 @@ __global__ void __launch_bounds__(128) k_step_mixed(const SimDev *__restrict__ S
                                                    const int *__restrict__ nn, unsigned *__restrict__ flags,
                                                    long long step)
 {
+    if (flags[0]) return;                  // a latched error stops the run
     const SimDev &S = *Sp;
     const StageDev &st = *stp;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -253,6 +265,7 @@ __global__ void __launch_bounds__(128) k_step_f64(const SimDev *__restrict__ Sp,
                                                  const int *__restrict__ nn, unsigned *__restrict__ flags,
                                                  long long step)
 {
+    if (flags[0]) return;                  // a latched error stops the run
     const SimDev &S = *Sp;
     const StageDev &st = *stp;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -285,14 +298,9 @@ __global__ void __launch_bounds__(128) k_step_f64(const SimDev *__restrict__ Sp,
 }
 
 // ---------------------------------------------------------------------------
-// rebuild chain (each kernel returns at once unless flags[2] is set)
+// rebuild chain: each kernel returns at once unless flags[1] requests a
+// rebuild; the last block of k_nlist to finish clears the request
 // ---------------------------------------------------------------------------
-__global__ void k_rebuild_begin(unsigned *flags)
-{
-    flags[2] = flags[1];
-    flags[1] = 0u;
-}
-
 __device__ __forceinline__ long long floor_ll(double v) { return (long long)floor(v); }
 
 // records on the code grid, gather buffer reset, Verlet-grid cell + rank
@@ -300,14 +308,18 @@ __global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, c
                                                float4 *__restrict__ recb, float4 *__restrict__ dcur,
                                                double4_32a *__restrict__ pcur, double4_32a *__restrict__ xb,
                                                int *__restrict__ cellid, int *__restrict__ rank,
-                                               int *__restrict__ count, const unsigned *__restrict__ flags)
+                                               int *__restrict__ count, unsigned *__restrict__ flags)
 {
-    if (!flags[2]) return;
+    if (!flags[1] || flags[0]) return;
     const SimDev &S = *Sp;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S.M) return;
     const MeltDev &md = S.melt[melt_of(S, s)];
     const int Mp = S.Mp;
+    if (!isfinite(x[s] + x[Mp + s] + x[2 * Mp + s])) {   // never bin a non-finite position
+        atomicOr((unsigned *)flags, ERR_NONFINITE);
+        return;
+    }
     float off[3];
     int code[3], cell[3];
     double xs[3];
@@ -362,7 +374,7 @@ __global__ void __launch_bounds__(256) k_bin_db(const SimDev *__restrict__ Sp, c
 __global__ void __launch_bounds__(1024) k_scan1(const int *__restrict__ in, int *__restrict__ out,
                                                int *__restrict__ bsum, int n, const unsigned *__restrict__ flags)
 {
-    if (flags && !flags[2]) return;
+    if (flags && (!flags[1] || flags[0])) return;
     __shared__ int wsum[32];
     const int i = blockIdx.x * 1024 + threadIdx.x;
     const int v = i < n ? in[i] : 0;
@@ -394,7 +406,7 @@ __global__ void __launch_bounds__(1024) k_scan1(const int *__restrict__ in, int 
 __global__ void __launch_bounds__(1024) k_scan2(int *__restrict__ out, const int *__restrict__ bsum, int n,
                                                int nblk, const unsigned *__restrict__ flags)
 {
-    if (flags && !flags[2]) return;
+    if (flags && (!flags[1] || flags[0])) return;
     __shared__ int off_s;
     if (threadIdx.x < 32) {
         int acc = 0;
@@ -417,27 +429,30 @@ __global__ void __launch_bounds__(256) k_scatter(const int *__restrict__ cellid,
                                                 const int *__restrict__ start, int *__restrict__ list, int M,
                                                 const unsigned *__restrict__ flags)
 {
-    if (flags && !flags[2]) return;
+    if (flags && (!flags[1] || flags[0])) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < M) list[start[cellid[s]] + rank[s]] = s;
 }
 
 // within-cell order by slot (deterministic lists), then clear the counts
 __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start, int *__restrict__ list,
-                                                 int *__restrict__ count, int ncell,
-                                                 const unsigned *__restrict__ flags)
+                                                 int *__restrict__ count, int ncell, unsigned *__restrict__ flags)
 {
-    if (!flags[2]) return;
+    if (!flags[1] || flags[0]) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     const int a = start[c], b = start[c + 1];
+    count[c] = 0;
+    if (b - a > MAX_CELL_OCC) {                    // bounded work: an over-full cell is an error
+        atomicOr(flags, ERR_NL_CAPACITY);
+        return;
+    }
     for (int k = a + 1; k < b; ++k) {
         const int v = list[k];
         int j = k - 1;
         while (j >= a && list[j] > v) { list[j + 1] = list[j]; --j; }
         list[j + 1] = v;
     }
-    count[c] = 0;
 }
 
 // Verlet list: all t != s, not 1-2 bonded, with r^2 < (r_c + skin)^2.  The
@@ -445,16 +460,12 @@ __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start,
 // width 1e-5 around the cutoff (its error is below 2e-6); pairs inside the band
 // are decided by the binary64 distance evaluated exactly as
 // ((dx*dx + dy*dy) + dz*dz), dx = d - L rint(d/L).
-__global__ void __launch_bounds__(128) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
-                                              const float4 *__restrict__ recb, const int *__restrict__ cellid,
-                                              const int *__restrict__ start, const int *__restrict__ list,
-                                              int *__restrict__ nl, int *__restrict__ nn,
-                                              unsigned *__restrict__ flags)
+__device__ __forceinline__ void nlist_row(const SimDev &S, const double *__restrict__ x,
+                                          const float4 *__restrict__ recb, const int *__restrict__ cellid,
+                                          const int *__restrict__ start, const int *__restrict__ list,
+                                          int *__restrict__ nl, int *__restrict__ nn, unsigned *__restrict__ flags,
+                                          int s)
 {
-    if (!flags[2]) return;
-    const SimDev &S = *Sp;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S.M) return;
     const MeltDev &md = S.melt[melt_of(S, s)];
     const int N = md.N, chain = (s - md.off) / N;
     const float4 bi = __ldg(recb + s);
@@ -469,8 +480,12 @@ __global__ void __launch_bounds__(128) k_nlist(const SimDev *__restrict__ Sp, co
             for (int dx = -1; dx <= 1; ++dx) {
                 const int xx = (cx + dx + nc) % nc;
                 const int cell = md.cell_off + (zz * nc + yy) * nc + xx;
-                const int e = start[cell + 1];
-                for (int k = start[cell]; k < e; ++k) {
+                const int b0 = start[cell], e = start[cell + 1];
+                if (e - b0 > MAX_CELL_OCC) {
+                    atomicOr(flags, ERR_NL_CAPACITY);
+                    continue;
+                }
+                for (int k = b0; k < e; ++k) {
                     const int t = list[k];
                     if (t == s) continue;
                     if ((t == s + 1 || t == s - 1) && (t - md.off) / N == chain) continue;
@@ -492,6 +507,26 @@ __global__ void __launch_bounds__(128) k_nlist(const SimDev *__restrict__ Sp, co
     if (cnt > S.maxnb) {
         atomicOr(flags, ERR_NL_CAPACITY);
         atomicMax(flags + 3, (unsigned)cnt);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
+                                              const float4 *__restrict__ recb, const int *__restrict__ cellid,
+                                              const int *__restrict__ start, const int *__restrict__ list,
+                                              int *__restrict__ nl, int *__restrict__ nn,
+                                              unsigned *__restrict__ flags)
+{
+    if (!flags[1] || flags[0]) return;
+    const SimDev &S = *Sp;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S.M) nlist_row(S, x, recb, cellid, start, list, nl, nn, flags, s);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(flags + 4, 1u) == gridDim.x - 1) {
+            flags[1] = 0u;
+            flags[4] = 0u;
+        }
     }
 }
 
@@ -558,8 +593,7 @@ static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 void rebuild_md(kg_ctx *c)
 {
     cudaStream_t st = c->stream;
-    c->launches += 7;
-    k_rebuild_begin<<<1, 1, 0, st>>>(c->flags);
+    c->launches += 6;
     const bool mixed = c->precision == KG_MIXED;
     k_bin_md<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->recb, mixed ? c->dlt[c->cur] : nullptr,
                                               mixed ? nullptr : c->pos64[c->cur], c->xb, c->cellid, c->rank,

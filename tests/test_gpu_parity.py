@@ -248,3 +248,30 @@ def test_full_size_80k(kg):
     xo, uo, pido = m.x.copy(), m.v.copy(), np.arange(m.M, dtype=np.int32)
     _, _, acc = O.db_sweep(q, xo, uo, pido, 0, 800)
     assert st.accepted == acc and np.array_equal(pid, pido)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-5)])
+def test_regularised_fene_forces(kg, precision, tol):
+    # a few bonds pulled past r* = R0 sqrt(1 - qmin) and past R0 itself
+    m = KI.random_walk_melt(20, 30, 0.85, 1.0, 81)
+    x = m.x.copy()
+    for c, f in ((0, 1.55), (3, 1.62), (7, 1.495)):
+        s = c * 30 + 10
+        b = x[:, s + 1] - x[:, s]
+        x[:, s + 1:(c + 1) * 30] += (f / np.linalg.norm(b) - 1.0) * b[:, None]
+    import torch
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=precision, seed=11,
+                       fene_qmin=0.01)
+    ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+    try:
+        kg.kg_set_potential_schedule(ctx, [kg.stage(2.0, 10, 0.002)])
+        kg.kg_load_config(ctx, 0, x, m.v)
+        F = np.zeros_like(x)
+        e4 = np.zeros(4)
+        kg.kg_forces(ctx, 0, F, e4)
+    finally:
+        kg.kg_destroy(ctx)
+    q = oparams(m, 2.0, fene_qmin=0.01)
+    Fo, eo = O.forces(q, x)
+    assert _force_err(F, Fo) < tol
+    assert e4[1] == pytest.approx(eo[1], rel=1e-9 if precision == 0 else 1e-5)

@@ -133,3 +133,30 @@ def test_overstretched_bond_is_an_error():
     p = O.params(1, 2, 20.0, 0.0, n_exp=2.0)
     with pytest.raises(O.OracleError):
         O.forces(p, x)
+
+
+@pytest.mark.parametrize("qmin", [0.01, 0.1])
+def test_regularised_fene(qmin):
+    # equals Eq. 3 below r* = R0 sqrt(1 - qmin); value and slope continuous at r*;
+    # harmonic beyond (second derivative k/qmin in r^2); finite past R0
+    k, R0 = 2.25, 1.5
+    rs = R0 * (1 - qmin) ** 0.5
+    for r in np.linspace(0.5, rs * 0.999, 9):
+        assert O.fene_reg_u(k, R0, qmin, r) == O.fene_u(k, R0, r)
+        assert O.fene_reg_du(k, R0, qmin, r) == O.fene_du(k, R0, r)
+    e = 1e-10
+    assert O.fene_reg_u(k, R0, qmin, rs + e) == pytest.approx(O.fene_u(k, R0, rs - e), rel=1e-6)
+    assert O.fene_reg_du(k, R0, qmin, rs + e) == pytest.approx(O.fene_du(k, R0, rs - e), rel=1e-5)
+    for r in (rs + 0.01, R0, 1.2 * R0):
+        h = 1e-6
+        fd = (O.fene_reg_u(k, R0, qmin, r + h) - O.fene_reg_u(k, R0, qmin, r - h)) / (2 * h)
+        assert O.fene_reg_du(k, R0, qmin, r) == pytest.approx(fd, rel=1e-6)
+        assert O.fene_reg_du(k, R0, qmin, r) == pytest.approx(k * r / qmin, rel=1e-12)
+    assert O.fene_reg_u(k, R0, 0.0, 1.2) == O.fene_u(k, R0, 1.2)
+
+
+def test_regularised_bond_is_finite_past_R0():
+    x = np.array([[1.0, 2.6], [1.0, 1.0], [1.0, 1.0]])       # bond 1.6 > R0
+    p = O.params(1, 2, 20.0, 0.0, n_exp=2.0, fene_qmin=0.01)
+    F, e = O.forces(p, x)
+    assert np.isfinite(F).all() and F[0, 0] > 0               # pulled back together
