@@ -211,6 +211,34 @@ kg_status kg_schedule_paper(double kappa, int chain_len, double dt, double scale
 void kg_destroy(kg_ctx *c);
 const char *kg_strerror(kg_status s);
 
+/* Largest n_chains * chain_len that kg_r2n_noalloc accepts. */
+#define KG_NOALLOC_MAX_MONOMERS 2097152
+
+/* <R^2(n)> for n = 0..N-1 of chains whose positions already sit in device
+ * memory, computed without allocating anything.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory -- code that runs while another framework owns the whole
+ * device heap, or between steps of a latency-critical loop where a
+ * cudaMalloc/cudaFree (which can synchronise the device) is not acceptable.
+ *
+ *   x        device pointer, (3, stride) binary64 SoA, chain-major slots
+ *            c*N + i in [0, n_chains*chain_len); unwrapped positions
+ *   stride   distance in doubles between the x, y and z rows (>= M)
+ *   out      device pointer to chain_len doubles; out[0] = 0
+ *   stream   cudaStream_t to enqueue on (NULL: the default stream)
+ *
+ * Its per-chain partial sums go to one file-scope device array of
+ * KG_NOALLOC_MAX_MONOMERS doubles (16 MiB), which every GPU that loads the
+ * library holds until the process exits.  Sizes beyond that maximum (or
+ * chains longer than fit one block's shared memory, N > 9685) return
+ * KG_ERR_INVALID_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Calls share the array and overwrite it
+ * completely, so calls that overlap on the GPU (different streams, or devices
+ * sharing nothing but this host code) race: serialise them.  No cudaMalloc,
+ * cudaFree or allocating library routine is called. */
+kg_status kg_r2n_noalloc(const double *x, long long stride, int n_chains, int chain_len, double *out,
+                         void *stream);
 
 #ifdef __cplusplus
 }

@@ -25,7 +25,7 @@ KG_FLAG_PAPER_METROPOLIS = 1
 EXPORTS = ["kg_create", "kg_load_config", "kg_get_config", "kg_set_potential_schedule", "kg_step",
            "kg_db_sweep", "kg_db_sweep_k", "kg_observables", "kg_sync", "kg_get_counters",
            "kg_set_counters", "kg_get_nlist", "kg_forces", "kg_profile", "kg_profile_read", "kg_kn", "kg_schedule_paper", "kg_destroy",
-           "kg_strerror"]
+           "kg_strerror", "kg_r2n_noalloc"]
 
 
 class kg_melt(C.Structure):
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "kg_schedule_paper": (i, [d, i, d, d, C.POINTER(kg_stage)]),
         "kg_destroy": (None, [p]),
         "kg_strerror": (C.c_char_p, [i]),
+        "kg_r2n_noalloc": (i, [p, ll, i, i, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +256,11 @@ def kg_schedule_paper(kappa, chain_len, dt, scale=1.0):
 def kg_destroy(ctx):
     load().kg_destroy(ctx)
     _ALLOCATORS.pop(ctx.value, None)
+
+
+def kg_r2n_noalloc(x, stride, n_chains, chain_len, out, stream=None):
+    return _check(load().kg_r2n_noalloc(ptr(x), int(stride), int(n_chains), int(chain_len), ptr(out), stream),
+                  "kg_r2n_noalloc")
 
 
 def kg_strerror(status):

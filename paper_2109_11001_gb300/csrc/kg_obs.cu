@@ -3,6 +3,8 @@
 // repeated calls give identical results.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "kg_host.h"
 
 namespace kg {
@@ -88,4 +90,62 @@ void hist_eval(kg_ctx *c, int melt, int nbins, int *out_dev)
                                                       nbins, out_dev, out_dev + nbins);
 }
 
+// ---------------------------------------------------------------------------
+// <R^2(n)> without any allocation (kg_r2n_noalloc)
+// ---------------------------------------------------------------------------
+// The per-chain partial sums of k_r2n_chain live in this file-scope array
+// instead of a buffer the caller or the library allocates.  Every GPU that
+// loads the library holds it (KG_NOALLOC_MAX_MONOMERS doubles, 16 MiB) until
+// the process exits.
+static __device__ __align__(256) double g_r2n_scratch[KG_NOALLOC_MAX_MONOMERS];
+
 }  // namespace kg
+
+namespace {
+
+// Device address of g_r2n_scratch, looked up once per device (with that device
+// current): in host code the symbol names a host-side stand-in, not device
+// memory, so it must never be handed to a kernel directly.
+double *scratch_address(int device, kg_status *st)
+{
+    static std::mutex mu;
+    static double *addr[256] = {};
+    static bool done[256] = {};
+    if (device < 0 || device >= 256) { *st = KG_ERR_INVALID_ARG; return nullptr; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, kg::g_r2n_scratch);
+        if (e != cudaSuccess) { *st = KG_ERR_CUDA; return nullptr; }
+        addr[device] = (double *)p;
+        done[device] = true;
+    }
+    *st = KG_OK;
+    return addr[device];
+}
+
+}  // namespace
+
+extern "C" kg_status kg_r2n_noalloc(const double *x, long long stride, int n_chains, int chain_len, double *out,
+                                    void *stream)
+{
+    if (!x || !out || n_chains < 1 || chain_len < 2 || stride < (long long)n_chains * chain_len)
+        return KG_ERR_INVALID_ARG;
+    if ((long long)n_chains * chain_len > KG_NOALLOC_MAX_MONOMERS) return KG_ERR_INVALID_ARG;
+    if ((size_t)3 * chain_len * sizeof(double) > 227 * 1024) return KG_ERR_INVALID_ARG;
+    if (stride >= (1LL << 31)) return KG_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return KG_ERR_CUDA;
+    kg_status st;
+    double *scratch = scratch_address(dev, &st);
+    if (!scratch) return st;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = sizeof(double) * 3 * chain_len;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kg::k_r2n_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return KG_ERR_CUDA;
+    kg::k_r2n_chain<<<n_chains, 256, smem, s>>>(x, (int)stride, 0, chain_len, scratch);
+    kg::k_r2n_reduce<<<(chain_len + 255) / 256, 256, 0, s>>>(scratch, n_chains, chain_len, out);
+    return cudaGetLastError() == cudaSuccess ? KG_OK : KG_ERR_CUDA;
+}
+
