@@ -94,6 +94,8 @@ typedef struct {
                                  matches its value and slope there (finite past R0;
                                  r >= 2 R0 is still an error)                          */
     unsigned long long seed;  /* key of every counter-based random draw                */
+    int sort_interval;        /* MD steps between re-sorts of the per-monomer arrays into
+                                 cell order (<= 0: 200); results do not depend on it    */
     int precision;            /* KG_FP64 or KG_MIXED                                    */
     int flags;                /* KG_FLAG_*                                              */
 } kg_params;

@@ -36,8 +36,8 @@ class kg_params(C.Structure):
     _fields_ = [("n_melts", C.c_int), ("melts", C.POINTER(kg_melt)), ("T", C.c_double),
                 ("gamma", C.c_double), ("R0", C.c_double), ("l0", C.c_double),
                 ("db_bond_max", C.c_double), ("r_mc", C.c_double), ("skin", C.c_double),
-                ("fene_qmin", C.c_double), ("seed", C.c_ulonglong), ("precision", C.c_int),
-                ("flags", C.c_int)]
+                ("fene_qmin", C.c_double), ("seed", C.c_ulonglong), ("sort_interval", C.c_int),
+                ("precision", C.c_int), ("flags", C.c_int)]
 
 
 class kg_stage(C.Structure):
@@ -270,11 +270,11 @@ def kg_strerror(status):
 # ---- convenience: parameter construction ----
 
 def make_params(melts, precision=KG_MIXED, seed=1, T=1.0, gamma=1.0, R0=1.5, l0=0.960897, db_bond_max=1.3,
-                r_mc=1e-3, skin=0.3, flags=0, fene_qmin=0.0):
+                r_mc=1e-3, skin=0.3, flags=0, fene_qmin=0.0, sort_interval=0):
     """melts: iterable of (n_chains, chain_len, box, kappa)."""
     arr = (kg_melt * len(melts))(*[kg_melt(int(a), int(b), float(c), float(d)) for a, b, c, d in melts])
     p = kg_params(len(melts), arr, T, gamma, R0, l0, db_bond_max, r_mc, skin, float(fene_qmin), int(seed),
-                  int(precision), int(flags))
+                  int(sort_interval), int(precision), int(flags))
     p._keep = arr
     return p
 

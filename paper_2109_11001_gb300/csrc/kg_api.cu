@@ -222,6 +222,7 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->melts.assign(p->melts, p->melts + p->n_melts);
     c->p.melts = c->melts.data();
     if (!(c->p.skin > 0)) c->p.skin = 0.3;
+    c->sort_interval = p->sort_interval > 0 ? p->sort_interval : 200;
     c->precision = p->precision;
     if (allocator && allocator->alloc && allocator->free) { c->alloc = *allocator; c->have_alloc = true; }
     auto fail = [&](kg_status s) { kg_destroy(c); return s; };
@@ -251,13 +252,22 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
         md.ndb = (int)std::floor(ml.box / (p->db_bond_max * (1.0 + 1e-9)));
         if (md.nc < 3 || md.ndb < 3) return fail(KG_ERR_INVALID_ARG);
         md.h = ml.box / md.nc; md.invh = 1.0 / md.h;
+        md.nbk = (md.nc + 3) / 4;
+        {   // binary32 wrapped-position prefilter: per-component error <= 4 L 2^-24
+            const double dd = std::sqrt(3.0) * 4.0 * ml.box * std::ldexp(1.0, -24);
+            const double band = 2.0 * (2.0 * rl * dd + dd * dd + 1e-6 * rl * rl);
+            md.nl_lo = (float)(rl * rl - band);
+            md.nl_hi = (float)(rl * rl + band);
+            md.Lf_wrap = (float)ml.box;
+            md.invLf = (float)(1.0 / ml.box);
+        }
         md.ncc = std::max(md.nc, 16);
         if (md.ncc > (1 << kg::CODE_BITS)) return fail(KG_ERR_INVALID_ARG);
         md.hc = ml.box / md.ncc; md.invhc = 1.0 / md.hc; md.hcf = (float)md.hc;
         md.hdb = ml.box / md.ndb; md.invhdb = 1.0 / md.hdb;
         md.cell_off = (int)ncell;
         md.dbcell_off = (int)ndbcell;
-        ncell += (long long)md.nc * md.nc * md.nc;
+        ncell += 64LL * md.nbk * md.nbk * md.nbk;
         ndbcell += (long long)md.ndb * md.ndb * md.ndb;
         M += md.M;
     }
@@ -290,6 +300,8 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->u = A(3 * Mp * ureal);
     c->pid = (int *)A(Mp * sizeof(int));
     c->recb = (float4 *)A(Mp * sizeof(float4));
+    c->recs = (float4 *)A(Mp * sizeof(float4));
+    c->wpos = (float4 *)A(Mp * sizeof(float4));
     if (c->precision == KG_MIXED) {
         c->dlt[0] = (float4 *)A(Mp * sizeof(float4));
         c->dlt[1] = (float4 *)A(Mp * sizeof(float4));
@@ -313,13 +325,15 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->dbstart = (int *)A(((size_t)c->ncell_db + 1) * sizeof(int));
     c->dblist = (int *)A(Mp * sizeof(int));
     c->koff = (int *)A((kg::MAX_MELTS + 1) * sizeof(int));
-    c->occ = (int *)A(Mp * sizeof(int));
-    c->curmap = (int *)A(Mp * sizeof(int));
+    c->slot_of = (int *)A(Mp * sizeof(int));
+    c->comp_of = (int *)A(Mp * sizeof(int));
+    c->bp = (int4 *)A(Mp * sizeof(int4));
     c->img = (int *)A(3 * Mp * sizeof(int));
     c->dirty = (int *)A(Mp * sizeof(int));
     c->db_stats = (long long *)A(4 * kg::MAX_MELTS * sizeof(long long));
     c->scratch = (double *)A(7 * Mp * sizeof(double));
     c->flags = (unsigned *)A(16 * sizeof(unsigned));
+    c->d_step = (long long *)A(sizeof(long long));
     c->fout = (double *)A(3 * Mp * sizeof(double));
     c->partials_cap = (int)(Mp / 128 + 2) * 5;
     c->partials = (double *)A((size_t)c->partials_cap * sizeof(double));
@@ -331,8 +345,9 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     if (cudaMemcpyAsync(c->d_sim, &c->sim, sizeof(SimDev), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return fail(KG_ERR_CUDA);
     const int nb = (int)((Mp + 255) / 256);
-    k_iota<<<nb, 256, 0, c->stream>>>(c->occ, (int)Mp, 0);
-    k_iota<<<nb, 256, 0, c->stream>>>(c->curmap, (int)Mp, 0);
+    k_iota<<<nb, 256, 0, c->stream>>>(c->slot_of, (int)Mp, 0);
+    k_iota<<<nb, 256, 0, c->stream>>>(c->comp_of, (int)Mp, 0);
+    kg::bonded_partners(c);
     kg_stage def{12.0, -1.0, -1, 0.01};
     if (upload_stage(c, def) != KG_OK) return fail(KG_ERR_CUDA);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(KG_ERR_CUDA);
@@ -347,13 +362,18 @@ void kg_destroy(kg_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    void *bufs[] = {c->d_sim, c->d_stage, c->x, c->u, c->pid, c->recb, c->dlt[0], c->dlt[1], c->pos64[0],
+    void *bufs[] = {c->d_sim, c->d_stage, c->x, c->u, c->pid, c->recb, c->recs, c->wpos, c->dlt[0], c->dlt[1], c->pos64[0],
                     c->pos64[1], c->xb, c->cellid, c->rank, c->ccount, c->cstart, c->clist, c->bsum, c->nl,
-                    c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->att, c->koff, c->occ,
-                    c->curmap, c->img, c->dirty, c->db_stats, c->scratch, c->flags, c->fout, c->partials,
+                    c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->att, c->koff, c->slot_of,
+                    c->comp_of, c->bp, c->img, c->dirty, c->db_stats, c->scratch, c->flags, c->fout, c->partials,
                     c->r2tmp, c->hist};
     for (void *b : bufs) dev_free(c, b);
+    dev_free(c, c->d_step);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k)
+        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -390,6 +410,17 @@ kg_status kg_load_config(kg_ctx *c, int melt, const double *x, const double *v, 
     }
     if (pid) KG_TRY(cudaMemcpyAsync(c->pid + md.off, pid, Mm * sizeof(int), cudaMemcpyDefault, c->stream));
     else k_iota<<<(int)((Mm + 255) / 256), 256, 0, c->stream>>>(c->pid + md.off, (int)Mm, 0);
+    // the melt's monomers start in slot order: compute index = slot
+    k_iota<<<(int)((Mm + 255) / 256), 256, 0, c->stream>>>(c->slot_of + md.off, (int)Mm, md.off);
+    k_iota<<<(int)((Mm + 255) / 256), 256, 0, c->stream>>>(c->comp_of + md.off, (int)Mm, md.off);
+    kg::bonded_partners(c);
+    c->clist_valid = false;
+    {   // keep the count of graph-side rebuild kernels across the reset of the status words
+        unsigned f[8];
+        KG_TRY(cudaMemcpyAsync(f, c->flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
+        KG_TRY(cudaStreamSynchronize(c->stream));
+        c->launches += 6LL * (long long)f[6];
+    }
     KG_TRY(cudaMemsetAsync(c->flags, 0, 16 * sizeof(unsigned), c->stream));
     // a rebuild cut short by an earlier error may have left cell counts behind
     KG_TRY(cudaMemsetAsync(c->ccount, 0, sizeof(int) * (size_t)c->ncell_md, c->stream));
@@ -404,21 +435,20 @@ kg_status kg_get_config(kg_ctx *c, int melt, double *x, double *v, int *pid)
     kg_status s = check_melt(c, melt);
     if (s != KG_OK) return s;
     const MeltDev &md = c->sim.melt[melt];
-    const size_t Mm = md.M, Mp = c->Mp;
-    for (int d = 0; d < 3; ++d) {
-        if (x) KG_TRY(cudaMemcpyAsync(x + d * Mm, c->x + d * Mp + md.off, Mm * sizeof(double), cudaMemcpyDefault, c->stream));
-        if (v) {
-            if (c->precision == KG_MIXED) {
-                k_f2d<<<(int)((Mm + 255) / 256), 256, 0, c->stream>>>((const float *)c->u + d * Mp + md.off,
-                                                                      c->scratch + d * Mm, (int)Mm);
-                KG_TRY(cudaMemcpyAsync(v + d * Mm, c->scratch + d * Mm, Mm * sizeof(double), cudaMemcpyDefault, c->stream));
-            } else {
-                KG_TRY(cudaMemcpyAsync(v + d * Mm, (const double *)c->u + d * Mp + md.off, Mm * sizeof(double),
-                                       cudaMemcpyDefault, c->stream));
-            }
-        }
+    const size_t Mm = md.M;
+    if (x) {
+        kg::to_slots(c, melt, c->x, c->scratch, 3);
+        KG_TRY(cudaMemcpyAsync(x, c->scratch, 3 * Mm * sizeof(double), cudaMemcpyDefault, c->stream));
     }
-    if (pid) KG_TRY(cudaMemcpyAsync(pid, c->pid + md.off, Mm * sizeof(int), cudaMemcpyDefault, c->stream));
+    if (v) {
+        kg::u_to_slots(c, melt, c->scratch + 3 * Mm);
+        KG_TRY(cudaMemcpyAsync(v, c->scratch + 3 * Mm, 3 * Mm * sizeof(double), cudaMemcpyDefault, c->stream));
+    }
+    if (pid) {
+        int *tmp = (int *)(c->scratch + 6 * Mm);
+        kg::pid_to_slots(c, melt, tmp);
+        KG_TRY(cudaMemcpyAsync(pid, tmp, Mm * sizeof(int), cudaMemcpyDefault, c->stream));
+    }
     KG_TRY(cudaStreamSynchronize(c->stream));
     return KG_OK;
 }
@@ -451,9 +481,26 @@ kg_status kg_step(kg_ctx *c, long long n_steps)
         }
         long long chunk = n_steps;
         if (c->stage_left > 0) chunk = std::min(chunk, c->stage_left);
-        for (long long i = 0; i < chunk; ++i) {
-            kg::md_step(c, c->step);
-            ++c->step;
+        if (c->d_step_stale) {                  // the device counter holds the last step run
+            kg::set_device_step(c, c->step - 1);
+            c->d_step_stale = false;
+        }
+        long long done = 0;
+        while (done < chunk) {
+            if (c->since_sort >= c->sort_interval && c->clist_valid) {
+                kg::md_sort(c);                 // restore cell order for locality
+                c->since_sort = 0;
+                c->clist_valid = false;
+            }
+            long long n = 1;
+            if (!c->prof_on && c->use_graphs && chunk - done >= kg::GRAPH_STEPS && kg::md_graph_steps(c, 1))
+                n = kg::GRAPH_STEPS;
+            else
+                kg::md_step(c);
+            c->clist_valid = true;              // a Verlet build has run since the last load / sort
+            c->step += n;
+            c->since_sort += n;
+            done += n;
         }
         c->t_since_sweep += chunk * c->stage.dt;
         if (c->stage_left > 0) c->stage_left -= chunk;
@@ -537,6 +584,7 @@ kg_status kg_set_counters(kg_ctx *c, long long step, long long sweep)
     if (!c || step < 0 || sweep < 0) return KG_ERR_INVALID_ARG;
     c->step = step;
     c->sweep = sweep;
+    c->d_step_stale = true;
     return KG_OK;
 }
 
@@ -550,9 +598,10 @@ kg_status kg_forces(kg_ctx *c, int melt, double *F, double *e4)
     kg::forces_eval(c, melt, c->step, c->fout, c->partials, nb);
     const MeltDev &md = c->sim.melt[melt];
     const size_t Mm = md.M, Mp = c->Mp;
-    if (F)
-        for (int d = 0; d < 3; ++d)
-            KG_TRY(cudaMemcpyAsync(F + d * Mm, c->fout + d * Mp + md.off, Mm * sizeof(double), cudaMemcpyDefault, c->stream));
+    if (F) {
+        kg::to_slots(c, melt, c->fout, c->scratch, 3);
+        KG_TRY(cudaMemcpyAsync(F, c->scratch, 3 * Mm * sizeof(double), cudaMemcpyDefault, c->stream));
+    }
     std::vector<double> part((size_t)nb * 5);
     KG_TRY(cudaMemcpyAsync(part.data(), c->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if ((s = read_flags(c, pinned_flags())) != KG_OK) return s;
@@ -632,7 +681,13 @@ kg_status kg_profile_read(kg_ctx *c, double *ms, long long *n, long long *launch
     kg::prof_collect(c);
     if (ms) *ms = c->prof_ms;
     if (n) *n = c->prof_n;
-    if (launches) *launches = c->launches;
+    if (launches) {
+        // inside graphs the six rebuild kernels run only when requested; the
+        // device counts those runs in flags[6]
+        unsigned f[8];
+        if (cudaMemcpy(f, c->flags, sizeof(f), cudaMemcpyDeviceToHost) != cudaSuccess) return KG_ERR_CUDA;
+        *launches = c->launches + 6LL * (long long)f[6];
+    }
     return KG_OK;
 }
 
@@ -646,18 +701,21 @@ kg_status kg_get_nlist(kg_ctx *c, int melt, int *offs, int *nbr, long long cap, 
     kg::rebuild_md(c);
     const MeltDev &md = c->sim.melt[melt];
     const size_t Mm = md.M, Mp = c->Mp;
-    std::vector<int> nn(Mm), nl((size_t)c->maxnb * Mm);
+    std::vector<int> nn(Mm), nl((size_t)c->maxnb * Mm), comp(Mm), slot(Mm);
     KG_TRY(cudaMemcpyAsync(nn.data(), c->nn + md.off, Mm * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    KG_TRY(cudaMemcpyAsync(comp.data(), c->comp_of + md.off, Mm * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    KG_TRY(cudaMemcpyAsync(slot.data(), c->slot_of + md.off, Mm * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     for (int k = 0; k < c->maxnb; ++k)
         KG_TRY(cudaMemcpyAsync(nl.data() + (size_t)k * Mm, c->nl + (size_t)k * Mp + md.off, Mm * sizeof(int),
                                cudaMemcpyDeviceToHost, c->stream));
     if ((s = read_flags(c, pinned_flags())) != KG_OK) return s;
     long long tot = 0;
     std::vector<int> row;
-    for (size_t i = 0; i < Mm; ++i) {
+    for (size_t i = 0; i < Mm; ++i) {          // slot i of the melt
         offs[i] = (int)tot;
         row.clear();
-        for (int k = 0; k < nn[i]; ++k) row.push_back(nl[(size_t)k * Mm + i] - md.off);
+        const size_t j = (size_t)(comp[i] - md.off);
+        for (int k = 0; k < nn[j]; ++k) row.push_back(slot[nl[k * Mm + j] - md.off] - md.off);
         std::sort(row.begin(), row.end());
         if (tot + (long long)row.size() > cap) return KG_ERR_CAPACITY;
         std::copy(row.begin(), row.end(), nbr + tot);

@@ -14,7 +14,9 @@
 //   1. bin every monomer on a grid of >= 1.3 sigma cells (positions do not move
 //      during a sweep: swaps only relabel slots);
 //   2. k_db_eval: every attempt evaluated in parallel against the pre-sweep
-//      topology (one thread each);
+//      topology (one thread each).  A "monomer" here is its compute index; the
+//      topology is the pair of maps slot -> monomer (comp_of) and monomer ->
+//      slot (slot_of);
 //   3. k_db_commit: one block per melt walks the attempts in order.  An attempt
 //      is re-evaluated against the current topology when an earlier accepted
 //      swap in the sweep touched one of its two chains, or put a junction
@@ -22,8 +24,10 @@
 //      neighbourhood it scanned.  Nothing else an evaluation reads can change:
 //      swaps preserve positions, the bonds inside moved segments, and the
 //      lengths of the two pieces on either side of every bond.  Accepted swaps
-//      update slot<->monomer maps and per-monomer box shifts only;
-//   4. k_db_apply / k_db_finish: one gather applies the permutation and shifts.
+//      rewrite the two maps for the slots of their two chains and add box
+//      shifts to a per-monomer counter;
+//   4. k_db_finish: the box shifts are added to the positions in place; no
+//      monomer data moves (the maps are the topology).
 #include <cuda_runtime.h>
 
 #include "kg_host.h"
@@ -49,11 +53,7 @@ struct DBC {
     double lim2, kfene, R0, T, qmin;
 };
 
-// topology views: slot -> monomer (pre-sweep slot) and monomer -> slot
-struct ViewId {
-    __device__ __forceinline__ int occ(int s) const { return s; }
-    __device__ __forceinline__ int cur(int p) const { return p; }
-};
+// topology view: slot -> monomer (occ) and monomer -> slot (cur)
 struct ViewMap {
     const int *o;
     const int *c;
@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(128) k_db_eval(const SimDev *__restrict__ Sp, 
                                                 const double *__restrict__ x, const int *__restrict__ pid,
                                                 const int *__restrict__ cell, const int *__restrict__ start,
                                                 const int *__restrict__ list, const int *__restrict__ koff,
+                                                const int *__restrict__ comp_of, const int *__restrict__ slot_of,
                                                 Attempt *__restrict__ att, long long sweep, unsigned *flags)
 {
     if (flags[0]) return;                          // a latched error stops the sweep
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(128) k_db_eval(const SimDev *__restrict__ Sp, 
     while (g >= koff[m + 1]) ++m;
     const DBC C = make_dbc(S, *stp, m, x, pid, cell, start, list, stp->T);
     unsigned err = 0;
-    att[g] = evaluate(C, ViewId{}, S.seed, sweep, g - koff[m], S.paper_metropolis, err);
+    att[g] = evaluate(C, ViewMap{comp_of, slot_of}, S.seed, sweep, g - koff[m], S.paper_metropolis, err);
     if (err) atomicOr(flags, err);
 }
 
@@ -375,60 +376,37 @@ __global__ void __launch_bounds__(256) k_db_commit(const SimDev *__restrict__ Sp
     }
 }
 
-// gather the permuted state (with box shifts) into scratch
-template <typename U>
-__global__ void __launch_bounds__(256) k_db_apply(const SimDev *__restrict__ Sp, const double *__restrict__ x,
-                                                 const U *__restrict__ u, const int *__restrict__ pid,
-                                                 const int *__restrict__ occ, const int *__restrict__ img,
-                                                 double *__restrict__ sx, U *__restrict__ su, int *__restrict__ spid)
-{
-    const SimDev &S = *Sp;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S.M) return;
-    const double L = S.melt[melt_of(S, s)].L;
-    const int p = occ[s], Mp = S.Mp;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        sx[d * Mp + s] = __dadd_rn(x[d * Mp + p], __dmul_rn(L, (double)img[d * Mp + p]));
-        su[d * Mp + s] = u[d * Mp + p];
-    }
-    spid[s] = pid[p];
-}
-
-template <typename U>
+// end of a sweep: box shifts into the positions (x + L*img, as one rounding of
+// a product and one of a sum), counters cleared
 __global__ void __launch_bounds__(256) k_db_finish(const SimDev *__restrict__ Sp, double *__restrict__ x,
-                                                  U *__restrict__ u, int *__restrict__ pid,
-                                                  int *__restrict__ occ, int *__restrict__ curmap,
-                                                  int *__restrict__ img, int *__restrict__ dirty,
-                                                  const double *__restrict__ sx, const U *__restrict__ su,
-                                                  const int *__restrict__ spid)
+                                                  const int *__restrict__ slot_of, int *__restrict__ img,
+                                                  int *__restrict__ dirty)
 {
     const SimDev &S = *Sp;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S.M) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= S.M) return;
     const int Mp = S.Mp;
+    const double L = S.melt[melt_of(S, slot_of[j])].L;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        x[d * Mp + s] = sx[d * Mp + s];
-        u[d * Mp + s] = su[d * Mp + s];
-        img[d * Mp + s] = 0;
+        const int k = img[d * Mp + j];
+        if (k) x[d * Mp + j] = __dadd_rn(x[d * Mp + j], __dmul_rn(L, (double)k));
+        img[d * Mp + j] = 0;
     }
-    pid[s] = spid[s];
-    occ[s] = s;
-    curmap[s] = s;
-    dirty[s] = 0;
+    dirty[j] = 0;
 }
 
 // kg_md.cu
 __global__ void k_bin_db(const SimDev *__restrict__ Sp, const double *__restrict__ x, int *__restrict__ cellid,
-                         int *__restrict__ rank, int *__restrict__ count);
+                         int *__restrict__ rank, int *__restrict__ count, const int *__restrict__ slot_of);
 __global__ void k_scan1(const int *__restrict__ in, int *__restrict__ out, int *__restrict__ bsum, int n,
                         const unsigned *__restrict__ flags);
 __global__ void k_scan2(int *__restrict__ out, const int *__restrict__ bsum, int n, int nblk,
                         const unsigned *__restrict__ flags);
 __global__ void k_scatter(const int *__restrict__ cellid, const int *__restrict__ rank,
                           const int *__restrict__ start, int *__restrict__ list, int M,
-                          const unsigned *__restrict__ flags);
+                          const unsigned *__restrict__ flags, const float4 *__restrict__ recb,
+                          float4 *__restrict__ recs);
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
@@ -436,46 +414,34 @@ void db_sweep(kg_ctx *c, const std::vector<long long> &K, long long *host_stats)
 {
     cudaStream_t st = c->stream;
     const int nm = c->sim.n_melts;
-    c->launches += 8;
+    c->launches += 7;
     std::vector<int> koff(nm + 1, 0);
     for (int m = 0; m < nm; ++m) koff[m + 1] = koff[m] + (int)K[m];
     cudaMemcpyAsync(c->koff, koff.data(), sizeof(int) * (nm + 1), cudaMemcpyHostToDevice, st);
     // 1. grid of >= 1.3 sigma cells
     cudaMemsetAsync(c->dbcount, 0, sizeof(int) * c->ncell_db, st);
-    k_bin_db<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->dbcell, c->dbrank, c->dbcount);
+    k_bin_db<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->dbcell, c->dbrank, c->dbcount, c->slot_of);
     const int nb = nblk(c->ncell_db, 1024);
     k_scan1<<<nb, 1024, 0, st>>>(c->dbcount, c->dbstart, c->bsum, c->ncell_db, nullptr);
     k_scan2<<<nb, 1024, 0, st>>>(c->dbstart, c->bsum, c->ncell_db, nb, nullptr);
-    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->dbcell, c->dbrank, c->dbstart, c->dblist, c->M, nullptr);
+    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->dbcell, c->dbrank, c->dbstart, c->dblist, c->M, nullptr,
+                                               nullptr, nullptr);
     // 2. speculative evaluation
     Attempt *att = (Attempt *)c->att;
     if (koff[nm] > 0)
         k_db_eval<<<nblk(koff[nm], 128), 128, 0, st>>>(c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart,
-                                                       c->dblist, c->koff, att, c->sweep, c->flags);
+                                                       c->dblist, c->koff, c->comp_of, c->slot_of, att, c->sweep,
+                                                       c->flags);
     // 3. ordered commit, one block per melt
     int maxN = 0;
     for (int m = 0; m < nm; ++m) maxN = maxN > c->sim.melt[m].N ? maxN : c->sim.melt[m].N;
     k_db_commit<<<nm, 256, sizeof(int) * 2 * maxN, st>>>(c->d_sim, c->d_stage, c->x, c->pid, c->dbcell,
-                                                          c->dbstart, c->dblist, c->koff, att, c->occ,
-                                                          c->curmap, c->img, c->dirty, c->db_stats, c->sweep,
+                                                          c->dbstart, c->dblist, c->koff, att, c->comp_of,
+                                                          c->slot_of, c->img, c->dirty, c->db_stats, c->sweep,
                                                           c->flags);
-    // 4. apply the permutation and the box shifts
-    const int Mp = c->Mp;
-    double *sx = c->scratch;
-    int *spid = (int *)(c->scratch + 6 * (size_t)Mp);
-    if (c->precision == KG_MIXED) {
-        float *su = (float *)(c->scratch + 3 * (size_t)Mp);
-        k_db_apply<float><<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, (const float *)c->u, c->pid, c->occ,
-                                                           c->img, sx, su, spid);
-        k_db_finish<float><<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, (float *)c->u, c->pid, c->occ,
-                                                            c->curmap, c->img, c->dirty, sx, su, spid);
-    } else {
-        double *su = c->scratch + 3 * (size_t)Mp;
-        k_db_apply<double><<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, (const double *)c->u, c->pid, c->occ,
-                                                            c->img, sx, su, spid);
-        k_db_finish<double><<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, (double *)c->u, c->pid, c->occ,
-                                                             c->curmap, c->img, c->dirty, sx, su, spid);
-    }
+    // 4. box shifts into the positions; chain partners follow the new maps
+    k_db_finish<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->slot_of, c->img, c->dirty);
+    bonded_partners(c);
     cudaMemcpyAsync(host_stats, c->db_stats, sizeof(long long) * 4 * nm, cudaMemcpyDeviceToHost, st);
 }
 

@@ -35,8 +35,23 @@ struct kg_ctx {
     // state
     double *x = nullptr;         // [3][Mp]
     void *u = nullptr;           // [3][Mp] float or double
-    int *pid = nullptr;
+    int *pid = nullptr;          // particle id of the monomer at each compute index
+    int *slot_of = nullptr;      // compute index -> chain-major slot
+    int *comp_of = nullptr;      // chain-major slot -> compute index
+    int4 *bp = nullptr;          // compute indices of slots s-2, s-1, s+1, s+2 (-1 past a chain end)
+    bool clist_valid = false;    // the last Verlet build's cell order can seed a re-sort
+    long long since_sort = 0;
+    long long *d_step = nullptr;   // device step counter (index of the step being run)
+    bool d_step_stale = true;      // host must write it before the next step
+    cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool graph_failed = false;
+    bool use_graphs = true;
+    long long graph_replays = 0;
+    long long sort_interval = 200;
     float4 *recb = nullptr;
+    float4 *wpos = nullptr;      // wrapped binary32 positions (Verlet-list build)
+    float4 *recs = nullptr;      // the same in cell order
     float4 *dlt[2] = {nullptr, nullptr};
     double4_32a *pos64[2] = {nullptr, nullptr};
     double4_32a *xb = nullptr;
@@ -55,12 +70,13 @@ struct kg_ctx {
     void *att = nullptr;         // kg::Attempt[att_cap]
     long long att_cap = 0;
     int *koff = nullptr;         // [n_melts+1] attempt offsets
-    int *occ = nullptr, *curmap = nullptr, *img = nullptr, *dirty = nullptr;
+    int *img = nullptr, *dirty = nullptr;
     long long *db_stats = nullptr;   // [n_melts][4]
 
     // scratch
     double *scratch = nullptr;   // [3][Mp] doubles + [3][Mp] + [Mp] ints (gather / staging)
-    unsigned *flags = nullptr;   // [0] error bits, [1] rebuild request, [3] max list length, [4] blocks done
+    unsigned *flags = nullptr;   // [0] error bits, [1] rebuild request, [3] max list length, [4] blocks done,
+                                 // [5] Verlet builds, [6] rebuild bodies run inside graphs
     double *partials = nullptr;  // block partial sums for observables
     int partials_cap = 0;
     double *r2tmp = nullptr;     // per-chain <R^2(n)> partial sums
@@ -80,6 +96,8 @@ struct kg_ctx {
 
 namespace kg {
 
+constexpr int GRAPH_STEPS = 10;          // MD steps per captured graph (even)
+
 struct Attempt {
     int flags;                   // 1: non-empty partner set, 2: accepted
     int c, d;                    // chain of the drawn bond, chain of the chosen partner
@@ -89,9 +107,16 @@ struct Attempt {
 
 // kg_md.cu
 void rebuild_md(kg_ctx *c);                  // conditional on flags[1]
-void md_step(kg_ctx *c, long long step);     // one fused force + integrate step
+void md_step(kg_ctx *c);                     // one fused force + integrate step (direct launches)
+bool md_graph_steps(kg_ctx *c, long long nrep);  // nrep replays of a GRAPH_STEPS-step graph
+void set_device_step(kg_ctx *c, long long v);
 void forces_eval(kg_ctx *c, int melt, long long step, double *F_dev, double *part_dev, int nblk);
 void prof_collect(kg_ctx *c);                // fold recorded event pairs into the totals
+void bonded_partners(kg_ctx *c);             // bp from slot_of / comp_of
+void md_sort(kg_ctx *c);                     // re-sort the state into the last cell order
+void to_slots(kg_ctx *c, int melt, const double *in_comp, double *out_dev, int dims);
+void u_to_slots(kg_ctx *c, int melt, double *out_dev);
+void pid_to_slots(kg_ctx *c, int melt, int *out_dev);
 int forces_blocks(const kg_ctx *c, int melt);
 
 // kg_db.cu

@@ -37,9 +37,13 @@ struct MeltDev {
     int off, M, N, n_ch;          // slots [off, off+M): chain c, position i -> off + c*N + i
     double L, invL, kappa;
     float Lf, kappaf;
-    // Verlet-list cell grid (cells >= r_c + skin)
-    int nc, cell_off;
+    // Verlet-list cell grid (cells >= r_c + skin), numbered brick-major
+    // (4x4x4-cell bricks) so that a block of consecutive monomers in cell
+    // order has a compact neighbourhood
+    int nc, nbk, cell_off;
     double h, invh;
+    float nl_lo, nl_hi;      // binary32 prefilter: r^2 < nl_lo in, r^2 >= nl_hi out
+    float Lf_wrap, invLf;
     // code grid of the position records (>= 16 cells per axis)
     int ncc;
     double hc, invhc;
@@ -168,6 +172,21 @@ __device__ __forceinline__ int wrap_dk(int dk, int n)
     if (dk > n / 2) dk -= n;
     else if (dk < -(n / 2)) dk += n;
     return dk;
+}
+
+// Verlet-grid cell index of cell coordinates (cx, cy, cz), brick-major.
+__device__ __forceinline__ int md_cell(const MeltDev &md, int cx, int cy, int cz)
+{
+    return md.cell_off + ((((cz >> 2) * md.nbk + (cy >> 2)) * md.nbk + (cx >> 2)) << 6) +
+           (((cz & 3) << 4) | ((cy & 3) << 2) | (cx & 3));
+}
+
+__device__ __forceinline__ void md_cell_xyz(const MeltDev &md, int cell, int &cx, int &cy, int &cz)
+{
+    const int r = cell - md.cell_off, b = r >> 6, l = r & 63;
+    cx = ((b % md.nbk) << 2) | (l & 3);
+    cy = (((b / md.nbk) % md.nbk) << 2) | ((l >> 2) & 3);
+    cz = ((b / (md.nbk * md.nbk)) << 2) | (l >> 4);
 }
 
 // Minimum-image vector from record i to record j (binary32): the code grid

@@ -5,8 +5,12 @@
 //    U_bond^n bonds (Eq. 10), kappa (1 - cos theta) bending (Eq. 4), Langevin
 //    friction and Philox noise, and the leapfrog update of (x, u);
 //  * a force/energy kernel for observables and parity checks.
-// Thread per slot; slots are chain-major, so a warp walks 32 consecutive
-// monomers of a chain and its neighbour gathers overlap in L1.
+// Thread per monomer in compute order: the per-monomer arrays are kept sorted
+// by Verlet-list cell (re-sorted every few hundred steps), so a warp's
+// neighbours sit in a few contiguous runs of memory.  bp[i] holds the compute
+// indices of the monomers two and one before and after along the chain
+// (-1 past a chain end); slot_of[i] is the chain-major slot c*N + i, which keys
+// the random draws so results do not depend on the order.
 #include <cuda_runtime.h>
 
 #include "kg_host.h"
@@ -133,7 +137,7 @@ struct GeoF64 {
 // e[2] bending (the angle whose vertex is s), e[3] virial (1/2 per pair/bond).
 template <bool ENERGY, class G>
 __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, const StageDev &st,
-                                                   const MeltDev &md, int s, int i,
+                                                   const MeltDev &md, int s, int4 bp,
                                                    const int *__restrict__ nl, int cnt,
                                                    double *e, unsigned &err)
 {
@@ -153,17 +157,18 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
             if (ENERGY) { e[0] += 0.5 * (double)U; e[3] -= 0.5 * (double)(fr * r2); }
         }
     }
-    const int N = md.N;
+    // chain neighbours: bp = (s-2, s-1, s+1, s+2) along the chain, -1 past an end
+    const bool hm2 = bp.x >= 0, hm1 = bp.y >= 0, hp1 = bp.z >= 0, hp2 = bp.w >= 0;
     T3 rm2 = mk<T>(0, 0, 0), rm1 = mk<T>(0, 0, 0), rp1 = mk<T>(0, 0, 0), rp2 = mk<T>(0, 0, 0);
-    if (i >= 1) rm1 = g.rel(s - 1);
-    if (i >= 2) rm2 = g.rel(s - 2);
-    if (i <= N - 2) rp1 = g.rel(s + 1);
-    if (i <= N - 3) rp2 = g.rel(s + 2);
+    if (hm1) rm1 = g.rel(bp.y);
+    if (hm2) rm2 = g.rel(bp.x);
+    if (hp1) rp1 = g.rel(bp.z);
+    if (hp2) rp2 = g.rel(bp.w);
     // bonds: U_MLJ^n + FENE(k_n) (Eq. 10)
     const T kf = st_c<T>(st, 0), R0sq = st_c<T>(st, 1);
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
-        if ((side == 0 && i >= 1) || (side == 1 && i <= N - 2)) {
+        if ((side == 0 && hm1) || (side == 1 && hp1)) {
             const T3 d = side == 0 ? rm1 : rp1;
             const T r2 = dot3(d, d);
             const T qmin = st_c<T>(st, 5);
@@ -191,20 +196,20 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
     const T kap = (T)md.kappa;
     if (kap != (T)0) {
         const T3 Bm2 = sub3(rm1, rm2), Bm1 = mk<T>(-rm1.x, -rm1.y, -rm1.z), B0 = rp1, Bp1 = sub3(rp2, rp1);
-        if (i >= 1 && i <= N - 2) {          // vertex s: force kappa (g1 - g2)
+        if (hm1 && hp1) {                    // vertex s: force kappa (g1 - g2)
             const T l1 = dot3(Bm1, Bm1), l2 = dot3(B0, B0), inv = frsqrt(l1 * l2), cs = dot3(Bm1, B0) * inv;
             F.x += kap * ((B0.x * inv - cs * Bm1.x / l1) - (Bm1.x * inv - cs * B0.x / l2));
             F.y += kap * ((B0.y * inv - cs * Bm1.y / l1) - (Bm1.y * inv - cs * B0.y / l2));
             F.z += kap * ((B0.z * inv - cs * Bm1.z / l1) - (Bm1.z * inv - cs * B0.z / l2));
             if (ENERGY) e[2] += (double)kap * (1.0 - (double)cs);
         }
-        if (i <= N - 3) {                    // vertex s+1, s is its first end: -kappa g1
+        if (hp2) {                           // vertex s+1, s is its first end: -kappa g1
             const T l1 = dot3(B0, B0), l2 = dot3(Bp1, Bp1), inv = frsqrt(l1 * l2), cs = dot3(B0, Bp1) * inv;
             F.x -= kap * (Bp1.x * inv - cs * B0.x / l1);
             F.y -= kap * (Bp1.y * inv - cs * B0.y / l1);
             F.z -= kap * (Bp1.z * inv - cs * B0.z / l1);
         }
-        if (i >= 2) {                        // vertex s-1, s is its last end: +kappa g2
+        if (hm2) {                           // vertex s-1, s is its last end: +kappa g2
             const T l1 = dot3(Bm2, Bm2), l2 = dot3(Bm1, Bm1), inv = frsqrt(l1 * l2), cs = dot3(Bm2, Bm1) * inv;
             F.x += kap * (Bm2.x * inv - cs * Bm1.x / l2);
             F.y += kap * (Bm2.y * inv - cs * Bm1.y / l2);
@@ -222,22 +227,25 @@ __global__ void __launch_bounds__(128) k_step_mixed(const SimDev *__restrict__ S
                                                    double *__restrict__ x, float *__restrict__ u,
                                                    const float4 *__restrict__ recb, const float4 *__restrict__ dcur,
                                                    float4 *__restrict__ dnext, const int *__restrict__ nl,
-                                                   const int *__restrict__ nn, unsigned *__restrict__ flags,
-                                                   long long step)
+                                                   const int *__restrict__ nn, const int *__restrict__ slot_of,
+                                                   const int4 *__restrict__ bp, unsigned *__restrict__ flags,
+                                                   const long long *__restrict__ stepp)
 {
     if (flags[0]) return;                  // a latched error stops the run
     const SimDev &S = *Sp;
     const StageDev &st = *stp;
+    const long long step = *stepp;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     bool rebuild = false;
     unsigned err = 0;
     if (s < S.M) {
-        const int m = melt_of(S, s);
+        const int slot = __ldg(slot_of + s);
+        const int m = melt_of(S, slot);
         const MeltDev &md = S.melt[m];
-        const int rel = s - md.off, i = rel % md.N;
+        const int rel = slot - md.off;
         GeoMixed g{recb, dcur, md.ncc, md.hcf};
         g.self(s);
-        float3 F = force_on<false>(g, S, st, md, s, i, nl, __ldg(nn + s), nullptr, err);
+        float3 F = force_on<false>(g, S, st, md, s, __ldg(bp + s), nl, __ldg(nn + s), nullptr, err);
         const float3 gn = gauss3_f(draw(S.seed, m, 0, (unsigned long long)step, (uint32_t)rel));
         const int Mp = S.Mp;
         float3 v = make_float3(u[s], u[Mp + s], u[2 * Mp + s]);
@@ -262,22 +270,25 @@ __global__ void __launch_bounds__(128) k_step_f64(const SimDev *__restrict__ Sp,
                                                  double *__restrict__ x, double *__restrict__ u,
                                                  const double4_32a *__restrict__ pcur, double4_32a *__restrict__ pnext,
                                                  const double4_32a *__restrict__ xb, const int *__restrict__ nl,
-                                                 const int *__restrict__ nn, unsigned *__restrict__ flags,
-                                                 long long step)
+                                                 const int *__restrict__ nn, const int *__restrict__ slot_of,
+                                                 const int4 *__restrict__ bp, unsigned *__restrict__ flags,
+                                                 const long long *__restrict__ stepp)
 {
     if (flags[0]) return;                  // a latched error stops the run
     const SimDev &S = *Sp;
     const StageDev &st = *stp;
+    const long long step = *stepp;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     bool rebuild = false;
     unsigned err = 0;
     if (s < S.M) {
-        const int m = melt_of(S, s);
+        const int slot = __ldg(slot_of + s);
+        const int m = melt_of(S, slot);
         const MeltDev &md = S.melt[m];
-        const int rel = s - md.off, i = rel % md.N;
+        const int rel = slot - md.off;
         GeoF64 g{pcur, md.L, md.invL};
         g.self(s);
-        double3 F = force_on<false>(g, S, st, md, s, i, nl, __ldg(nn + s), nullptr, err);
+        double3 F = force_on<false>(g, S, st, md, s, __ldg(bp + s), nl, __ldg(nn + s), nullptr, err);
         const double3 gn = gauss3_d(draw(S.seed, m, 0, (unsigned long long)step, (uint32_t)rel));
         const int Mp = S.Mp;
         double3 v = make_double3(u[s], u[Mp + s], u[2 * Mp + s]);
@@ -301,20 +312,19 @@ __global__ void __launch_bounds__(128) k_step_f64(const SimDev *__restrict__ Sp,
 // rebuild chain: each kernel returns at once unless flags[1] requests a
 // rebuild; the last block of k_nlist to finish clears the request
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ long long floor_ll(double v) { return (long long)floor(v); }
-
 // records on the code grid, gather buffer reset, Verlet-grid cell + rank
 __global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, const double *__restrict__ x,
                                                float4 *__restrict__ recb, float4 *__restrict__ dcur,
                                                double4_32a *__restrict__ pcur, double4_32a *__restrict__ xb,
                                                int *__restrict__ cellid, int *__restrict__ rank,
-                                               int *__restrict__ count, unsigned *__restrict__ flags)
+                                               int *__restrict__ count, const int *__restrict__ slot_of,
+                                               float4 *__restrict__ wpos, unsigned *__restrict__ flags)
 {
     if (!flags[1] || flags[0]) return;
     const SimDev &S = *Sp;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S.M) return;
-    const MeltDev &md = S.melt[melt_of(S, s)];
+    const MeltDev &md = S.melt[melt_of(S, slot_of[s])];
     const int Mp = S.Mp;
     if (!isfinite(x[s] + x[Mp + s] + x[2 * Mp + s])) {   // never bin a non-finite position
         atomicOr((unsigned *)flags, ERR_NONFINITE);
@@ -322,17 +332,18 @@ __global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, c
     }
     float off[3];
     int code[3], cell[3];
-    double xs[3];
+    double xs[3], ws[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double xd = x[d * Mp + s];
         xs[d] = xd;
-        const long long K = floor_ll(xd * md.invhc);
+        const int K = (int)floor(xd * md.invhc);          // |x| / h < 2^31 (unwrapped cell)
         off[d] = (float)(xd - (double)K * md.hc);
-        long long km = K % md.ncc;
+        int km = K % md.ncc;
         if (km < 0) km += md.ncc;
-        code[d] = (int)km;
+        code[d] = km;
         const double w = xd - md.L * floor(xd * md.invL);
+        ws[d] = w;
         int c = (int)(w * md.invh);
         cell[d] = c < 0 ? 0 : (c >= md.nc ? md.nc - 1 : c);
     }
@@ -343,20 +354,21 @@ __global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, c
         pcur[s] = p;
         xb[s] = p;
     }
-    const int c = md.cell_off + (cell[2] * md.nc + cell[1]) * md.nc + cell[0];
+    const int c = md_cell(md, cell[0], cell[1], cell[2]);
     cellid[s] = c;
     rank[s] = atomicAdd(count + c, 1);
+    wpos[s] = make_float4((float)ws[0], (float)ws[1], (float)ws[2], 0.f);
 }
 
 // DB grid: cell of each particle from its wrapped position (cells >= 1.3 sigma)
 __global__ void __launch_bounds__(256) k_bin_db(const SimDev *__restrict__ Sp, const double *__restrict__ x,
                                                int *__restrict__ cellid, int *__restrict__ rank,
-                                               int *__restrict__ count)
+                                               int *__restrict__ count, const int *__restrict__ slot_of)
 {
     const SimDev &S = *Sp;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S.M) return;
-    const MeltDev &md = S.melt[melt_of(S, s)];
+    const MeltDev &md = S.melt[melt_of(S, slot_of[s])];
     int cell[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -425,18 +437,25 @@ __global__ void __launch_bounds__(1024) k_scan2(int *__restrict__ out, const int
     }
 }
 
+// slot list in cell order; with recb, the wrapped positions are copied into
+// the same order (recs) so that a cell's candidates are one contiguous run
 __global__ void __launch_bounds__(256) k_scatter(const int *__restrict__ cellid, const int *__restrict__ rank,
                                                 const int *__restrict__ start, int *__restrict__ list, int M,
-                                                const unsigned *__restrict__ flags)
+                                                const unsigned *__restrict__ flags,
+                                                const float4 *__restrict__ recb, float4 *__restrict__ recs)
 {
     if (flags && (!flags[1] || flags[0])) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < M) list[start[cellid[s]] + rank[s]] = s;
+    if (s >= M) return;
+    const int pos = start[cellid[s]] + rank[s];
+    list[pos] = s;
+    if (recs) recs[pos] = recb[s];
 }
 
 // within-cell order by slot (deterministic lists), then clear the counts
 __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start, int *__restrict__ list,
-                                                 int *__restrict__ count, int ncell, unsigned *__restrict__ flags)
+                                                 float4 *__restrict__ recs, int *__restrict__ count, int ncell,
+                                                 unsigned *__restrict__ flags)
 {
     if (!flags[1] || flags[0]) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -449,9 +468,11 @@ __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start,
     }
     for (int k = a + 1; k < b; ++k) {
         const int v = list[k];
+        const float4 rv = recs[k];
         int j = k - 1;
-        while (j >= a && list[j] > v) { list[j + 1] = list[j]; --j; }
+        while (j >= a && list[j] > v) { list[j + 1] = list[j]; recs[j + 1] = recs[j]; --j; }
         list[j + 1] = v;
+        recs[j + 1] = rv;
     }
 }
 
@@ -460,45 +481,51 @@ __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start,
 // width 1e-5 around the cutoff (its error is below 2e-6); pairs inside the band
 // are decided by the binary64 distance evaluated exactly as
 // ((dx*dx + dy*dy) + dz*dz), dx = d - L rint(d/L).
+// Verlet list of monomer s: every t != s, not 1-2 bonded, with r^2 < (r_c +
+// skin)^2.  The binary32 distance of wrapped positions decides every pair
+// outside a band around the cutoff that bounds its rounding error (nl_lo,
+// nl_hi, from L); pairs inside the band are decided by the binary64 distance
+// ((dx*dx + dy*dy) + dz*dz), dx = d - L rint(d/L), exactly as the definition.
 __device__ __forceinline__ void nlist_row(const SimDev &S, const double *__restrict__ x,
-                                          const float4 *__restrict__ recb, const int *__restrict__ cellid,
-                                          const int *__restrict__ start, const int *__restrict__ list,
-                                          int *__restrict__ nl, int *__restrict__ nn, unsigned *__restrict__ flags,
-                                          int s)
+                                          const float4 *__restrict__ wpos, const float4 *__restrict__ wps,
+                                          const int *__restrict__ cellid, const int *__restrict__ start,
+                                          const int *__restrict__ list, int *__restrict__ nl, int *__restrict__ nn,
+                                          unsigned *__restrict__ flags, const int *__restrict__ slot_of,
+                                          const int4 *__restrict__ bpa, int s)
 {
-    const MeltDev &md = S.melt[melt_of(S, s)];
-    const int N = md.N, chain = (s - md.off) / N;
-    const float4 bi = __ldg(recb + s);
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int c0 = cellid[s] - md.cell_off, nc = md.nc;
-    const int cx = c0 % nc, cy = (c0 / nc) % nc, cz = c0 / (nc * nc);
+    const MeltDev &md = S.melt[melt_of(S, slot_of[s])];
+    const int4 bp = bpa[s];                                  // 1-2 bonded partners: bp.y, bp.z
+    const float4 wi = __ldg(wpos + s);
+    const float L = md.Lf_wrap, invL = md.invLf;
+    int cx, cy, cz;
+    md_cell_xyz(md, cellid[s], cx, cy, cz);
+    const int nc = md.nc;
     int cnt = 0;
     for (int dz = -1; dz <= 1; ++dz) {
-        const int zz = (cz + dz + nc) % nc;
+        const int zz = cz + dz < 0 ? nc - 1 : (cz + dz >= nc ? 0 : cz + dz);
         for (int dy = -1; dy <= 1; ++dy) {
-            const int yy = (cy + dy + nc) % nc;
+            const int yy = cy + dy < 0 ? nc - 1 : (cy + dy >= nc ? 0 : cy + dy);
             for (int dx = -1; dx <= 1; ++dx) {
-                const int xx = (cx + dx + nc) % nc;
-                const int cell = md.cell_off + (zz * nc + yy) * nc + xx;
+                const int xx = cx + dx < 0 ? nc - 1 : (cx + dx >= nc ? 0 : cx + dx);
+                const int cell = md_cell(md, xx, yy, zz);
                 const int b0 = start[cell], e = start[cell + 1];
                 if (e - b0 > MAX_CELL_OCC) {
                     atomicOr(flags, ERR_NL_CAPACITY);
                     continue;
                 }
                 for (int k = b0; k < e; ++k) {
-                    const int t = list[k];
-                    if (t == s) continue;
-                    if ((t == s + 1 || t == s - 1) && (t - md.off) / N == chain) continue;
-                    const float3 d = rec_rel(bi, z, __ldg(recb + t), z, md.ncc, md.hcf);
-                    const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
-                    bool in;
-                    if (r2 < S.rl2f_lo) in = true;
-                    else if (r2 >= S.rl2f_hi) in = false;
-                    else in = dist2_exact(x, S.Mp, md.L, s, t) < S.rl2;
-                    if (in) {
-                        if (cnt < S.maxnb) nl[(size_t)cnt * S.Mp + s] = t;
-                        ++cnt;
-                    }
+                    const float4 wj = __ldg(wps + k);
+                    float ex = wj.x - wi.x, ey = wj.y - wi.y, ez = wj.z - wi.z;
+                    ex -= L * rintf(ex * invL);
+                    ey -= L * rintf(ey * invL);
+                    ez -= L * rintf(ez * invL);
+                    const float r2 = ex * ex + ey * ey + ez * ez;
+                    if (r2 >= md.nl_hi) continue;
+                    const int t = __ldg(list + k);
+                    if (t == s || t == bp.y || t == bp.z) continue;
+                    if (r2 >= md.nl_lo && !(dist2_exact(x, S.Mp, md.L, s, t) < S.rl2)) continue;
+                    if (cnt < S.maxnb) nl[(size_t)cnt * S.Mp + s] = t;
+                    ++cnt;
                 }
             }
         }
@@ -510,22 +537,25 @@ __device__ __forceinline__ void nlist_row(const SimDev &S, const double *__restr
     }
 }
 
-__global__ void __launch_bounds__(128) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
-                                              const float4 *__restrict__ recb, const int *__restrict__ cellid,
+__global__ void __launch_bounds__(128, 8) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
+                                              const float4 *__restrict__ wpos, const float4 *__restrict__ wps,
+                                              const int *__restrict__ cellid,
                                               const int *__restrict__ start, const int *__restrict__ list,
                                               int *__restrict__ nl, int *__restrict__ nn,
-                                              unsigned *__restrict__ flags)
+                                              unsigned *__restrict__ flags, const int *__restrict__ slot_of,
+                                              const int4 *__restrict__ bp)
 {
     if (!flags[1] || flags[0]) return;
     const SimDev &S = *Sp;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < S.M) nlist_row(S, x, recb, cellid, start, list, nl, nn, flags, s);
+    if (s < S.M) nlist_row(S, x, wpos, wps, cellid, start, list, nl, nn, flags, slot_of, bp, s);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(flags + 4, 1u) == gridDim.x - 1) {
             flags[1] = 0u;
             flags[4] = 0u;
+            flags[5] += 1u;                    // Verlet builds completed
         }
     }
 }
@@ -539,6 +569,7 @@ template <class G>
 __global__ void __launch_bounds__(128) k_forces(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
                                                G g, const void *__restrict__ uptr, int lo, int hi,
                                                const int *__restrict__ nl, const int *__restrict__ nn,
+                                               const int *__restrict__ slot_of, const int4 *__restrict__ bp,
                                                double *__restrict__ Fout, double *__restrict__ part,
                                                unsigned *__restrict__ flags, long long step)
 {
@@ -549,13 +580,14 @@ __global__ void __launch_bounds__(128) k_forces(const SimDev *__restrict__ Sp, c
     double e[5] = {0, 0, 0, 0, 0};
     unsigned err = 0;
     if (s < hi) {
-        const int m = melt_of(S, s);
+        const int slot = slot_of[s];
+        const int m = melt_of(S, slot);
         const MeltDev &md = S.melt[m];
-        const int rel = s - md.off, i = rel % md.N;
+        const int rel = slot - md.off;
         G gg = g;
         gg.melt(md);
         gg.self(s);
-        const auto F = force_on<true>(gg, S, st, md, s, i, nl, __ldg(nn + s), e, err);
+        const auto F = force_on<true>(gg, S, st, md, s, bp[s], nl, __ldg(nn + s), e, err);
         const int Mp = S.Mp;
         if (Fout) {
             Fout[s] = (double)F.x; Fout[Mp + s] = (double)F.y; Fout[2 * Mp + s] = (double)F.z;
@@ -586,25 +618,214 @@ __global__ void __launch_bounds__(128) k_forces(const SimDev *__restrict__ Sp, c
 }
 
 // ---------------------------------------------------------------------------
+// compute order: chain partners, re-sorting, and gathers back to slot order
+// ---------------------------------------------------------------------------
+// bp[i] = compute indices of slots s-2, s-1, s+1, s+2 of i's chain (-1 past an end)
+__global__ void __launch_bounds__(256) k_bonded(const SimDev *__restrict__ Sp, const int *__restrict__ slot_of,
+                                               const int *__restrict__ comp_of, int4 *__restrict__ bp)
+{
+    const SimDev &S = *Sp;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= S.M) return;
+    const int s = slot_of[j];
+    const MeltDev &md = S.melt[melt_of(S, s)];
+    const int i = (s - md.off) % md.N, N = md.N;
+    bp[j] = make_int4(i >= 2 ? comp_of[s - 2] : -1, i >= 1 ? comp_of[s - 1] : -1,
+                      i <= N - 2 ? comp_of[s + 1] : -1, i <= N - 3 ? comp_of[s + 2] : -1);
+}
+
+// New compute order = the cell order of the last Verlet build (clist): gather
+// the per-monomer state into scratch ...
+template <typename U>
+__global__ void __launch_bounds__(256) k_sort_gather(int M, int Mp, const int *__restrict__ order,
+                                                    const double *__restrict__ x, const U *__restrict__ u,
+                                                    const int *__restrict__ pid, const int *__restrict__ slot_of,
+                                                    double *__restrict__ sx, U *__restrict__ su,
+                                                    int *__restrict__ spid, int *__restrict__ sslot)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int o = order[j];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        sx[d * Mp + j] = x[d * Mp + o];
+        su[d * Mp + j] = u[d * Mp + o];
+    }
+    spid[j] = pid[o];
+    sslot[j] = slot_of[o];
+}
+
+// ... and copy it back, with the inverse map.
+template <typename U>
+__global__ void __launch_bounds__(256) k_sort_finish(int M, int Mp, double *__restrict__ x, U *__restrict__ u,
+                                                    int *__restrict__ pid, int *__restrict__ slot_of,
+                                                    int *__restrict__ comp_of, const double *__restrict__ sx,
+                                                    const U *__restrict__ su, const int *__restrict__ spid,
+                                                    const int *__restrict__ sslot)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        x[d * Mp + j] = sx[d * Mp + j];
+        u[d * Mp + j] = su[d * Mp + j];
+    }
+    pid[j] = spid[j];
+    const int s = sslot[j];
+    slot_of[j] = s;
+    comp_of[s] = j;
+}
+
+// out[d][r] = in[d][comp_of[off + r]] for r < n: slot order for the caller
+__global__ void __launch_bounds__(256) k_to_slots(const double *__restrict__ in, int in_stride,
+                                                 const int *__restrict__ comp_of, int off, int n,
+                                                 double *__restrict__ out, int out_stride, int dims)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int j = comp_of[off + r];
+    for (int d = 0; d < dims; ++d) out[(size_t)d * out_stride + r] = in[(size_t)d * in_stride + j];
+}
+
+__global__ void __launch_bounds__(256) k_to_slots_f(const float *__restrict__ in, int in_stride,
+                                                   const int *__restrict__ comp_of, int off, int n,
+                                                   double *__restrict__ out, int out_stride)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int j = comp_of[off + r];
+    for (int d = 0; d < 3; ++d) out[(size_t)d * out_stride + r] = (double)in[(size_t)d * in_stride + j];
+}
+
+__global__ void __launch_bounds__(256) k_to_slots_i(const int *__restrict__ in, const int *__restrict__ comp_of,
+                                                   int off, int n, int *__restrict__ out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) out[r] = in[comp_of[off + r]];
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
+void bonded_partners(kg_ctx *c)
+{
+    ++c->launches;
+    k_bonded<<<nblk(c->M, 256), 256, 0, c->stream>>>(c->d_sim, c->slot_of, c->comp_of, c->bp);
+}
+
+// Re-sort the per-monomer state into the cell order of the last Verlet build.
+// The list then refers to the old order, so a rebuild is requested.
+void md_sort(kg_ctx *c)
+{
+    const int Mp = c->Mp;
+    double *sx = c->scratch;
+    int *spid = (int *)(c->scratch + 6 * (size_t)Mp);
+    int *sslot = spid + Mp;
+    c->launches += 2;
+    if (c->precision == KG_MIXED) {
+        float *su = (float *)(c->scratch + 3 * (size_t)Mp);
+        k_sort_gather<float><<<nblk(c->M, 256), 256, 0, c->stream>>>(c->M, Mp, c->clist, c->x, (const float *)c->u,
+                                                                    c->pid, c->slot_of, sx, su, spid, sslot);
+        k_sort_finish<float><<<nblk(c->M, 256), 256, 0, c->stream>>>(c->M, Mp, c->x, (float *)c->u, c->pid,
+                                                                    c->slot_of, c->comp_of, sx, su, spid, sslot);
+    } else {
+        double *su = c->scratch + 3 * (size_t)Mp;
+        k_sort_gather<double><<<nblk(c->M, 256), 256, 0, c->stream>>>(c->M, Mp, c->clist, c->x,
+                                                                     (const double *)c->u, c->pid, c->slot_of, sx,
+                                                                     su, spid, sslot);
+        k_sort_finish<double><<<nblk(c->M, 256), 256, 0, c->stream>>>(c->M, Mp, c->x, (double *)c->u, c->pid,
+                                                                     c->slot_of, c->comp_of, sx, su, spid, sslot);
+    }
+    bonded_partners(c);
+    static const unsigned one = 1u;
+    cudaMemcpyAsync(c->flags + 1, &one, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream);
+}
+
+void to_slots(kg_ctx *c, int melt, const double *in_comp, double *out_dev, int dims)
+{
+    const MeltDev &md = c->sim.melt[melt];
+    ++c->launches;
+    k_to_slots<<<nblk(md.M, 256), 256, 0, c->stream>>>(in_comp, c->Mp, c->comp_of, md.off, md.M, out_dev, md.M,
+                                                       dims);
+}
+
+void u_to_slots(kg_ctx *c, int melt, double *out_dev)
+{
+    const MeltDev &md = c->sim.melt[melt];
+    ++c->launches;
+    if (c->precision == KG_MIXED)
+        k_to_slots_f<<<nblk(md.M, 256), 256, 0, c->stream>>>((const float *)c->u, c->Mp, c->comp_of, md.off, md.M,
+                                                             out_dev, md.M);
+    else
+        k_to_slots<<<nblk(md.M, 256), 256, 0, c->stream>>>((const double *)c->u, c->Mp, c->comp_of, md.off, md.M,
+                                                           out_dev, md.M, 3);
+}
+
+void pid_to_slots(kg_ctx *c, int melt, int *out_dev)
+{
+    const MeltDev &md = c->sim.melt[melt];
+    ++c->launches;
+    k_to_slots_i<<<nblk(md.M, 256), 256, 0, c->stream>>>(c->pid, c->comp_of, md.off, md.M, out_dev);
+}
+
+// First kernel of every MD step: advance the device step counter (the index
+// of the step about to run) and, inside a captured graph, arm the conditional
+// rebuild node with the rebuild request.
+__global__ void k_begin_step(long long *__restrict__ stepp, unsigned *__restrict__ flags,
+                             cudaGraphConditionalHandle h, int armed)
+{
+    stepp[0] += 1;
+    if (armed) {
+        const unsigned go = (flags[1] && !flags[0]) ? 1u : 0u;
+        cudaGraphSetConditional(h, go);
+        flags[6] += go;                        // rebuild bodies run inside graphs
+    }
+}
+
+__global__ void k_set_step(long long *__restrict__ stepp, long long v) { stepp[0] = v; }
+
+static void launch_rebuild(kg_ctx *c, cudaStream_t st);
+
 void rebuild_md(kg_ctx *c)
 {
-    cudaStream_t st = c->stream;
     c->launches += 6;
+    launch_rebuild(c, c->stream);
+}
+
+static void launch_rebuild(kg_ctx *c, cudaStream_t st)
+{
     const bool mixed = c->precision == KG_MIXED;
     k_bin_md<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->recb, mixed ? c->dlt[c->cur] : nullptr,
                                               mixed ? nullptr : c->pos64[c->cur], c->xb, c->cellid, c->rank,
-                                              c->ccount, c->flags);
+                                              c->ccount, c->slot_of, c->wpos, c->flags);
     const int nb = nblk(c->ncell_md, 1024);
     k_scan1<<<nb, 1024, 0, st>>>(c->ccount, c->cstart, c->bsum, c->ncell_md, c->flags);
     k_scan2<<<nb, 1024, 0, st>>>(c->cstart, c->bsum, c->ncell_md, nb, c->flags);
-    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->cellid, c->rank, c->cstart, c->clist, c->M, c->flags);
-    k_cellsort<<<nblk(c->ncell_md, 256), 256, 0, st>>>(c->cstart, c->clist, c->ccount, c->ncell_md, c->flags);
-    k_nlist<<<nblk(c->M, 128), 128, 0, st>>>(c->d_sim, c->x, c->recb, c->cellid, c->cstart, c->clist, c->nl,
-                                             c->nn, c->flags);
+    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->cellid, c->rank, c->cstart, c->clist, c->M, c->flags, c->wpos,
+                                               c->recs);
+    k_cellsort<<<nblk(c->ncell_md, 256), 256, 0, st>>>(c->cstart, c->clist, c->recs, c->ccount, c->ncell_md,
+                                                       c->flags);
+    k_nlist<<<nblk(c->M, 128), 128, 0, st>>>(c->d_sim, c->x, c->wpos, c->recs, c->cellid, c->cstart, c->clist, c->nl,
+                                             c->nn, c->flags, c->slot_of, c->bp);
+}
+
+static void launch_step_kernel(kg_ctx *c, cudaStream_t st, int cur)
+{
+    const int nb = nblk(c->M, 128);
+    if (c->precision == KG_MIXED)
+        k_step_mixed<<<nb, 128, 0, st>>>(c->d_sim, c->d_stage, c->x, (float *)c->u, c->recb, c->dlt[cur],
+                                         c->dlt[cur ^ 1], c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
+    else
+        k_step_f64<<<nb, 128, 0, st>>>(c->d_sim, c->d_stage, c->x, (double *)c->u, c->pos64[cur], c->pos64[cur ^ 1],
+                                       c->xb, c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
+}
+
+void set_device_step(kg_ctx *c, long long v)
+{
+    ++c->launches;
+    k_set_step<<<1, 1, 0, c->stream>>>(c->d_step, v);
 }
 
 // One MD step: the Verlet list is rebuilt first if the previous step (or a
@@ -622,10 +843,11 @@ void prof_collect(kg_ctx *c)
     c->ev_used = 0;
 }
 
-void md_step(kg_ctx *c, long long step)
+void md_step(kg_ctx *c)
 {
+    k_begin_step<<<1, 1, 0, c->stream>>>(c->d_step, c->flags, cudaGraphConditionalHandle{}, 0);
+    ++c->launches;
     rebuild_md(c);
-    const int nb = nblk(c->M, 128);
     cudaEvent_t e1 = nullptr;
     if (c->prof_on) {
         if (c->ev.empty()) {
@@ -638,15 +860,91 @@ void md_step(kg_ctx *c, long long step)
         ++c->ev_used;
     }
     ++c->launches;
-    if (c->precision == KG_MIXED) {
-        k_step_mixed<<<nb, 128, 0, c->stream>>>(c->d_sim, c->d_stage, c->x, (float *)c->u, c->recb,
-                                                c->dlt[c->cur], c->dlt[c->cur ^ 1], c->nl, c->nn, c->flags, step);
-    } else {
-        k_step_f64<<<nb, 128, 0, c->stream>>>(c->d_sim, c->d_stage, c->x, (double *)c->u, c->pos64[c->cur],
-                                              c->pos64[c->cur ^ 1], c->xb, c->nl, c->nn, c->flags, step);
-    }
+    launch_step_kernel(c, c->stream, c->cur);
     if (e1) cudaEventRecord(e1, c->stream);
     c->cur ^= 1;
+}
+
+// A CUDA graph of GRAPH_STEPS MD steps: per step, the begin kernel, a
+// conditional node holding the rebuild chain (run only when a rebuild was
+// requested), and the fused step kernel.  GRAPH_STEPS is even, so a replay
+// leaves the ping-pong buffers as it found them; one graph per starting buffer.
+static bool capture_graph(kg_ctx *c, int parity)
+{
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    bool ok = cudaStreamBeginCaptureToGraph(c->cap_stream, g, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int cur = parity;
+    for (int i = 0; ok && i < GRAPH_STEPS; ++i) {
+        cudaGraphConditionalHandle h;
+        ok = cudaGraphConditionalHandleCreate(&h, g, 0, 0) == cudaSuccess;
+        if (!ok) break;
+        k_begin_step<<<1, 1, 0, c->cap_stream>>>(c->d_step, c->flags, h, 1);
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        ok = cudaStreamGetCaptureInfo(c->cap_stream, &cs, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess;
+        if (!ok) break;
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        ok = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp) == cudaSuccess &&
+             cudaStreamUpdateCaptureDependencies(c->cap_stream, &cn, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies) == cudaSuccess;
+        if (!ok) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(c->cap_stream2, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (!ok) break;
+        const int save = c->cur;
+        c->cur = cur;
+        launch_rebuild(c, c->cap_stream2);
+        c->cur = save;
+        ok = cudaStreamEndCapture(c->cap_stream2, &body) == cudaSuccess;
+        if (!ok) break;
+        launch_step_kernel(c, c->cap_stream, cur);
+        cur ^= 1;
+    }
+    cudaGraph_t out = nullptr;
+    const bool ended = cudaStreamEndCapture(c->cap_stream, &out) == cudaSuccess;
+    ok = ok && ended && cudaGetLastError() == cudaSuccess &&
+         cudaGraphInstantiate(&c->gexec[parity], g, 0) == cudaSuccess;
+    cudaGraphDestroy(g);
+    if (!ok) {
+        cudaGetLastError();
+        c->gexec[parity] = nullptr;
+    }
+    return ok;
+}
+
+bool md_graph_steps(kg_ctx *c, long long nrep)
+{
+    const int parity = c->cur;
+    if (!c->gexec[parity]) {
+        if (c->graph_failed) return false;
+        if (!c->cap_stream) {
+            if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking) != cudaSuccess) {
+                c->graph_failed = true;
+                return false;
+            }
+        }
+        if (!capture_graph(c, parity)) {
+            c->graph_failed = true;
+            return false;
+        }
+    }
+    for (long long r = 0; r < nrep; ++r) {
+        if (cudaGraphLaunch(c->gexec[parity], c->stream) != cudaSuccess) return false;
+        c->launches += 2 * GRAPH_STEPS;        // begin + step kernels; executed rebuilds counted on the device
+        ++c->graph_replays;
+    }
+    return true;
 }
 
 int forces_blocks(const kg_ctx *c, int melt) { return nblk(c->sim.melt[melt].M, 128); }
@@ -658,11 +956,11 @@ void forces_eval(kg_ctx *c, int melt, long long step, double *F_dev, double *par
     if (c->precision == KG_MIXED) {
         GeoMixed g{c->recb, c->dlt[c->cur], 0, 0.f, {}, {}};
         k_forces<GeoMixed><<<nb, 128, 0, c->stream>>>(c->d_sim, c->d_stage, g, c->u, md.off, md.off + md.M,
-                                                     c->nl, c->nn, F_dev, part_dev, c->flags, step);
+                                                     c->nl, c->nn, c->slot_of, c->bp, F_dev, part_dev, c->flags, step);
     } else {
         GeoF64 g{c->pos64[c->cur], 0.0, 0.0, {}};
         k_forces<GeoF64><<<nb, 128, 0, c->stream>>>(c->d_sim, c->d_stage, g, c->u, md.off, md.off + md.M,
-                                                   c->nl, c->nn, F_dev, part_dev, c->flags, step);
+                                                   c->nl, c->nn, c->slot_of, c->bp, F_dev, part_dev, c->flags, step);
     }
 }
 

@@ -12,15 +12,17 @@ namespace kg {
 // One block per chain: the chain's unwrapped positions in shared memory;
 // thread t accumulates sum_i |x_{i+n} - x_i|^2 for n = t+1, t+1+blockDim, ...
 __global__ void __launch_bounds__(256) k_r2n_chain(const double *__restrict__ x, int Mp, int off, int N,
-                                                  double *__restrict__ out /* [n_ch][N] */)
+                                                  double *__restrict__ out /* [n_ch][N] */,
+                                                  const int *__restrict__ comp_of /* NULL: slot order */)
 {
     extern __shared__ double pos[];          // 3N
     const int c = blockIdx.x;
     const int base = off + c * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        pos[i] = x[base + i];
-        pos[N + i] = x[Mp + base + i];
-        pos[2 * N + i] = x[2 * Mp + base + i];
+        const int j = comp_of ? comp_of[base + i] : base + i;
+        pos[i] = x[j];
+        pos[N + i] = x[Mp + j];
+        pos[2 * N + i] = x[2 * Mp + j];
     }
     __syncthreads();
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
@@ -48,22 +50,23 @@ __global__ void __launch_bounds__(256) k_r2n_reduce(const double *__restrict__ i
 
 __global__ void __launch_bounds__(256) k_hist(const double *__restrict__ x, int Mp, int off, int M, int N,
                                              double L, double R0, int nbins, int *__restrict__ bond_h,
-                                             int *__restrict__ cos_h)
+                                             int *__restrict__ cos_h, const int *__restrict__ comp_of)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= M) return;
     const int s = off + r, i = r % N;
+    const int j0 = comp_of[s], jm = i >= 1 ? comp_of[s - 1] : j0, jp = i + 1 < N ? comp_of[s + 1] : j0;
     double b1[3], b2[3];
     if (i + 1 < N) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) b2[k] = min_image_exact(x[k * Mp + s + 1] - x[k * Mp + s], L);
+        for (int k = 0; k < 3; ++k) b2[k] = min_image_exact(x[k * Mp + jp] - x[k * Mp + j0], L);
         const double len = sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]);
         const int b = (int)floor(len / R0 * nbins);
         if (b >= 0 && b < nbins) atomicAdd(bond_h + b, 1);
     }
     if (i >= 1 && i + 1 < N) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) b1[k] = min_image_exact(x[k * Mp + s] - x[k * Mp + s - 1], L);
+        for (int k = 0; k < 3; ++k) b1[k] = min_image_exact(x[k * Mp + j0] - x[k * Mp + jm], L);
         const double cs = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2])
                           / (sqrt(b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2])
                              * sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]));
@@ -77,7 +80,8 @@ void r2n_eval(kg_ctx *c, int melt, double *out_dev)
 {
     const MeltDev &md = c->sim.melt[melt];
     c->launches += 2;
-    k_r2n_chain<<<md.n_ch, 256, sizeof(double) * 3 * md.N, c->stream>>>(c->x, c->Mp, md.off, md.N, c->r2tmp);
+    k_r2n_chain<<<md.n_ch, 256, sizeof(double) * 3 * md.N, c->stream>>>(c->x, c->Mp, md.off, md.N, c->r2tmp,
+                                                                          c->comp_of);
     k_r2n_reduce<<<(md.N + 255) / 256, 256, 0, c->stream>>>(c->r2tmp, md.n_ch, md.N, out_dev);
 }
 
@@ -87,7 +91,7 @@ void hist_eval(kg_ctx *c, int melt, int nbins, int *out_dev)
     cudaMemsetAsync(out_dev, 0, sizeof(int) * 2 * nbins, c->stream);
     ++c->launches;
     k_hist<<<(md.M + 255) / 256, 256, 0, c->stream>>>(c->x, c->Mp, md.off, md.M, md.N, md.L, sqrt(c->stage.R0sq),
-                                                      nbins, out_dev, out_dev + nbins);
+                                                      nbins, out_dev, out_dev + nbins, c->comp_of);
 }
 
 // ---------------------------------------------------------------------------
@@ -144,7 +148,7 @@ extern "C" kg_status kg_r2n_noalloc(const double *x, long long stride, int n_cha
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kg::k_r2n_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return KG_ERR_CUDA;
-    kg::k_r2n_chain<<<n_chains, 256, smem, s>>>(x, (int)stride, 0, chain_len, scratch);
+    kg::k_r2n_chain<<<n_chains, 256, smem, s>>>(x, (int)stride, 0, chain_len, scratch, nullptr);
     kg::k_r2n_reduce<<<(chain_len + 255) / 256, 256, 0, s>>>(scratch, n_chains, chain_len, out);
     return cudaGetLastError() == cudaSuccess ? KG_OK : KG_ERR_CUDA;
 }

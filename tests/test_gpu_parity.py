@@ -275,3 +275,28 @@ def test_regularised_fene_forces(kg, precision, tol):
     Fo, eo = O.forces(q, x)
     assert _force_err(F, Fo) < tol
     assert e4[1] == pytest.approx(eo[1], rel=1e-9 if precision == 0 else 1e-5)
+
+
+def test_long_run_across_resorts_and_sweeps(kg):
+    # MD steps cross the periodic re-sort into cell order (every 200 steps) with
+    # double-bridging sweeps in between; binary64 path against the oracle
+    m = KI.random_walk_melt(30, 40, 0.85, 1.0, 91)
+    dt = 0.002
+    q = oparams(m, 2.0, dt=dt)
+    xo, uo, pido = m.x.copy(), m.v.copy(), np.arange(m.M, dtype=np.int32)
+    step = 0
+    with context(kg, [m], 0, schedule=[kg.stage(2.0, 10 ** 9, dt)]) as ctx:
+        for sweep, n in enumerate((150, 120, 90)):
+            kg.kg_step(ctx, n)
+            step = O.run(q, xo, uo, step, n)
+            st = kg.kg_db_sweep_k(ctx, [300])
+            _, _, acc = O.db_sweep(q, xo, uo, pido, sweep, 300)
+            assert st.accepted == acc
+        x = np.zeros_like(m.x)
+        pid = np.zeros(m.M, dtype=np.int32)
+        kg.kg_get_config(ctx, 0, x, None, pid)
+        offs, nbr = kg.kg_get_nlist(ctx, 0, m.M)
+    assert np.array_equal(pid, pido)
+    assert np.abs(x - xo).max() < 1e-8
+    oo, on = O.nlist(q, x, RL)
+    assert np.array_equal(offs, oo) and np.array_equal(nbr, on)
