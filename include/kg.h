@@ -96,6 +96,8 @@ typedef struct {
     unsigned long long seed;  /* key of every counter-based random draw                */
     int sort_interval;        /* MD steps between re-sorts of the per-monomer arrays into
                                  cell order (<= 0: 200); results do not depend on it    */
+    int block_size;           /* threads per block of the fused step kernel: 64, 128
+                                 or 256 (<= 0: 128); results do not depend on it        */
     int precision;            /* KG_FP64 or KG_MIXED                                    */
     int flags;                /* KG_FLAG_*                                              */
 } kg_params;
@@ -202,6 +204,24 @@ kg_status kg_forces(kg_ctx *c, int melt, double *F, double *e4);
 kg_status kg_profile(kg_ctx *c, int enable);
 kg_status kg_profile_read(kg_ctx *c, double *step_kernel_ms, long long *step_kernel_launches,
                           long long *kernel_launches);
+
+/* Launch settings picked by kg_autotune. */
+typedef struct {
+    double skin;          /* Verlet skin (also sets the cell size, >= r_c + skin)      */
+    int block_size;       /* threads per block of the fused step kernel                */
+    double ms_per_step;   /* measured wall time of one MD step with these settings     */
+    int trials;           /* configurations timed                                       */
+} kg_tuning;
+
+/* Autotuner: for the melts of *p in the states x[m], v[m] ((3, M_m) arrays,
+ * host or device; v may be NULL) under `stage`, time trial_steps MD steps
+ * (graph-captured, after a warm-up of the same length) for every candidate
+ * skin in {0.25, 0.3, 0.4, 0.5, 0.6} and block size in {64, 128, 256}, each in
+ * a scratch context of its own; return the fastest in *best.  The settings do
+ * not change results beyond floating-point summation order.  Synchronises. */
+kg_status kg_autotune(const kg_params *p, const double *const *x, const double *const *v,
+                      const kg_stage *stage, int trial_steps, int device, void *stream,
+                      const kg_allocator *allocator, kg_tuning *best);
 
 /* Host helpers (no context): k_n of Eq. 9, and the twelve stages of the
  * paper's schedule for (kappa, N) at time step dt (Eqs. 12, 16-20; scheme 1

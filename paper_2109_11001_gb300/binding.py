@@ -24,7 +24,7 @@ KG_FLAG_PAPER_METROPOLIS = 1
 
 EXPORTS = ["kg_create", "kg_load_config", "kg_get_config", "kg_set_potential_schedule", "kg_step",
            "kg_db_sweep", "kg_db_sweep_k", "kg_observables", "kg_sync", "kg_get_counters",
-           "kg_set_counters", "kg_get_nlist", "kg_forces", "kg_profile", "kg_profile_read", "kg_kn", "kg_schedule_paper", "kg_destroy",
+           "kg_set_counters", "kg_get_nlist", "kg_forces", "kg_profile", "kg_profile_read", "kg_autotune", "kg_kn", "kg_schedule_paper", "kg_destroy",
            "kg_strerror", "kg_r2n_noalloc"]
 
 
@@ -37,7 +37,7 @@ class kg_params(C.Structure):
                 ("gamma", C.c_double), ("R0", C.c_double), ("l0", C.c_double),
                 ("db_bond_max", C.c_double), ("r_mc", C.c_double), ("skin", C.c_double),
                 ("fene_qmin", C.c_double), ("seed", C.c_ulonglong), ("sort_interval", C.c_int),
-                ("precision", C.c_int), ("flags", C.c_int)]
+                ("block_size", C.c_int), ("precision", C.c_int), ("flags", C.c_int)]
 
 
 class kg_stage(C.Structure):
@@ -51,6 +51,10 @@ class kg_obs(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class kg_tuning(C.Structure):
+    _fields_ = [("skin", C.c_double), ("block_size", C.c_int), ("ms_per_step", C.c_double), ("trials", C.c_int)]
 
 
 class kg_db_stats(C.Structure):
@@ -97,6 +101,7 @@ def load(path: str = LIB_PATH):
         "kg_get_nlist": (i, [p, i, p, p, ll, C.POINTER(ll)]),
         "kg_forces": (i, [p, i, p, p]),
         "kg_profile": (i, [p, i]),
+        "kg_autotune": (i, [C.POINTER(kg_params), p, p, C.POINTER(kg_stage), i, i, p, p, C.POINTER(kg_tuning)]),
         "kg_profile_read": (i, [p, C.POINTER(d), C.POINTER(ll), C.POINTER(ll)]),
         "kg_kn": (d, [d, d, d]),
         "kg_schedule_paper": (i, [d, i, d, d, C.POINTER(kg_stage)]),
@@ -242,6 +247,17 @@ def kg_profile_read(ctx):
     return ms.value, n.value, launches.value
 
 
+def kg_autotune(params, xs, vs, stage, trial_steps=40, device=0, stream=None, allocator=None):
+    """xs, vs: one (3, M) array per melt (vs may be None)."""
+    xp = (C.c_void_p * len(xs))(*[ptr(a) for a in xs])
+    vp = (C.c_void_p * len(vs))(*[ptr(a) for a in vs]) if vs is not None else None
+    best = kg_tuning()
+    _check(load().kg_autotune(C.byref(params), xp, vp, C.byref(stage), int(trial_steps), int(device), stream,
+                              C.byref(allocator) if allocator is not None else None, C.byref(best)),
+           "kg_autotune")
+    return best
+
+
 def kg_kn(n, R0=1.5, l0=0.960897):
     return load().kg_kn(float(n), float(R0), float(l0))
 
@@ -270,11 +286,11 @@ def kg_strerror(status):
 # ---- convenience: parameter construction ----
 
 def make_params(melts, precision=KG_MIXED, seed=1, T=1.0, gamma=1.0, R0=1.5, l0=0.960897, db_bond_max=1.3,
-                r_mc=1e-3, skin=0.3, flags=0, fene_qmin=0.0, sort_interval=0):
+                r_mc=1e-3, skin=0.3, flags=0, fene_qmin=0.0, sort_interval=0, block_size=0):
     """melts: iterable of (n_chains, chain_len, box, kappa)."""
     arr = (kg_melt * len(melts))(*[kg_melt(int(a), int(b), float(c), float(d)) for a, b, c, d in melts])
     p = kg_params(len(melts), arr, T, gamma, R0, l0, db_bond_max, r_mc, skin, float(fene_qmin), int(seed),
-                  int(sort_interval), int(precision), int(flags))
+                  int(sort_interval), int(block_size), int(precision), int(flags))
     p._keep = arr
     return p
 

@@ -223,6 +223,8 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->p.melts = c->melts.data();
     if (!(c->p.skin > 0)) c->p.skin = 0.3;
     c->sort_interval = p->sort_interval > 0 ? p->sort_interval : 200;
+    c->block = p->block_size > 0 ? p->block_size : 128;
+    if (c->block != 64 && c->block != 128 && c->block != 256) { delete c; return KG_ERR_INVALID_ARG; }
     c->precision = p->precision;
     if (allocator && allocator->alloc && allocator->free) { c->alloc = *allocator; c->have_alloc = true; }
     auto fail = [&](kg_status s) { kg_destroy(c); return s; };
@@ -457,7 +459,7 @@ kg_status kg_set_potential_schedule(kg_ctx *c, const kg_stage *stages, int n_sta
 {
     if (!c || !stages || n_stages < 1) return KG_ERR_INVALID_ARG;
     for (int i = 0; i < n_stages; ++i)
-        if (!(stages[i].dt > 0) || stages[i].n_exp == 6.0 || !(stages[i].n_exp > 0) || stages[i].n_steps < 0)
+        if (!(stages[i].dt > 0) || stages[i].n_exp == 6.0 || !(stages[i].n_exp > 0))
             return KG_ERR_INVALID_ARG;
     if (cudaSetDevice(c->device) != cudaSuccess) return KG_ERR_CUDA;
     c->schedule.assign(stages, stages + n_stages);
@@ -689,6 +691,60 @@ kg_status kg_profile_read(kg_ctx *c, double *ms, long long *n, long long *launch
         *launches = c->launches + 6LL * (long long)f[6];
     }
     return KG_OK;
+}
+
+kg_status kg_autotune(const kg_params *p, const double *const *x, const double *const *v, const kg_stage *stage,
+                      int trial_steps, int device, void *stream, const kg_allocator *allocator, kg_tuning *best)
+{
+    if (!p || !x || !stage || !best || trial_steps < kg::GRAPH_STEPS) return KG_ERR_INVALID_ARG;
+    const double skins[] = {0.25, 0.3, 0.4, 0.5, 0.6};
+    const int blocks[] = {64, 128, 256};
+    best->ms_per_step = 1e300;
+    best->trials = 0;
+    cudaEvent_t e0, e1;
+    if (cudaSetDevice(device) != cudaSuccess) return KG_ERR_CUDA;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KG_ERR_CUDA;
+    kg_status out = KG_OK;
+    for (double skin : skins) {
+        for (int blk : blocks) {
+            kg_params q = *p;
+            q.skin = skin;
+            q.block_size = blk;
+            kg_ctx *c = nullptr;
+            kg_status s = kg_create(&c, &q, device, stream, allocator);
+            if (s == KG_ERR_INVALID_ARG) continue;               // this skin does not fit the box
+            if (s != KG_OK) { out = s; break; }
+            kg_stage st = *stage;
+            st.n_steps = -1;                                       // open-ended stage for the trial
+            for (int m = 0; s == KG_OK && m < p->n_melts; ++m) s = kg_load_config(c, m, x[m], v ? v[m] : nullptr, nullptr);
+            if (s == KG_OK) s = kg_set_potential_schedule(c, &st, 1);
+            if (s == KG_OK) s = kg_step(c, trial_steps);          // warm-up: first build, graph capture
+            float ms = 1e30f;
+            for (int rep = 0; s == KG_OK && rep < 2; ++rep) {   // best of two windows
+                float t = 0.f;
+                cudaEventRecord(e0, c->stream);
+                s = kg_step(c, trial_steps);
+                cudaEventRecord(e1, c->stream);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&t, e0, e1);
+                ms = t < ms ? t : ms;
+            }
+            kg_destroy(c);
+            if (s != KG_OK) { out = s; break; }
+            ++best->trials;
+            const double per = ms / trial_steps;
+            if (per < best->ms_per_step) {
+                best->ms_per_step = per;
+                best->skin = skin;
+                best->block_size = blk;
+            }
+        }
+        if (out != KG_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (out == KG_OK && best->trials == 0) out = KG_ERR_INVALID_ARG;
+    return out;
 }
 
 kg_status kg_get_nlist(kg_ctx *c, int melt, int *offs, int *nbr, long long cap, long long *total)

@@ -49,6 +49,7 @@ struct kg_ctx {
     bool use_graphs = true;
     long long graph_replays = 0;
     long long sort_interval = 200;
+    int block = 128;             // threads per block of the fused step kernel
     float4 *recb = nullptr;
     float4 *wpos = nullptr;      // wrapped binary32 positions (Verlet-list build)
     float4 *recs = nullptr;      // the same in cell order

@@ -223,7 +223,7 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
 // fused MD step: forces at x_n, then u <- u + dt F_n, x <- x + dt u
 // F_n = F_c - gamma u + sqrt(2 gamma T / dt) g_n,  g_n = Philox normals.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_step_mixed(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
+__global__ void __launch_bounds__(256) k_step_mixed(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
                                                    double *__restrict__ x, float *__restrict__ u,
                                                    const float4 *__restrict__ recb, const float4 *__restrict__ dcur,
                                                    float4 *__restrict__ dnext, const int *__restrict__ nl,
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(128) k_step_mixed(const SimDev *__restrict__ S
     if (err) atomicOr(flags, err);
 }
 
-__global__ void __launch_bounds__(128) k_step_f64(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
+__global__ void __launch_bounds__(256) k_step_f64(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
                                                  double *__restrict__ x, double *__restrict__ u,
                                                  const double4_32a *__restrict__ pcur, double4_32a *__restrict__ pnext,
                                                  const double4_32a *__restrict__ xb, const int *__restrict__ nl,
@@ -500,36 +500,42 @@ __device__ __forceinline__ void nlist_row(const SimDev &S, const double *__restr
     int cx, cy, cz;
     md_cell_xyz(md, cellid[s], cx, cy, cz);
     const int nc = md.nc;
-    int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
-        const int zz = cz + dz < 0 ? nc - 1 : (cz + dz >= nc ? 0 : cz + dz);
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int yy = cy + dy < 0 ? nc - 1 : (cy + dy >= nc ? 0 : cy + dy);
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int xx = cx + dx < 0 ? nc - 1 : (cx + dx >= nc ? 0 : cx + dx);
-                const int cell = md_cell(md, xx, yy, zz);
-                const int b0 = start[cell], e = start[cell + 1];
-                if (e - b0 > MAX_CELL_OCC) {
-                    atomicOr(flags, ERR_NL_CAPACITY);
-                    continue;
-                }
-                for (int k = b0; k < e; ++k) {
-                    const float4 wj = __ldg(wps + k);
-                    float ex = wj.x - wi.x, ey = wj.y - wi.y, ez = wj.z - wi.z;
-                    ex -= L * rintf(ex * invL);
-                    ey -= L * rintf(ey * invL);
-                    ez -= L * rintf(ez * invL);
-                    const float r2 = ex * ex + ey * ey + ez * ez;
-                    if (r2 >= md.nl_hi) continue;
-                    const int t = __ldg(list + k);
-                    if (t == s || t == bp.y || t == bp.z) continue;
-                    if (r2 >= md.nl_lo && !(dist2_exact(x, S.Mp, md.L, s, t) < S.rl2)) continue;
-                    if (cnt < S.maxnb) nl[(size_t)cnt * S.Mp + s] = t;
-                    ++cnt;
-                }
+    const int xm = cx ? cx - 1 : nc - 1, xp = cx + 1 < nc ? cx + 1 : 0;
+    const int ym = cy ? cy - 1 : nc - 1, yp = cy + 1 < nc ? cy + 1 : 0;
+    const int zm = cz ? cz - 1 : nc - 1, zp = cz + 1 < nc ? cz + 1 : 0;
+    // the 27 cells as one flattened stream of candidates, so that a warp runs
+    // about the largest lane's total count instead of the largest count per cell
+    int cnt = 0, ci = 0, k = 0, e = 0;
+    for (;;) {
+        while (k >= e) {
+            if (ci == 27) goto done;
+            const int q = ci++;
+            const int xx = (q % 3) == 0 ? xm : ((q % 3) == 1 ? cx : xp);
+            const int yy = ((q / 3) % 3) == 0 ? ym : (((q / 3) % 3) == 1 ? cy : yp);
+            const int zz = (q / 9) == 0 ? zm : ((q / 9) == 1 ? cz : zp);
+            const int cell = md_cell(md, xx, yy, zz);
+            k = start[cell];
+            e = start[cell + 1];
+            if (e - k > MAX_CELL_OCC) {
+                atomicOr(flags, ERR_NL_CAPACITY);
+                k = e;
             }
         }
+        const float4 wj = __ldg(wps + k);
+        float ex = wj.x - wi.x, ey = wj.y - wi.y, ez = wj.z - wi.z;
+        ex -= L * rintf(ex * invL);
+        ey -= L * rintf(ey * invL);
+        ez -= L * rintf(ez * invL);
+        const float r2 = ex * ex + ey * ey + ez * ez;
+        const int kk = k++;
+        if (r2 >= md.nl_hi) continue;
+        const int t = __ldg(list + kk);
+        if (t == s || t == bp.y || t == bp.z) continue;
+        if (r2 >= md.nl_lo && !(dist2_exact(x, S.Mp, md.L, s, t) < S.rl2)) continue;
+        if (cnt < S.maxnb) nl[(size_t)cnt * S.Mp + s] = t;
+        ++cnt;
     }
+done:
     nn[s] = cnt < S.maxnb ? cnt : S.maxnb;
     if (cnt > S.maxnb) {
         atomicOr(flags, ERR_NL_CAPACITY);
@@ -813,12 +819,12 @@ static void launch_rebuild(kg_ctx *c, cudaStream_t st)
 
 static void launch_step_kernel(kg_ctx *c, cudaStream_t st, int cur)
 {
-    const int nb = nblk(c->M, 128);
+    const int nb = nblk(c->M, c->block);
     if (c->precision == KG_MIXED)
-        k_step_mixed<<<nb, 128, 0, st>>>(c->d_sim, c->d_stage, c->x, (float *)c->u, c->recb, c->dlt[cur],
+        k_step_mixed<<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->x, (float *)c->u, c->recb, c->dlt[cur],
                                          c->dlt[cur ^ 1], c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
     else
-        k_step_f64<<<nb, 128, 0, st>>>(c->d_sim, c->d_stage, c->x, (double *)c->u, c->pos64[cur], c->pos64[cur ^ 1],
+        k_step_f64<<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->x, (double *)c->u, c->pos64[cur], c->pos64[cur ^ 1],
                                        c->xb, c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
 }
 

@@ -300,3 +300,38 @@ def test_long_run_across_resorts_and_sweeps(kg):
     assert np.abs(x - xo).max() < 1e-8
     oo, on = O.nlist(q, x, RL)
     assert np.array_equal(offs, oo) and np.array_equal(nbr, on)
+
+
+@pytest.mark.parametrize("skin,block", [(0.6, 64), (0.25, 256)])
+def test_other_skin_and_block(kg, skin, block):
+    import torch
+    m = KI.make(1)
+    dt = 0.002
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=0, seed=11, skin=skin,
+                       block_size=block)
+    ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+    try:
+        kg.kg_set_potential_schedule(ctx, [kg.stage(2.0, 10 ** 9, dt)])
+        kg.kg_load_config(ctx, 0, m.x, m.v)
+        offs, nbr = kg.kg_get_nlist(ctx, 0, m.M)
+        kg.kg_step(ctx, 30)
+        x = np.zeros_like(m.x)
+        kg.kg_get_config(ctx, 0, x)
+    finally:
+        kg.kg_destroy(ctx)
+    q = oparams(m, 2.0, dt=dt)
+    oo, on = O.nlist(q, m.x, 2.0 ** (1 / 6) + skin)
+    assert np.array_equal(offs, oo) and np.array_equal(nbr, on)
+    xo, uo = m.x.copy(), m.v.copy()
+    O.run(q, xo, uo, 0, 30)
+    assert np.abs(x - xo).max() < 1e-9
+
+
+def test_autotune_returns_a_working_setting(kg):
+    import torch
+    m = KI.random_walk_melt(60, 50, 0.85, 2.0, 93)
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=1, seed=3)
+    best = kg.kg_autotune(p, [m.x], [m.v], kg.stage(2.0, -1, 0.002), 20, 0,
+                          torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+    assert best.trials >= 6 and best.block_size in (64, 128, 256) and 0.25 <= best.skin <= 0.6
+    assert 0 < best.ms_per_step < 100
