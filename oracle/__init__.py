@@ -64,6 +64,9 @@ def lib():
             "orc_db_sweep": (i, [p, p, p, p, ll, ll, p]),
             "orc_db_partners": (i, [p, p, p, i, i]),
             "orc_topo_energy": (d, [p, p]),
+            "orc_mlp_forward": (d, [p, p]),
+            "orc_move_features": (None, [p, p, i, i, i, i, i, p]),
+            "orc_db_sweep_learned": (i, [p, p, p, p, ll, ll, p, d, p, p, p, ll, p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -216,3 +219,33 @@ def db_partners(p: Params, x, pid, chain: int, bond: int) -> int:
 def topo_energy(p: Params, x) -> float:
     x = np.ascontiguousarray(x, dtype=np.float64)
     return lib().orc_topo_energy(C.byref(p), _ptr(x))
+
+
+MLP_NPARAM = 64 * 24 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def mlp_forward(w, f):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    return lib().orc_mlp_forward(_ptr(w), _ptr(f))
+
+
+def move_features(p: Params, x, c, b, kind, d, q):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    f = np.zeros(24)
+    lib().orc_move_features(C.byref(p), _ptr(x), int(c), int(b), int(kind), int(d), int(q), _ptr(f))
+    return f
+
+
+def db_sweep_learned(p: Params, x, u, pid, sweep: int, K: int, w, lam: float, log_cap: int = 0):
+    """Sweep with the learned proposal; returns (stats, log features, log targets)."""
+    assert x.flags.c_contiguous and u.flags.c_contiguous and pid.dtype == np.int32
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    stats = np.zeros(3, dtype=np.int64)
+    lf = np.zeros((max(log_cap, 1), 24))
+    lt = np.zeros(max(log_cap, 1))
+    n = C.c_longlong(0)
+    _check(lib().orc_db_sweep_learned(C.byref(p), _ptr(x), _ptr(u), _ptr(pid), int(sweep), int(K), _ptr(w),
+                                      float(lam), _ptr(stats), _ptr(lf) if log_cap else None,
+                                      _ptr(lt) if log_cap else None, int(log_cap), C.byref(n)))
+    return tuple(int(v) for v in stats), lf[:n.value], lt[:n.value]

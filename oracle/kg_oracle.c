@@ -690,3 +690,228 @@ int orc_db_sweep(const orc_params *p, double *x, double *u, int *pid,
     if (stats) { stats[0] = n_att; stats[1] = n_empty; stats[2] = n_acc; }
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned proposal (not in the paper; a reading of the proposal family      */
+/* "any q with q(x->x') > 0 iff q(x'->x) > 0", made exact by the ratio).     */
+/* ------------------------------------------------------------------------ */
+
+double orc_mlp_forward(const double *w, const double f[24])
+{
+    const double *W1 = w, *b1 = W1 + 64 * 24, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *w3 = b2 + 64;
+    const double b3 = w3[64];
+    double h1[64], h2[64];
+    for (int o = 0; o < 64; ++o) {
+        double a = b1[o];
+        for (int i = 0; i < 24; ++i) a += W1[o * 24 + i] * f[i];
+        h1[o] = a > 0.0 ? a : 0.0;
+    }
+    for (int o = 0; o < 64; ++o) {
+        double a = b2[o];
+        for (int i = 0; i < 64; ++i) a += W2[o * 64 + i] * h1[i];
+        h2[o] = a > 0.0 ? a : 0.0;
+    }
+    double s = b3;
+    for (int i = 0; i < 64; ++i) s += w3[i] * h2[i];
+    return s;
+}
+
+static void sort4(double *v)
+{
+    for (int i = 1; i < 4; ++i) {
+        double t = v[i];
+        int j = i - 1;
+        while (j >= 0 && v[j] > t) { v[j + 1] = v[j]; --j; }
+        v[j + 1] = t;
+    }
+}
+
+/* cos of the angle at vertex i of chain c (1 when i is a chain end) */
+static double vertex_cos(const orc_params *p, const double *x, int c, int i)
+{
+    int N = p->chain_len, M = p->n_chains * N;
+    if (i < 1 || i > N - 2) return 1.0;
+    int a = c * N + i - 1;
+    double L = p->box, b1[3], b2[3];
+    for (int k = 0; k < 3; ++k) {
+        b1[k] = min_image(x[k * M + a + 1] - x[k * M + a], L);
+        b2[k] = min_image(x[k * M + a + 2] - x[k * M + a + 1], L);
+    }
+    return (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2])
+           / (sqrt(b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2])
+              * sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]));
+}
+
+static void canon(int N, int c, int b, int kind, int d, int q, int *A, int *B, int *pA, int *pB)
+{
+    (void)N; (void)kind;
+    *A = c < d ? c : d;
+    *B = c < d ? d : c;
+    *pA = (*A == c) ? b : q;
+    *pB = (*A == c) ? q : b;
+}
+
+/* Features (all a function of the move, not of which of its bonds was drawn):
+ *  0-1 removed bond lengths (sorted)      2-3 new bond lengths (sorted)
+ *  4   change of FENE log terms           5   change of bending energy
+ *  6-9 cos at the four junction vertices before (sorted)
+ * 10-13 the same after                   14-17 cos one vertex further out, before (sorted)
+ * 18 kind  19 kappa/4  20 n/12  21 min(p+1, N-1-p)/N  22 dE  23 1 */
+void orc_move_features(const orc_params *p, const double *x, int c, int b, int kind, int d, int q,
+                       double f[24])
+{
+    int N = p->chain_len, M = p->n_chains * N;
+    double L = p->box;
+    int u = c * N + b, w = u + 1, X, Y;
+    if (kind == 0) { Y = d * N + b; X = Y + 1; } else { X = d * N + q; Y = X + 1; }
+    double o1 = sqrt(dist2(x, M, L, u, w)), o2 = sqrt(dist2(x, M, L, X, Y));
+    double n1 = sqrt(dist2(x, M, L, u, X)), n2 = sqrt(dist2(x, M, L, Y, w));
+    f[0] = o1 < o2 ? o1 : o2; f[1] = o1 < o2 ? o2 : o1;
+    f[2] = n1 < n2 ? n1 : n2; f[3] = n1 < n2 ? n2 : n1;
+    f[4] = orc_fene_reg_u(p->k_fene, p->R0, p->fene_qmin, n1) + orc_fene_reg_u(p->k_fene, p->R0, p->fene_qmin, n2)
+           - orc_fene_reg_u(p->k_fene, p->R0, p->fene_qmin, o1) - orc_fene_reg_u(p->k_fene, p->R0, p->fene_qmin, o2);
+    int A, B, pA, pB;
+    canon(N, c, b, kind, d, q, &A, &B, &pA, &pB);
+    double before[4] = {vertex_cos(p, x, A, pA), vertex_cos(p, x, A, pA + 1), vertex_cos(p, x, B, pB),
+                        vertex_cos(p, x, B, pB + 1)};
+    double outer[4] = {vertex_cos(p, x, A, pA - 1), vertex_cos(p, x, A, pA + 2), vertex_cos(p, x, B, pB - 1),
+                       vertex_cos(p, x, B, pB + 2)};
+    /* the state after the move, on copies of the two chains' positions */
+    double *xx = (double *)malloc(sizeof(double) * 3 * (size_t)M);
+    memcpy(xx, x, sizeof(double) * 3 * (size_t)M);
+    for (int k = 0; k < 3; ++k) {
+        for (int i = 0; i < N; ++i) {
+            int sa = A * N + i, sb = B * N + i, ta, tb;
+            if (kind == 0) {
+                ta = i > pA ? B * N + i : sa;
+                tb = i > pA ? A * N + i : sb;
+            } else {
+                ta = i > pA ? B * N + (N - 1 - i) : sa;
+                tb = i <= pB ? A * N + (N - 1 - i) : sb;
+            }
+            xx[k * M + sa] = x[k * M + ta];
+            xx[k * M + sb] = x[k * M + tb];
+        }
+    }
+    double after[4] = {vertex_cos(p, xx, A, pA), vertex_cos(p, xx, A, pA + 1), vertex_cos(p, xx, B, pB),
+                       vertex_cos(p, xx, B, pB + 1)};
+    double dbend = 0.0;
+    for (int i = 0; i < 4; ++i) dbend += p->kappa * ((1.0 - after[i]) - (1.0 - before[i]));
+    free(xx);
+    f[5] = dbend;
+    sort4(before); sort4(after); sort4(outer);
+    for (int i = 0; i < 4; ++i) { f[6 + i] = before[i]; f[10 + i] = after[i]; f[14 + i] = outer[i]; }
+    f[18] = kind;
+    f[19] = p->kappa / 4.0;
+    f[20] = p->n_exp / 12.0;
+    int lo = b + 1 < N - 1 - b ? b + 1 : N - 1 - b;
+    f[21] = (double)lo / N;
+    f[22] = f[4] + f[5];
+    f[23] = 1.0;
+}
+
+/* proposal weights over a sorted partner list; returns the weight of entry j */
+static void proposal_weights(const orc_params *p, const double *x, const double *w, double lambda, int c, int b,
+                             const orc_cand *cand, int n, double *pi)
+{
+    double smax = -1e300, z = 0.0;
+    double *s = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int j = 0; j < n; ++j) {
+        double f[24];
+        orc_move_features(p, x, c, b, cand[j].kind, cand[j].d, cand[j].q, f);
+        s[j] = orc_mlp_forward(w, f);
+        if (s[j] > smax) smax = s[j];
+    }
+    for (int j = 0; j < n; ++j) z += exp(s[j] - smax);
+    for (int j = 0; j < n; ++j) pi[j] = (1.0 - lambda) * exp(s[j] - smax) / z + lambda / n;
+    free(s);
+}
+
+/* probability that bond (c, b)'s proposal picks the move with canonical form
+ * (kind, A, B, pA, pB) */
+static double pick_prob(const orc_params *p, const double *x, const int *pid, const double *w, double lambda,
+                        int c, int b, int kind, int A, int B, int pA, int pB, orc_cand *cand, double *pi)
+{
+    int N = p->chain_len;
+    int n = enum_partners(p, x, pid, c, b, cand);
+    if (n == 0) return 0.0;
+    qsort(cand, (size_t)n, sizeof(orc_cand), cmp_cand);
+    proposal_weights(p, x, w, lambda, c, b, cand, n, pi);
+    for (int j = 0; j < n; ++j) {
+        int a2, b2, pa2, pb2;
+        canon(N, c, b, cand[j].kind, cand[j].d, cand[j].q, &a2, &b2, &pa2, &pb2);
+        if (cand[j].kind == kind && a2 == A && b2 == B && pa2 == pA && pb2 == pB) return pi[j];
+    }
+    return 0.0;
+}
+
+int orc_db_sweep_learned(const orc_params *p, double *x, double *u, int *pid, long long sweep, long long K,
+                         const double *w, double lambda, long long *stats, double *log_f, double *log_t,
+                         long long log_cap, long long *log_n)
+{
+    int N = p->chain_len, M = p->n_chains * N;
+    long long nbonds = (long long)p->n_chains * (N - 1), nlog = 0;
+    int *img = (int *)calloc(3 * (size_t)M, sizeof(int));
+    orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)M * 2);
+    double *pi = (double *)malloc(sizeof(double) * (size_t)M * 2);
+    slotrec *save = (slotrec *)malloc(sizeof(slotrec) * 2 * (size_t)N);
+    slotrec *tmp = (slotrec *)malloc(sizeof(slotrec) * 2 * (size_t)N);
+    long long n_att = 0, n_empty = 0, n_acc = 0;
+    int st = ORC_OK;
+    for (long long k = 0; k < K; ++k) {
+        uint32_t r[4], r2[4];
+        philox_draw(p->seed, p->stream, 1, (unsigned long long)sweep, (uint32_t)k, r);
+        philox_draw(p->seed, p->stream, 2, (unsigned long long)sweep, (uint32_t)k, r2);
+        long long bond = mul_hi64(((uint64_t)r[1] << 32) | r[0], (uint64_t)nbonds);
+        double u_acc = ((double)(r[2] >> 5) * 67108864.0 + (double)(r[3] >> 6)) * (1.0 / 9007199254740992.0);
+        double u_pick = (double)((((uint64_t)r2[1] << 32) | r2[0]) >> 11) * (1.0 / 9007199254740992.0);
+        int c = (int)(bond / (N - 1)), b = (int)(bond % (N - 1));
+        ++n_att;
+        int n1 = enum_partners(p, x, pid, c, b, cand);
+        if (n1 == 0) { ++n_empty; continue; }
+        qsort(cand, (size_t)n1, sizeof(orc_cand), cmp_cand);
+        proposal_weights(p, x, w, lambda, c, b, cand, n1, pi);
+        if (log_f) {
+            for (int j = 0; j < n1 && nlog < log_cap; ++j, ++nlog) {
+                orc_move_features(p, x, c, b, cand[j].kind, cand[j].d, cand[j].q, log_f + 24 * nlog);
+                double de = log_f[24 * nlog + 22] / p->T;
+                log_t[nlog] = de > 0.0 ? exp(-de) : 1.0;
+            }
+        }
+        int j = 0;
+        double cum = pi[0];
+        while (j + 1 < n1 && u_pick >= cum) cum += pi[++j];
+        orc_cand m = cand[j];
+        int A, B, pA, pB;
+        canon(N, c, b, m.kind, m.d, m.q, &A, &B, &pA, &pB);
+        double f[24];
+        orc_move_features(p, x, c, b, m.kind, m.d, m.q, f);
+        double dE = f[22];
+        /* forward: either removed bond may have been drawn */
+        double q_fwd = pi[j] + pick_prob(p, x, pid, w, lambda, m.d, m.q, m.kind, A, B, pA, pB,
+                                         cand + M, pi + M);
+        for (int i = 0; i < N; ++i) {
+            load_rec(&save[i], x, u, pid, img, M, A * N + i);
+            load_rec(&save[N + i], x, u, pid, img, M, B * N + i);
+        }
+        apply_move(p, x, u, pid, img, m.kind, A, B, pA, pB, tmp);
+        double q_rev = pick_prob(p, x, pid, w, lambda, A, pA, m.kind, A, B, pA, pB, cand + M, pi + M)
+                       + pick_prob(p, x, pid, w, lambda, B, pB, m.kind, A, B, pA, pB, cand + M, pi + M);
+        if (q_rev <= 0.0 || q_fwd <= 0.0) { st = ORC_BADARG; break; }
+        double a = exp(-dE / p->T) * q_rev / q_fwd;
+        if (u_acc < a) {
+            ++n_acc;
+        } else {
+            for (int i = 0; i < N; ++i) {
+                store_rec(&save[i], x, u, pid, img, M, A * N + i);
+                store_rec(&save[N + i], x, u, pid, img, M, B * N + i);
+            }
+        }
+    }
+    for (int s = 0; s < M; ++s)
+        for (int k = 0; k < 3; ++k) x[k * M + s] += p->box * (double)img[3 * s + k];
+    free(img); free(cand); free(pi); free(save); free(tmp);
+    if (stats) { stats[0] = n_att; stats[1] = n_empty; stats[2] = n_acc; }
+    if (log_n) *log_n = nlog;
+    return st;
+}

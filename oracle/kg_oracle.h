@@ -101,6 +101,26 @@ int orc_db_partners(const orc_params *p, const double *x, const int *pid, int c,
 /* topology energy of the chains: sum of FENE log terms + bending (Eq. 4) */
 double orc_topo_energy(const orc_params *p, const double *x);
 
+/* ---- learned double-bridging proposal (not in the paper) ----
+ * MLP 24 -> 64 -> 64 -> 1 with ReLU; parameters packed as
+ * W1[64][24], b1[64], W2[64][64], b2[64], w3[64], b3 (ORC_MLP_NPARAM doubles). */
+#define ORC_MLP_NPARAM (64 * 24 + 64 + 64 * 64 + 64 + 64 + 1)
+double orc_mlp_forward(const double *w, const double f[24]);
+
+/* features of the swap that pairs bond (chain c, index b) with partner entry
+ * (kind, d, q) of its partner list, in the current state */
+void orc_move_features(const orc_params *p, const double *x, int c, int b, int kind, int d, int q,
+                       double f[24]);
+
+/* One sweep with the learned proposal: the drawn bond's partner is chosen with
+ * probability (1 - lambda) softmax(MLP logits) + lambda / |P|, and moves are
+ * accepted with min(1, exp(-dE/T) q(x'->x) / q(x->x')).  log_f / log_t (may be
+ * NULL) receive the features and min(1, exp(-dE/T)) of every candidate of every
+ * non-empty attempt, up to log_cap rows; *log_n the number written. */
+int orc_db_sweep_learned(const orc_params *p, double *x, double *u, int *pid, long long sweep, long long K,
+                         const double *w, double lambda, long long *stats, double *log_f, double *log_t,
+                         long long log_cap, long long *log_n);
+
 #ifdef __cplusplus
 }
 #endif
