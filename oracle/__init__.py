@@ -66,7 +66,8 @@ def lib():
             "orc_topo_energy": (d, [p, p]),
             "orc_mlp_forward": (d, [p, p]),
             "orc_move_features": (None, [p, p, i, i, i, i, i, p]),
-            "orc_db_sweep_learned": (i, [p, p, p, p, ll, ll, p, d, p, p, p, ll, p]),
+            "orc_db_sweep_learned": (i, [p, p, p, p, ll, ll, p, d, i, p, p, p, ll, p]),
+            "orc_bf16_round": (d, [d]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -237,7 +238,12 @@ def move_features(p: Params, x, c, b, kind, d, q):
     return f
 
 
-def db_sweep_learned(p: Params, x, u, pid, sweep: int, K: int, w, lam: float, log_cap: int = 0):
+def bf16_round(v):
+    return lib().orc_bf16_round(float(v))
+
+
+def db_sweep_learned(p: Params, x, u, pid, sweep: int, K: int, w, lam: float, log_cap: int = 0,
+                     bf16_inputs: bool = False):
     """Sweep with the learned proposal; returns (stats, log features, log targets)."""
     assert x.flags.c_contiguous and u.flags.c_contiguous and pid.dtype == np.int32
     w = np.ascontiguousarray(w, dtype=np.float64)
@@ -246,6 +252,6 @@ def db_sweep_learned(p: Params, x, u, pid, sweep: int, K: int, w, lam: float, lo
     lt = np.zeros(max(log_cap, 1))
     n = C.c_longlong(0)
     _check(lib().orc_db_sweep_learned(C.byref(p), _ptr(x), _ptr(u), _ptr(pid), int(sweep), int(K), _ptr(w),
-                                      float(lam), _ptr(stats), _ptr(lf) if log_cap else None,
+                                      float(lam), int(bool(bf16_inputs)), _ptr(stats), _ptr(lf) if log_cap else None,
                                       _ptr(lt) if log_cap else None, int(log_cap), C.byref(n)))
     return tuple(int(v) for v in stats), lf[:n.value], lt[:n.value]

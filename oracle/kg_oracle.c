@@ -756,7 +756,11 @@ static void canon(int N, int c, int b, int kind, int d, int q, int *A, int *B, i
  *  4   change of FENE log terms           5   change of bending energy
  *  6-9 cos at the four junction vertices before (sorted)
  * 10-13 the same after                   14-17 cos one vertex further out, before (sorted)
- * 18 kind  19 kappa/4  20 n/12  21 min(p+1, N-1-p)/N  22 dE  23 1 */
+ * 18 cos between the removed bonds, each pointing from the monomer that bonds to u to the one that
+ *    bonds to w (u -> w and X -> Y, new bonds u-X and Y-w)
+ * 19 kappa/4  20 n/12  21 min(p+1, N-1-p)/N  22 dE  23 1
+ * Every feature is a function of positions and bonds alone, not of the direction in which a chain's
+ * slots are numbered: kinds 0 and 1 are the same reconnection seen from the two numberings. */
 void orc_move_features(const orc_params *p, const double *x, int c, int b, int kind, int d, int q,
                        double f[24])
 {
@@ -801,7 +805,16 @@ void orc_move_features(const orc_params *p, const double *x, int c, int b, int k
     f[5] = dbend;
     sort4(before); sort4(after); sort4(outer);
     for (int i = 0; i < 4; ++i) { f[6 + i] = before[i]; f[10 + i] = after[i]; f[14 + i] = outer[i]; }
-    f[18] = kind;
+    {
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) {
+            e1[k] = min_image(x[k * M + w] - x[k * M + u], L);
+            e2[k] = min_image(x[k * M + Y] - x[k * M + X], L);
+        }
+        f[18] = (e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2])
+                / (sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2])
+                   * sqrt(e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]));
+    }
     f[19] = p->kappa / 4.0;
     f[20] = p->n_exp / 12.0;
     int lo = b + 1 < N - 1 - b ? b + 1 : N - 1 - b;
@@ -810,15 +823,26 @@ void orc_move_features(const orc_params *p, const double *x, int c, int b, int k
     f[23] = 1.0;
 }
 
+/* v rounded to the nearest bfloat16 (8 significant bits), ties to even */
+double orc_bf16_round(double v)
+{
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    double m = frexp(v, &e);                  /* v = m 2^e, 0.5 <= |m| < 1 */
+    return ldexp(nearbyint(ldexp(m, 8)), e - 8);
+}
+
 /* proposal weights over a sorted partner list; returns the weight of entry j */
-static void proposal_weights(const orc_params *p, const double *x, const double *w, double lambda, int c, int b,
-                             const orc_cand *cand, int n, double *pi)
+static void proposal_weights(const orc_params *p, const double *x, const double *w, double lambda, int bf16_in,
+                             int c, int b, const orc_cand *cand, int n, double *pi)
 {
     double smax = -1e300, z = 0.0;
     double *s = (double *)malloc(sizeof(double) * (size_t)n);
     for (int j = 0; j < n; ++j) {
         double f[24];
         orc_move_features(p, x, c, b, cand[j].kind, cand[j].d, cand[j].q, f);
+        if (bf16_in)
+            for (int i = 0; i < 24; ++i) f[i] = orc_bf16_round(f[i]);
         s[j] = orc_mlp_forward(w, f);
         if (s[j] > smax) smax = s[j];
     }
@@ -830,13 +854,13 @@ static void proposal_weights(const orc_params *p, const double *x, const double 
 /* probability that bond (c, b)'s proposal picks the move with canonical form
  * (kind, A, B, pA, pB) */
 static double pick_prob(const orc_params *p, const double *x, const int *pid, const double *w, double lambda,
-                        int c, int b, int kind, int A, int B, int pA, int pB, orc_cand *cand, double *pi)
+                        int bf16_in, int c, int b, int kind, int A, int B, int pA, int pB, orc_cand *cand, double *pi)
 {
     int N = p->chain_len;
     int n = enum_partners(p, x, pid, c, b, cand);
     if (n == 0) return 0.0;
     qsort(cand, (size_t)n, sizeof(orc_cand), cmp_cand);
-    proposal_weights(p, x, w, lambda, c, b, cand, n, pi);
+    proposal_weights(p, x, w, lambda, bf16_in, c, b, cand, n, pi);
     for (int j = 0; j < n; ++j) {
         int a2, b2, pa2, pb2;
         canon(N, c, b, cand[j].kind, cand[j].d, cand[j].q, &a2, &b2, &pa2, &pb2);
@@ -846,8 +870,8 @@ static double pick_prob(const orc_params *p, const double *x, const int *pid, co
 }
 
 int orc_db_sweep_learned(const orc_params *p, double *x, double *u, int *pid, long long sweep, long long K,
-                         const double *w, double lambda, long long *stats, double *log_f, double *log_t,
-                         long long log_cap, long long *log_n)
+                         const double *w, double lambda, int bf16_in, long long *stats, double *log_f,
+                         double *log_t, long long log_cap, long long *log_n)
 {
     int N = p->chain_len, M = p->n_chains * N;
     long long nbonds = (long long)p->n_chains * (N - 1), nlog = 0;
@@ -870,7 +894,7 @@ int orc_db_sweep_learned(const orc_params *p, double *x, double *u, int *pid, lo
         int n1 = enum_partners(p, x, pid, c, b, cand);
         if (n1 == 0) { ++n_empty; continue; }
         qsort(cand, (size_t)n1, sizeof(orc_cand), cmp_cand);
-        proposal_weights(p, x, w, lambda, c, b, cand, n1, pi);
+        proposal_weights(p, x, w, lambda, bf16_in, c, b, cand, n1, pi);
         if (log_f) {
             for (int j = 0; j < n1 && nlog < log_cap; ++j, ++nlog) {
                 orc_move_features(p, x, c, b, cand[j].kind, cand[j].d, cand[j].q, log_f + 24 * nlog);
@@ -888,15 +912,15 @@ int orc_db_sweep_learned(const orc_params *p, double *x, double *u, int *pid, lo
         orc_move_features(p, x, c, b, m.kind, m.d, m.q, f);
         double dE = f[22];
         /* forward: either removed bond may have been drawn */
-        double q_fwd = pi[j] + pick_prob(p, x, pid, w, lambda, m.d, m.q, m.kind, A, B, pA, pB,
+        double q_fwd = pi[j] + pick_prob(p, x, pid, w, lambda, bf16_in, m.d, m.q, m.kind, A, B, pA, pB,
                                          cand + M, pi + M);
         for (int i = 0; i < N; ++i) {
             load_rec(&save[i], x, u, pid, img, M, A * N + i);
             load_rec(&save[N + i], x, u, pid, img, M, B * N + i);
         }
         apply_move(p, x, u, pid, img, m.kind, A, B, pA, pB, tmp);
-        double q_rev = pick_prob(p, x, pid, w, lambda, A, pA, m.kind, A, B, pA, pB, cand + M, pi + M)
-                       + pick_prob(p, x, pid, w, lambda, B, pB, m.kind, A, B, pA, pB, cand + M, pi + M);
+        double q_rev = pick_prob(p, x, pid, w, lambda, bf16_in, A, pA, m.kind, A, B, pA, pB, cand + M, pi + M)
+                       + pick_prob(p, x, pid, w, lambda, bf16_in, B, pB, m.kind, A, B, pA, pB, cand + M, pi + M);
         if (q_rev <= 0.0 || q_fwd <= 0.0) { st = ORC_BADARG; break; }
         double a = exp(-dE / p->T) * q_rev / q_fwd;
         if (u_acc < a) {

@@ -114,12 +114,17 @@ void orc_move_features(const orc_params *p, const double *x, int c, int b, int k
 
 /* One sweep with the learned proposal: the drawn bond's partner is chosen with
  * probability (1 - lambda) softmax(MLP logits) + lambda / |P|, and moves are
- * accepted with min(1, exp(-dE/T) q(x'->x) / q(x->x')).  log_f / log_t (may be
+ * accepted with min(1, exp(-dE/T) q(x'->x) / q(x->x')).  bf16_in = 1 rounds the
+ * features to bfloat16 before the network (the input precision of a bf16
+ * tensor-core network); the network itself stays FP64.  log_f / log_t (may be
  * NULL) receive the features and min(1, exp(-dE/T)) of every candidate of every
  * non-empty attempt, up to log_cap rows; *log_n the number written. */
 int orc_db_sweep_learned(const orc_params *p, double *x, double *u, int *pid, long long sweep, long long K,
-                         const double *w, double lambda, long long *stats, double *log_f, double *log_t,
-                         long long log_cap, long long *log_n);
+                         const double *w, double lambda, int bf16_in, long long *stats, double *log_f,
+                         double *log_t, long long log_cap, long long *log_n);
+
+/* v rounded to the nearest bfloat16 (8 significant bits), ties to even */
+double orc_bf16_round(double v);
 
 #ifdef __cplusplus
 }

@@ -165,9 +165,44 @@ def test_features_do_not_depend_on_the_drawn_bond():
             for kind, d, q in _moves_of_bond(s, P, m.box, nch, N, c, b):
                 f1 = O.move_features(p, x, c, b, kind, d, q)
                 f2 = O.move_features(p, x, d, q, kind, c, b)
-                assert np.allclose(f1[:21], f2[:21], rtol=1e-12, atol=1e-12) and np.allclose(f1[22:], f2[22:])
+                assert np.allclose(f1, f2, rtol=1e-12, atol=1e-12)
                 n += 1
     assert n > 0
+
+
+def _features_by_move(p, P, state, nch, N, c, b):
+    """features of every admissible swap of bond (c, b), keyed by the two new bonds"""
+    x = np.ascontiguousarray(P[list(state)].T)
+    u, w = state[c * N + b], state[c * N + b + 1]
+    out = {}
+    for kind, d, q in _moves_of_bond(state, P, p.box, nch, N, c, b):
+        if kind == 0:
+            Y, X = state[d * N + b], state[d * N + b + 1]
+        else:
+            X, Y = state[d * N + q], state[d * N + q + 1]
+        out[frozenset([frozenset([u, X]), frozenset([Y, w])])] = O.move_features(p, x, c, b, kind, d, q)
+    return out
+
+
+def test_features_do_not_depend_on_slot_numbering_direction():
+    # reversing the slot order of one chain relabels kinds 0 <-> 1 and p <-> N-2-p
+    # but is the same melt: every move keeps its features
+    m, nch, N, P, states = _pick_tiny()
+    p = O.params(nch, N, m.box, 1.5, n_exp=3.0)
+    n = 0
+    for s in sorted(states)[:12]:
+        for d in range(nch):
+            r = list(s)
+            r[d * N:(d + 1) * N] = r[d * N:(d + 1) * N][::-1]
+            for c in range(nch):
+                for b in range(N - 1):
+                    f1 = _features_by_move(p, P, s, nch, N, c, b)
+                    f2 = _features_by_move(p, P, tuple(r), nch, N, c, N - 2 - b if c == d else b)
+                    assert f1.keys() == f2.keys()
+                    for k in f1:
+                        assert np.allclose(f1[k], f2[k], rtol=1e-12, atol=1e-12), (s, d, c, b)
+                        n += 1
+    assert n > 50
 
 
 def test_sweep_log():
@@ -180,3 +215,54 @@ def test_sweep_log():
     assert len(lf) >= att - empty and np.isfinite(lf).all()
     assert ((lt > 0) & (lt <= 1)).all()
     assert np.allclose(lt, np.minimum(1.0, np.exp(-lf[:, 22])))
+
+
+def test_bf16_rounding():
+    torch = pytest.importorskip("torch")
+    # hand values: 8 significant bits, ties to even
+    assert O.bf16_round(1.0 + 2.0 ** -8) == 1.0
+    assert O.bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    assert O.bf16_round(1.0 + 2.0 ** -8 + 2.0 ** -30) == 1.0 + 2.0 ** -7
+    assert O.bf16_round(-3.0) == -3.0 and O.bf16_round(0.0) == 0.0
+    rng = np.random.default_rng(4)
+    v = rng.normal(size=2000) * 10.0 ** rng.uniform(-6, 3, 2000)
+    # binary32 inputs: torch's float32 -> bfloat16 conversion rounds to nearest even
+    v32 = v.astype(np.float32)
+    ref = torch.from_numpy(v32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16(v32.astype(np.float64)), ref)
+    assert all(O.bf16_round(a) == b for a, b in zip(v32.astype(np.float64), ref))
+    # binary64 inputs: C and numpy agree, and the result is within half a bf16 ulp
+    c = np.array([O.bf16_round(a) for a in v])
+    assert np.array_equal(c, mlp.bf16(v))
+    assert np.all(np.abs(c - v) <= np.abs(v) * 2.0 ** -8)
+
+
+def test_bf16_network_tracks_fp64():
+    rng = np.random.default_rng(6)
+    w = mlp.init(9)
+    F = rng.normal(size=(200, 24))
+    t = rng.random(200)
+    s64, _ = mlp.forward(w, F)
+    s16, _ = mlp.forward_bf16(w, F)
+    assert np.abs(s16 - s64).max() < 0.05 * (1 + np.abs(s64).max())
+    l64, g64 = mlp.loss_and_grad(w, F, t)
+    l16, g16 = mlp.loss_and_grad_bf16(w, F, t)
+    assert l16 == pytest.approx(l64, rel=2e-2)
+    assert np.dot(g16, g64) / np.linalg.norm(g16) / np.linalg.norm(g64) > 0.999
+    # exactly representable weights and inputs: the two agree to rounding of sums
+    wd = mlp.sparse_dyadic(1)
+    Fb = mlp.bf16(F)
+    assert np.allclose(mlp.forward_bf16(wd, Fb)[0], mlp.forward(wd, Fb)[0], rtol=1e-12, atol=1e-12)
+
+
+def test_learned_sweep_bf16_inputs():
+    # the input rounding changes features by <= 2^-9 relative; with the sparse
+    # dyadic network the sweep still balances (exact kernel on bf16 inputs)
+    m, nch, N, P, states = _pick_tiny()
+    p = O.params(nch, N, m.box, 0.5, n_exp=2.0, seed=5)
+    x = np.ascontiguousarray(m.x.copy())
+    u = np.zeros_like(x)
+    pid = np.arange(nch * N, dtype=np.int32)
+    (att, empty, acc), _, _ = O.db_sweep_learned(p, x, u, pid, 0, 400, mlp.sparse_dyadic(2), 0.1,
+                                                 bf16_inputs=True)
+    assert att == 400 and acc > 0
