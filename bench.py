@@ -337,10 +337,12 @@ def run_ours(args, world, rank, local):
     t_e2e = allmax(world, time.perf_counter() - t0)
     log(f"e2e {t_e2e:.3f} s")
 
-    # secondary: the same step in plain binary64 on this GPU (single rank)
-    sec = None
+    # secondary: the same step in plain binary64 on this GPU (single rank), and
+    # the learned double-bridging proposal against the uniform one
+    sec = lsec = None
     if world == 1 and args.secondary:
         sec = secondary(kg, torch, args, local)
+        lsec = learned_secondary(kg, torch, args, local)
     kg.kg_destroy(ctx)
     if rank != 0:
         return
@@ -384,6 +386,8 @@ def run_ours(args, world, rank, local):
     }
     if sec:
         line["secondary"] = sec
+    if lsec:
+        line["learned_db"] = lsec
     print(json.dumps(line))
 
 
@@ -417,6 +421,74 @@ def secondary(kg, torch, args, local):
         out[name + "_monomer_steps_per_s"] = m.M * MD_PER_STEP * n / (e0.elapsed_time(e1) / 1e3)
         kg.kg_destroy(ctx)
     return out
+
+
+LEARNED_STAGES = [(2.0, 300, 0.0005), (2.0, 300, 0.001), (2.0, 300, 0.002), (2.0, 10 ** 15, 0.005)]
+
+
+def learned_secondary(kg, torch, args, local):
+    """400k-monomer melt in the softest stage (n = 2, where the schedule spends
+    most of its swaps): double-bridging sweeps with the paper's uniform partner
+    draw against the learned proposal (lambda = 0.1) after online training on
+    logged uniform sweeps; sweeps alternate between 50-step MD runs so both see
+    the same kind of states."""
+    import kg_inputs as KI
+    m = KI.make(4)
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=kg.KG_MIXED, seed=17,
+                       fene_qmin=FENE_QMIN)
+    s = torch.cuda.current_stream()
+    ctx = kg.kg_create(p, local, s.cuda_stream, kg.torch_allocator())
+    kg.kg_set_potential_schedule(ctx, [kg.stage(n, k, dt) for n, k, dt in LEARNED_STAGES])
+    kg.kg_load_config(ctx, 0, m.x, m.v)
+    kg.kg_step(ctx, 1200)
+    K = m.M // 20
+    lam = 0.1
+    kg.kg_mlp_log(ctx, 4_000_000)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for _ in range(6):                          # log: uniform proposal through the learned path
+        kg.kg_step(ctx, MD_PER_STEP)
+        kg.kg_db_sweep_learned_k(ctx, [K], 1.0)
+    kg.kg_mlp_set_weights(ctx, _init_weights())
+    iters, batch = 400, 2048
+    e0, e1 = ev(), ev()
+    e0.record(s)
+    loss = kg.kg_mlp_train(ctx, iters, batch, 2e-3)
+    e1.record(s)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    log(f"learned: trained {iters} x {batch} rows in {train_ms:.1f} ms, loss {loss:.4f}")
+    kg.kg_mlp_log(ctx, 0)
+    res = {"uniform": [0, 0, 0.0], "learned": [0, 0, 0.0]}
+    for _ in range(4):
+        for name in ("uniform", "learned"):
+            kg.kg_step(ctx, MD_PER_STEP)
+            torch.cuda.synchronize()
+            a, b = ev(), ev()
+            a.record(s)
+            st = kg.kg_db_sweep_k(ctx, [K]) if name == "uniform" else kg.kg_db_sweep_learned_k(ctx, [K], lam)
+            b.record(s)
+            torch.cuda.synchronize()
+            r = res[name]
+            r[0] += st.attempted
+            r[1] += st.accepted
+            r[2] += a.elapsed_time(b)
+    kg.kg_destroy(ctx)
+    out = {"workload": "cfg4: " + WORKLOADS["cfg4"]["desc"], "stage": "n = 2, k_2, dt = 0.005",
+           "attempts_per_sweep": K, "lambda": lam,
+           "train": {"iters": iters, "batch": batch, "ms": train_ms, "final_loss": loss}}
+    for name, (att, acc, ms) in res.items():
+        out[name] = {"acceptance": acc / att, "attempts_per_s": att / (ms / 1e3),
+                     "accepted_per_s": acc / (ms / 1e3), "sweep_ms": ms / 4}
+    return out
+
+
+def _init_weights(seed=0):
+    """He-style random start for the proposal network (zero biases)."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0, np.sqrt(2 / 24), (64, 24))
+    W2 = rng.normal(0, np.sqrt(2 / 64), (64, 64))
+    w3 = rng.normal(0, np.sqrt(1 / 64), 64) * 0.1
+    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [0.0]])
 
 
 def ncu_case(args):

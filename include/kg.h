@@ -223,6 +223,72 @@ kg_status kg_autotune(const kg_params *p, const double *const *x, const double *
                       const kg_stage *stage, int trial_steps, int device, void *stream,
                       const kg_allocator *allocator, kg_tuning *best);
 
+/* ---- Learned double-bridging proposal (an extension; the paper draws the
+ * swap partner uniformly, Fig. 1) ----
+ * A network of 24 move features -> 64 (ReLU) -> 64 (ReLU) -> 1 logit scores
+ * each admissible swap of the drawn bond; the partner is drawn from
+ *     pi_j = (1 - lambda) softmax_j(logits) + lambda / |P(b)|
+ * over the bond's partner list (in the list order of Fig. 1's proposal), and
+ * the swap is accepted with min(1, exp(-dE/T) q(x'->x) / q(x->x')), q summing
+ * the two ways a swap can be proposed (either removed bond drawn).  Any
+ * lambda in (0, 1] leaves the Boltzmann distribution of Sec. II.B stationary;
+ * lambda = 1 is the uniform proposal.  The network runs on bf16 tensor cores
+ * with fp32 accumulation; features, probabilities and the acceptance test are
+ * binary64.  A context starts with zero weights (the uniform proposal).
+ *
+ * Weights: KG_MLP_NPARAM binary64 values packed as W1[64][24], b1[64],
+ * W2[64][64], b2[64], w3[64], b3 (row = output unit); stored as binary32.
+ * Features of one swap (u-w the drawn bond, X-Y the partner bond, new bonds
+ * u-X and Y-w): 0-1 removed bond lengths (sorted), 2-3 new bond lengths
+ * (sorted), 4 change of the FENE terms, 5 change of the bending energy, 6-9
+ * cos at the four junction vertices before (sorted), 10-13 after, 14-17 cos
+ * one vertex further out (sorted), 18 cos between u->w and X->Y, 19 kappa/4,
+ * 20 n/12, 21 min(p+1, N-1-p)/N for the drawn bond p, 22 dE = [4] + [5], 23 1.
+ * Host pointers below are host memory; sizes are counts of rows. */
+#define KG_MLP_NPARAM 5825
+#define KG_DB_CAND_MAX 48   /* candidates one bond may have; more is KG_ERR_CAPACITY */
+
+kg_status kg_mlp_set_weights(kg_ctx *c, const double *w);   /* host, KG_MLP_NPARAM; resets Adam */
+kg_status kg_mlp_get_weights(kg_ctx *c, double *w);         /* host, KG_MLP_NPARAM (synchronises) */
+
+/* Logits of n feature rows (host, n x 24 -> n); synchronises. */
+kg_status kg_mlp_forward(kg_ctx *c, const double *features, long long n, double *logits);
+
+/* Mean binary cross-entropy of sigmoid(logit) against targets t in [0, 1]
+ * over n rows (host arrays), and its gradient with respect to the packed
+ * weights (host, KG_MLP_NPARAM); synchronises. */
+kg_status kg_mlp_loss_grad(kg_ctx *c, const double *features, const double *targets, long long n,
+                           double *loss, double *grad);
+
+/* Training log: capacity > 0 keeps the last `capacity` rows that learned
+ * sweeps log (the features of every candidate of every non-empty attempt,
+ * with target min(1, exp(-dE/T))); 0 turns logging off and frees the log. */
+kg_status kg_mlp_log(kg_ctx *c, long long capacity);
+
+/* Copy up to cap logged rows, oldest first, to host features (cap x 24) and
+ * targets (cap); *n receives the count; synchronises. */
+kg_status kg_mlp_log_read(kg_ctx *c, double *features, double *targets, long long cap, long long *n);
+
+/* iters Adam steps (lr; betas 0.9, 0.999) on minibatches of `batch` rows
+ * drawn uniformly from the log (with replacement); *loss receives the last
+ * minibatch's mean loss (may be NULL).  KG_ERR_STATE when the log is empty. */
+kg_status kg_mlp_train(kg_ctx *c, int iters, int batch, double lr, double *loss);
+
+/* As kg_db_sweep / kg_db_sweep_k with the learned proposal mixed at lambda in
+ * (0, 1].  The acceptance always includes the proposal ratio (the
+ * KG_FLAG_PAPER_METROPOLIS flag is ignored here). */
+kg_status kg_db_sweep_learned(kg_ctx *c, double attempts_per_monomer, double lambda, kg_db_stats *stats);
+kg_status kg_db_sweep_learned_k(kg_ctx *c, const long long *attempts, double lambda, kg_db_stats *stats);
+
+/* The learned proposal of one bond (chain, bond) of melt `melt` in the
+ * current state: *n candidates (0: none; their list order), their kind (0:
+ * partner bond at the same index, 1: at N-2-bond), partner chain and bond,
+ * features (n x 24), logits and probabilities pi; host arrays of
+ * KG_DB_CAND_MAX (x 24) entries; synchronises. */
+kg_status kg_db_proposal(kg_ctx *c, int melt, int chain, int bond, double lambda, int *n, int *kind,
+                         int *partner_chain, int *partner_bond, double *features, double *logits,
+                         double *prob);
+
 /* Host helpers (no context): k_n of Eq. 9, and the twelve stages of the
  * paper's schedule for (kappa, N) at time step dt (Eqs. 12, 16-20; scheme 1
  * for kappa <= 2.5), each stage's length scaled by `scale` (1: the paper's). */

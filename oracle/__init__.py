@@ -63,6 +63,7 @@ def lib():
             "orc_hist": (None, [p, p, i, p, p]),
             "orc_db_sweep": (i, [p, p, p, p, ll, ll, p]),
             "orc_db_partners": (i, [p, p, p, i, i]),
+            "orc_db_candidates": (i, [p, p, p, i, i, p, p, p, i]),
             "orc_topo_energy": (d, [p, p]),
             "orc_mlp_forward": (d, [p, p]),
             "orc_move_features": (None, [p, p, i, i, i, i, i, p]),
@@ -215,6 +216,16 @@ def db_partners(p: Params, x, pid, chain: int, bond: int) -> int:
     x = np.ascontiguousarray(x, dtype=np.float64)
     pid = np.ascontiguousarray(pid, dtype=np.int32)
     return lib().orc_db_partners(C.byref(p), _ptr(x), _ptr(pid), int(chain), int(bond))
+
+
+def db_candidates(p: Params, x, pid, chain: int, bond: int):
+    """partner list of bond (chain, bond) in proposal order: list of (kind, d, q)"""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    pid = np.ascontiguousarray(pid, dtype=np.int32)
+    cap = 2 * p.n_chains
+    k, d, q = (np.zeros(cap, dtype=np.int32) for _ in range(3))
+    n = lib().orc_db_candidates(C.byref(p), _ptr(x), _ptr(pid), int(chain), int(bond), _ptr(k), _ptr(d), _ptr(q), cap)
+    return [(int(k[j]), int(d[j]), int(q[j])) for j in range(n)]
 
 
 def topo_energy(p: Params, x) -> float:

@@ -538,6 +538,17 @@ int orc_db_partners(const orc_params *p, const double *x, const int *pid, int c,
     return enum_partners(p, x, pid, c, b, NULL);
 }
 
+int orc_db_candidates(const orc_params *p, const double *x, const int *pid, int c, int b, int *kind, int *d,
+                      int *q, int cap)
+{
+    orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * 2 * (size_t)p->n_chains * p->chain_len);
+    int n = enum_partners(p, x, pid, c, b, cand);
+    qsort(cand, (size_t)n, sizeof(orc_cand), cmp_cand);
+    for (int j = 0; j < n && j < cap; ++j) { kind[j] = cand[j].kind; d[j] = cand[j].d; q[j] = cand[j].q; }
+    free(cand);
+    return n;
+}
+
 /* FENE log terms plus bending energy of chain c */
 static double chain_topo_energy(const orc_params *p, const double *x, int c)
 {

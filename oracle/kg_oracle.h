@@ -98,6 +98,12 @@ int orc_db_sweep(const orc_params *p, double *x, double *u, int *pid,
 /* partner count |P(b)| of bond b = (chain c, index p) in the given state */
 int orc_db_partners(const orc_params *p, const double *x, const int *pid, int c, int b);
 
+/* the partner list of bond (c, b) in proposal order (by the ids of the
+ * partner monomer that bonds to (c, b) and of its bond neighbour): kind,
+ * chain and bond index of each entry, up to cap; returns |P(b)| */
+int orc_db_candidates(const orc_params *p, const double *x, const int *pid, int c, int b, int *kind, int *d,
+                      int *q, int cap);
+
 /* topology energy of the chains: sum of FENE log terms + bending (Eq. 4) */
 double orc_topo_energy(const orc_params *p, const double *x);
 

@@ -25,7 +25,12 @@ KG_FLAG_PAPER_METROPOLIS = 1
 EXPORTS = ["kg_create", "kg_load_config", "kg_get_config", "kg_set_potential_schedule", "kg_step",
            "kg_db_sweep", "kg_db_sweep_k", "kg_observables", "kg_sync", "kg_get_counters",
            "kg_set_counters", "kg_get_nlist", "kg_forces", "kg_profile", "kg_profile_read", "kg_autotune", "kg_kn", "kg_schedule_paper", "kg_destroy",
-           "kg_strerror", "kg_r2n_noalloc"]
+           "kg_strerror", "kg_r2n_noalloc", "kg_mlp_set_weights", "kg_mlp_get_weights", "kg_mlp_forward",
+           "kg_mlp_loss_grad", "kg_mlp_log", "kg_mlp_log_read", "kg_mlp_train", "kg_db_sweep_learned",
+           "kg_db_sweep_learned_k", "kg_db_proposal"]
+
+KG_MLP_NPARAM = 5825
+KG_DB_CAND_MAX = 48
 
 
 class kg_melt(C.Structure):
@@ -108,6 +113,16 @@ def load(path: str = LIB_PATH):
         "kg_destroy": (None, [p]),
         "kg_strerror": (C.c_char_p, [i]),
         "kg_r2n_noalloc": (i, [p, ll, i, i, p, p]),
+        "kg_mlp_set_weights": (i, [p, p]),
+        "kg_mlp_get_weights": (i, [p, p]),
+        "kg_mlp_forward": (i, [p, p, ll, p]),
+        "kg_mlp_loss_grad": (i, [p, p, p, ll, C.POINTER(d), p]),
+        "kg_mlp_log": (i, [p, ll]),
+        "kg_mlp_log_read": (i, [p, p, p, ll, C.POINTER(ll)]),
+        "kg_mlp_train": (i, [p, i, i, d, C.POINTER(d)]),
+        "kg_db_sweep_learned": (i, [p, d, d, C.POINTER(kg_db_stats)]),
+        "kg_db_sweep_learned_k": (i, [p, p, d, C.POINTER(kg_db_stats)]),
+        "kg_db_proposal": (i, [p, i, i, i, d, C.POINTER(i), p, p, p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,3 +312,87 @@ def make_params(melts, precision=KG_MIXED, seed=1, T=1.0, gamma=1.0, R0=1.5, l0=
 
 def stage(n_exp, n_steps, dt, k_fene=-1.0):
     return kg_stage(float(n_exp), float(k_fene), int(n_steps), float(dt))
+
+
+# ---- learned proposal ----
+
+def _host_f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        assert a.shape == shape, (a.shape, shape)
+    return a
+
+
+def kg_mlp_set_weights(ctx, w):
+    w = _host_f64(w, (KG_MLP_NPARAM,))
+    return _check(load().kg_mlp_set_weights(ctx, ptr(w)), "kg_mlp_set_weights")
+
+
+def kg_mlp_get_weights(ctx):
+    w = np.zeros(KG_MLP_NPARAM)
+    _check(load().kg_mlp_get_weights(ctx, ptr(w)), "kg_mlp_get_weights")
+    return w
+
+
+def kg_mlp_forward(ctx, features):
+    f = _host_f64(features)
+    n = f.shape[0]
+    assert f.shape == (n, 24)
+    out = np.zeros(n)
+    _check(load().kg_mlp_forward(ctx, ptr(f), n, ptr(out)), "kg_mlp_forward")
+    return out
+
+
+def kg_mlp_loss_grad(ctx, features, targets):
+    f = _host_f64(features)
+    t = _host_f64(targets, (f.shape[0],))
+    loss = C.c_double()
+    g = np.zeros(KG_MLP_NPARAM)
+    _check(load().kg_mlp_loss_grad(ctx, ptr(f), ptr(t), f.shape[0], C.byref(loss), ptr(g)), "kg_mlp_loss_grad")
+    return loss.value, g
+
+
+def kg_mlp_log(ctx, capacity):
+    return _check(load().kg_mlp_log(ctx, int(capacity)), "kg_mlp_log")
+
+
+def kg_mlp_log_read(ctx, cap):
+    f = np.zeros((max(cap, 1), 24))
+    t = np.zeros(max(cap, 1))
+    n = C.c_longlong()
+    _check(load().kg_mlp_log_read(ctx, ptr(f), ptr(t), int(cap), C.byref(n)), "kg_mlp_log_read")
+    return f[:n.value], t[:n.value]
+
+
+def kg_mlp_train(ctx, iters, batch, lr):
+    loss = C.c_double()
+    _check(load().kg_mlp_train(ctx, int(iters), int(batch), float(lr), C.byref(loss)), "kg_mlp_train")
+    return loss.value
+
+
+def kg_db_sweep_learned(ctx, attempts_per_monomer=-1.0, lam=0.1):
+    st = kg_db_stats()
+    _check(load().kg_db_sweep_learned(ctx, float(attempts_per_monomer), float(lam), C.byref(st)),
+           "kg_db_sweep_learned")
+    return st
+
+
+def kg_db_sweep_learned_k(ctx, attempts, lam=0.1):
+    a = np.ascontiguousarray(attempts, dtype=np.int64)
+    st = kg_db_stats()
+    _check(load().kg_db_sweep_learned_k(ctx, ptr(a), float(lam), C.byref(st)), "kg_db_sweep_learned_k")
+    return st
+
+
+def kg_db_proposal(ctx, melt, chain, bond, lam=0.1):
+    """dict of the bond's candidate list: kind, chain, bond, features, logits, prob."""
+    n = C.c_int()
+    cap = KG_DB_CAND_MAX
+    kind, pc, pb = (np.zeros(cap, dtype=np.int32) for _ in range(3))
+    f = np.zeros((cap, 24))
+    s, pi = np.zeros(cap), np.zeros(cap)
+    _check(load().kg_db_proposal(ctx, int(melt), int(chain), int(bond), float(lam), C.byref(n), ptr(kind),
+                                 ptr(pc), ptr(pb), ptr(f), ptr(s), ptr(pi)), "kg_db_proposal")
+    k = n.value
+    return {"n": k, "kind": kind[:k], "chain": pc[:k], "bond": pb[:k], "features": f[:k], "logits": s[:k],
+            "prob": pi[:k]}

@@ -15,6 +15,29 @@
 using kg::MeltDev;
 using kg::SimDev;
 using kg::StageDev;
+using kg::dev_alloc;
+using kg::dev_free;
+
+namespace kg {
+
+void *dev_alloc(kg_ctx *c, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (c->have_alloc) p = c->alloc.alloc(bytes, c->alloc.user);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) cudaMemsetAsync(p, 0, bytes, c->stream);
+    return p;
+}
+
+void dev_free(kg_ctx *c, void *p)
+{
+    if (!p) return;
+    if (c->have_alloc) c->alloc.free(p, c->alloc.user);
+    else cudaFree(p);
+}
+
+}  // namespace kg
 
 namespace {
 
@@ -48,23 +71,6 @@ kg_status cuda_status(cudaError_t e)
         kg_status _s = cuda_status(call);                  \
         if (_s != KG_OK) return _s;                        \
     } while (0)
-
-void *dev_alloc(kg_ctx *c, size_t bytes)
-{
-    bytes = (bytes + 255) & ~(size_t)255;
-    void *p = nullptr;
-    if (c->have_alloc) p = c->alloc.alloc(bytes, c->alloc.user);
-    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
-    if (p) cudaMemsetAsync(p, 0, bytes, c->stream);
-    return p;
-}
-
-void dev_free(kg_ctx *c, void *p)
-{
-    if (!p) return;
-    if (c->have_alloc) c->alloc.free(p, c->alloc.user);
-    else cudaFree(p);
-}
 
 // Stage parameters: U_MLJ^n = c1 r^-n - c2 r^-6 + 1 with c1 = 6 2^(n/6)/(n-6),
 // c2 = 2n/(n-6) (Eq. 5 with m = 6, shifted at r_c); FENE k_n from Eq. 9 when
@@ -368,7 +374,9 @@ void kg_destroy(kg_ctx *c)
                     c->pos64[1], c->xb, c->cellid, c->rank, c->ccount, c->cstart, c->clist, c->bsum, c->nl,
                     c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->att, c->koff, c->slot_of,
                     c->comp_of, c->bp, c->img, c->dirty, c->db_stats, c->scratch, c->flags, c->fout, c->partials,
-                    c->r2tmp, c->hist};
+                    c->r2tmp, c->hist, c->mlp_master, c->mlp_adam, c->mlp_grad, c->mlp_blob, c->mlp_w2t,
+                    c->logf, c->logt, c->logn, c->trainf, c->traint, c->d_train_head, c->tr_buf, c->bmax2,
+                    c->d_io};
     for (void *b : bufs) dev_free(c, b);
     dev_free(c, c->d_step);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -513,9 +521,10 @@ kg_status kg_step(kg_ctx *c, long long n_steps)
     return read_flags(c, h);
 }
 
-kg_status kg_db_sweep_k(kg_ctx *c, const long long *attempts, kg_db_stats *stats)
+static kg_status sweep_impl(kg_ctx *c, const long long *attempts, kg_db_stats *stats, bool learned, double lambda)
 {
     if (!c || !attempts) return KG_ERR_INVALID_ARG;
+    if (learned && !(lambda > 0.0 && lambda <= 1.0)) return KG_ERR_INVALID_ARG;
     if (c->latched != KG_OK) return KG_ERR_STATE;
     if (cudaSetDevice(c->device) != cudaSuccess) return KG_ERR_CUDA;
     const int nm = c->sim.n_melts;
@@ -532,10 +541,12 @@ kg_status kg_db_sweep_k(kg_ctx *c, const long long *attempts, kg_db_stats *stats
         c->att = dev_alloc(c, (size_t)c->att_cap * sizeof(kg::Attempt));
         if (!c->att) { c->att_cap = 0; return KG_ERR_OOM; }
     }
+    if (learned && !kg::mlp_ensure(c)) return KG_ERR_OOM;
     static thread_local long long *hstats = nullptr;
     if (!hstats && cudaMallocHost(&hstats, sizeof(long long) * 4 * kg::MAX_MELTS) != cudaSuccess) return KG_ERR_OOM;
     // the grid and the record buffers must describe the current positions
-    kg::db_sweep(c, K, hstats);
+    if (learned) kg::db_sweep_learned(c, K, lambda, hstats);
+    else kg::db_sweep(c, K, hstats);
     KG_TRY(cudaGetLastError());
     kg_status s = read_flags(c, pinned_flags());
     kg_db_stats out{0, 0, 0, 0, c->sweep};
@@ -551,9 +562,8 @@ kg_status kg_db_sweep_k(kg_ctx *c, const long long *attempts, kg_db_stats *stats
     return s;
 }
 
-kg_status kg_db_sweep(kg_ctx *c, double a, kg_db_stats *stats)
+static std::vector<long long> paper_attempts(kg_ctx *c, double a)
 {
-    if (!c) return KG_ERR_INVALID_ARG;
     const int nm = c->sim.n_melts;
     std::vector<long long> K(nm);
     for (int m = 0; m < nm; ++m) {
@@ -561,7 +571,214 @@ kg_status kg_db_sweep(kg_ctx *c, double a, kg_db_stats *stats)
         K[m] = (long long)std::floor(want);
         c->carry[m] = want - (double)K[m];
     }
+    return K;
+}
+
+kg_status kg_db_sweep_k(kg_ctx *c, const long long *attempts, kg_db_stats *stats)
+{
+    return sweep_impl(c, attempts, stats, false, 1.0);
+}
+
+kg_status kg_db_sweep(kg_ctx *c, double a, kg_db_stats *stats)
+{
+    if (!c) return KG_ERR_INVALID_ARG;
+    const std::vector<long long> K = paper_attempts(c, a);
     return kg_db_sweep_k(c, K.data(), stats);
+}
+
+kg_status kg_db_sweep_learned_k(kg_ctx *c, const long long *attempts, double lambda, kg_db_stats *stats)
+{
+    return sweep_impl(c, attempts, stats, true, lambda);
+}
+
+kg_status kg_db_sweep_learned(kg_ctx *c, double a, double lambda, kg_db_stats *stats)
+{
+    if (!c) return KG_ERR_INVALID_ARG;
+    if (!(lambda > 0.0 && lambda <= 1.0)) return KG_ERR_INVALID_ARG;
+    const std::vector<long long> K = paper_attempts(c, a);
+    return kg_db_sweep_learned_k(c, K.data(), lambda, stats);
+}
+
+// ---- learned proposal: weights, log, training ----
+
+static double *io_buffer(kg_ctx *c, long long n)
+{
+    if (n <= c->d_io_cap) return c->d_io;
+    dev_free(c, c->d_io);
+    c->d_io_cap = std::max(n, 2 * c->d_io_cap);
+    c->d_io = (double *)dev_alloc(c, sizeof(double) * (size_t)c->d_io_cap);
+    if (!c->d_io) c->d_io_cap = 0;
+    return c->d_io;
+}
+
+static kg_status mlp_begin(kg_ctx *c)
+{
+    if (!c) return KG_ERR_INVALID_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return KG_ERR_CUDA;
+    return kg::mlp_ensure(c) ? KG_OK : KG_ERR_OOM;
+}
+
+kg_status kg_mlp_set_weights(kg_ctx *c, const double *w)
+{
+    kg_status s = mlp_begin(c);
+    if (s != KG_OK) return s;
+    if (!w) return KG_ERR_INVALID_ARG;
+    for (int i = 0; i < KG_MLP_NPARAM; ++i)
+        if (!std::isfinite(w[i])) return KG_ERR_INVALID_ARG;
+    double *d = io_buffer(c, KG_MLP_NPARAM);
+    if (!d) return KG_ERR_OOM;
+    KG_TRY(cudaMemcpyAsync(d, w, sizeof(double) * KG_MLP_NPARAM, cudaMemcpyHostToDevice, c->stream));
+    kg::mlp_set(c, d);
+    KG_TRY(cudaGetLastError());
+    return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+kg_status kg_mlp_get_weights(kg_ctx *c, double *w)
+{
+    kg_status s = mlp_begin(c);
+    if (s != KG_OK) return s;
+    if (!w) return KG_ERR_INVALID_ARG;
+    double *d = io_buffer(c, KG_MLP_NPARAM);
+    if (!d) return KG_ERR_OOM;
+    kg::mlp_get(c, d);
+    KG_TRY(cudaMemcpyAsync(w, d, sizeof(double) * KG_MLP_NPARAM, cudaMemcpyDeviceToHost, c->stream));
+    return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+kg_status kg_mlp_forward(kg_ctx *c, const double *features, long long n, double *logits)
+{
+    kg_status s = mlp_begin(c);
+    if (s != KG_OK) return s;
+    if (n < 0 || (n > 0 && (!features || !logits)) || n > (1LL << 30)) return KG_ERR_INVALID_ARG;
+    if (n == 0) return KG_OK;
+    double *d = io_buffer(c, 25 * n);
+    if (!d) return KG_ERR_OOM;
+    KG_TRY(cudaMemcpyAsync(d, features, sizeof(double) * 24 * n, cudaMemcpyHostToDevice, c->stream));
+    kg::mlp_infer(c, d, n, d + 24 * n);
+    KG_TRY(cudaGetLastError());
+    KG_TRY(cudaMemcpyAsync(logits, d + 24 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+kg_status kg_mlp_loss_grad(kg_ctx *c, const double *features, const double *targets, long long n, double *loss,
+                           double *grad)
+{
+    kg_status s = mlp_begin(c);
+    if (s != KG_OK) return s;
+    if (n <= 0 || n > (1LL << 24) || !features || !targets) return KG_ERR_INVALID_ARG;
+    double *d = io_buffer(c, 25 * n + KG_MLP_NPARAM + 1);
+    if (!d) return KG_ERR_OOM;
+    KG_TRY(cudaMemcpyAsync(d, features, sizeof(double) * 24 * n, cudaMemcpyHostToDevice, c->stream));
+    KG_TRY(cudaMemcpyAsync(d + 24 * n, targets, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    double *out = d + 25 * n;
+    if (!kg::mlp_grad(c, d, d + 24 * n, n, out)) return KG_ERR_OOM;
+    KG_TRY(cudaGetLastError());
+    std::vector<double> h(KG_MLP_NPARAM + 1);
+    KG_TRY(cudaMemcpyAsync(h.data(), out, sizeof(double) * (KG_MLP_NPARAM + 1), cudaMemcpyDeviceToHost, c->stream));
+    KG_TRY(cudaStreamSynchronize(c->stream));
+    if (loss) *loss = h[0];
+    if (grad) std::copy(h.begin() + 1, h.end(), grad);
+    return KG_OK;
+}
+
+kg_status kg_mlp_log(kg_ctx *c, long long capacity)
+{
+    kg_status s = mlp_begin(c);
+    if (s != KG_OK) return s;
+    if (capacity < 0 || capacity > (1LL << 32)) return KG_ERR_INVALID_ARG;
+    KG_TRY(cudaStreamSynchronize(c->stream));
+    dev_free(c, c->trainf);
+    dev_free(c, c->traint);
+    dev_free(c, c->d_train_head);
+    c->trainf = c->traint = nullptr;
+    c->d_train_head = nullptr;
+    c->train_cap = 0;
+    if (capacity == 0) return KG_OK;
+    c->trainf = (double *)dev_alloc(c, sizeof(double) * 24 * (size_t)capacity);
+    c->traint = (double *)dev_alloc(c, sizeof(double) * (size_t)capacity);
+    c->d_train_head = (long long *)dev_alloc(c, sizeof(long long));
+    if (!c->trainf || !c->traint || !c->d_train_head) {
+        dev_free(c, c->trainf);
+        dev_free(c, c->traint);
+        dev_free(c, c->d_train_head);
+        c->trainf = c->traint = nullptr;
+        c->d_train_head = nullptr;
+        return KG_ERR_OOM;
+    }
+    c->train_cap = capacity;
+    return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+static kg_status train_rows(kg_ctx *c, long long *head)
+{
+    *head = 0;
+    if (c->train_cap <= 0) return KG_OK;
+    KG_TRY(cudaMemcpyAsync(head, c->d_train_head, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+kg_status kg_mlp_log_read(kg_ctx *c, double *features, double *targets, long long cap, long long *n)
+{
+    kg_status s = mlp_begin(c);
+    if (s != KG_OK) return s;
+    if (cap < 0 || !n || (cap > 0 && (!features || !targets))) return KG_ERR_INVALID_ARG;
+    long long head = 0;
+    if ((s = train_rows(c, &head)) != KG_OK) return s;
+    const long long avail = std::min(head, c->train_cap), take = std::min(avail, cap);
+    const long long first = head - avail;
+    for (long long done = 0; done < take;) {            // at most two contiguous pieces of the ring
+        const long long r = (first + done) % c->train_cap;
+        const long long len = std::min(take - done, c->train_cap - r);
+        KG_TRY(cudaMemcpyAsync(features + 24 * done, c->trainf + 24 * r, sizeof(double) * 24 * len,
+                               cudaMemcpyDeviceToHost, c->stream));
+        KG_TRY(cudaMemcpyAsync(targets + done, c->traint + r, sizeof(double) * len, cudaMemcpyDeviceToHost,
+                               c->stream));
+        done += len;
+    }
+    KG_TRY(cudaStreamSynchronize(c->stream));
+    *n = take;
+    return KG_OK;
+}
+
+kg_status kg_mlp_train(kg_ctx *c, int iters, int batch, double lr, double *loss)
+{
+    kg_status s = mlp_begin(c);
+    if (s != KG_OK) return s;
+    if (iters < 0 || batch < 1 || batch > (1 << 20) || !(lr >= 0.0) || !std::isfinite(lr)) return KG_ERR_INVALID_ARG;
+    long long head = 0;
+    if ((s = train_rows(c, &head)) != KG_OK) return s;
+    if (head <= 0) return KG_ERR_STATE;
+    double *d = io_buffer(c, 1);
+    if (!d) return KG_ERR_OOM;
+    if (!kg::mlp_train(c, iters, batch, lr, d)) return KG_ERR_OOM;
+    KG_TRY(cudaGetLastError());
+    double h = 0.0;
+    KG_TRY(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    KG_TRY(cudaStreamSynchronize(c->stream));
+    if (loss) *loss = h;
+    return KG_OK;
+}
+
+kg_status kg_db_proposal(kg_ctx *c, int melt, int chain, int bond, double lambda, int *n, int *kind,
+                         int *partner_chain, int *partner_bond, double *features, double *logits, double *prob)
+{
+    kg_status s = check_melt(c, melt);
+    if (s != KG_OK) return s;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    const MeltDev &md = c->sim.melt[melt];
+    if (chain < 0 || chain >= md.n_ch || bond < 0 || bond > md.N - 2 || !(lambda > 0.0 && lambda <= 1.0) || !n ||
+        !kind || !partner_chain || !partner_bond || !features || !logits || !prob)
+        return KG_ERR_INVALID_ARG;
+    if (!kg::mlp_ensure(c)) return KG_ERR_OOM;
+    std::vector<int> ints(3 * KG_DB_CAND_MAX);
+    if (!kg::db_proposal(c, melt, chain, bond, lambda, n, ints.data(), features, logits, prob)) return KG_ERR_CUDA;
+    if ((s = read_flags(c, pinned_flags())) != KG_OK) return s;
+    for (int j = 0; j < *n; ++j) {
+        kind[j] = ints[j];
+        partner_chain[j] = ints[KG_DB_CAND_MAX + j];
+        partner_bond[j] = ints[2 * KG_DB_CAND_MAX + j];
+    }
+    return KG_OK;
 }
 
 kg_status kg_sync(kg_ctx *c)

@@ -30,135 +30,9 @@
 //      monomer data moves (the maps are the topology).
 #include <cuda_runtime.h>
 
-#include "kg_host.h"
+#include "kg_db.cuh"
 
 namespace kg {
-
-constexpr int CAND_CAP = 48;
-constexpr int JCAP = 4096;
-
-struct Cand {
-    int key, key2, kind, d, q;
-};
-
-struct DBC {
-    const double *__restrict__ x;
-    int Mp;
-    const int *__restrict__ pid;
-    const int *__restrict__ cell;
-    const int *__restrict__ start;
-    const int *__restrict__ list;
-    MeltDev md;
-    int melt;
-    double lim2, kfene, R0, T, qmin;
-};
-
-// topology view: slot -> monomer (occ) and monomer -> slot (cur)
-struct ViewMap {
-    const int *o;
-    const int *c;
-    __device__ __forceinline__ int occ(int s) const { return o[s]; }
-    __device__ __forceinline__ int cur(int p) const { return c[p]; }
-};
-
-// Slot relabelling of one swap; the same map takes x -> x' and x' -> x.
-__device__ __forceinline__ int swap_slot(int s, int kind, int A, int B, int pA, int pB, int N, int off)
-{
-    const int r = s - off, ch = r / N, i = r - ch * N;
-    if (kind == 0) {
-        if (i > pA) {
-            if (ch == A) return off + B * N + i;
-            if (ch == B) return off + A * N + i;
-        }
-    } else {
-        if (ch == A && i > pA) return off + B * N + (N - 1 - i);
-        if (ch == B && i <= pB) return off + A * N + (N - 1 - i);
-    }
-    return s;
-}
-
-template <class V>
-struct ViewMove {
-    V b;
-    int kind, A, B, pA, pB, N, off;
-    __device__ __forceinline__ int occ(int s) const { return b.occ(swap_slot(s, kind, A, B, pA, pB, N, off)); }
-    __device__ __forceinline__ int cur(int p) const { return swap_slot(b.cur(p), kind, A, B, pA, pB, N, off); }
-};
-
-__device__ __forceinline__ double d2(const DBC &C, int a, int b) { return dist2_exact(C.x, C.Mp, C.md.L, a, b); }
-
-// |P(b)| for bond (chain c, index b) in view v; fills `out` (<= CAND_CAP) if given.
-template <class V>
-__device__ int count_partners(const DBC &C, const V &v, int c, int b, Cand *out)
-{
-    const MeltDev &md = C.md;
-    const int N = md.N;
-    const int us = md.off + c * N + b;
-    const int pu = v.occ(us), pw = v.occ(us + 1);
-    if (d2(C, pu, pw) > C.lim2) return 0;
-    const int n = md.ndb, c0 = C.cell[pu] - md.dbcell_off;
-    const int cx = c0 % n, cy = (c0 / n) % n, cz = c0 / (n * n);
-    int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int cell = md.dbcell_off + (((cz + dz + n) % n) * n + (cy + dy + n) % n) * n + (cx + dx + n) % n;
-                const int b0 = C.start[cell], e = C.start[cell + 1];
-                if (e - b0 > MAX_CELL_OCC) return -1;                  // caller reports capacity
-                for (int k = b0; k < e; ++k) {
-                    const int t = C.list[k];
-                    const int ts = v.cur(t), r = ts - md.off, d = r / N, i = r - d * N;
-                    if (d == c) continue;
-                    if (d2(C, pu, t) > C.lim2) continue;
-                    if (i == b + 1) {                          // kind 0: t = D_{b+1}
-                        const int up = v.occ(md.off + d * N + b);
-                        if (d2(C, up, pw) <= C.lim2 && d2(C, up, t) <= C.lim2) {
-                            if (out && cnt < CAND_CAP) out[cnt] = Cand{C.pid[t], C.pid[up], 0, d, b};
-                            ++cnt;
-                        }
-                    }
-                    if (i == N - 2 - b) {                      // kind 1: t = D_q, q = N-2-b
-                        const int t1 = v.occ(ts + 1);
-                        if (d2(C, t1, pw) <= C.lim2 && d2(C, t, t1) <= C.lim2) {
-                            if (out && cnt < CAND_CAP) out[cnt] = Cand{C.pid[t], C.pid[t1], 1, d, i};
-                            ++cnt;
-                        }
-                    }
-                }
-            }
-    return cnt;
-}
-
-template <class V>
-__device__ double bond_fene(const DBC &C, const V &v, int chain, int idx)
-{
-    const int s = C.md.off + chain * C.md.N + idx;
-    const double r = sqrt(d2(C, v.occ(s), v.occ(s + 1)));
-    const double q = 1.0 - (r / C.R0) * (r / C.R0);
-    if (C.qmin > 0.0 && q < C.qmin)           // continuation beyond r* (kg_params.fene_qmin)
-        return -0.5 * C.kfene * C.R0 * C.R0 * log(C.qmin) + C.kfene * (r * r - (1.0 - C.qmin) * C.R0 * C.R0) / (2.0 * C.qmin);
-    return -0.5 * C.kfene * C.R0 * C.R0 * log(q);
-}
-
-template <class V>
-__device__ double bend(const DBC &C, const V &v, int chain, int i)
-{
-    const int N = C.md.N;
-    if (i < 1 || i > N - 2) return 0.0;
-    const int s = C.md.off + chain * N + i;
-    const int a = v.occ(s - 1), b = v.occ(s), c = v.occ(s + 1);
-    const double L = C.md.L;
-    double b1[3], b2[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        b1[k] = min_image_exact(C.x[k * C.Mp + b] - C.x[k * C.Mp + a], L);
-        b2[k] = min_image_exact(C.x[k * C.Mp + c] - C.x[k * C.Mp + b], L);
-    }
-    const double cs = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2])
-                      / (sqrt(b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2])
-                         * sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]));
-    return C.md.kappa * (1.0 - cs);
-}
 
 template <class V>
 __device__ Attempt evaluate(const DBC &C, const V &v, unsigned long long seed, long long sweep, int k,
@@ -217,16 +91,6 @@ __device__ Attempt evaluate(const DBC &C, const V &v, unsigned long long seed, l
     return a;
 }
 
-__device__ __forceinline__ DBC make_dbc(const SimDev &S, const StageDev &st, int m, const double *x,
-                                        const int *pid, const int *cell, const int *start, const int *list,
-                                        double T)
-{
-    DBC C;
-    C.x = x; C.Mp = S.Mp; C.pid = pid; C.cell = cell; C.start = start; C.list = list;
-    C.md = S.melt[m]; C.melt = m; C.lim2 = S.db_lim2; C.kfene = st.kfene; C.R0 = sqrt(st.R0sq); C.T = T; C.qmin = st.qmin;
-    return C;
-}
-
 __global__ void __launch_bounds__(128) k_db_eval(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
                                                 const double *__restrict__ x, const int *__restrict__ pid,
                                                 const int *__restrict__ cell, const int *__restrict__ start,
@@ -246,17 +110,23 @@ __global__ void __launch_bounds__(128) k_db_eval(const SimDev *__restrict__ Sp, 
     if (err) atomicOr(flags, err);
 }
 
-__device__ __forceinline__ bool cells_near(int a, int b, int off, int n)
-{
-    a -= off; b -= off;
-    const int ax = a % n, ay = (a / n) % n, az = a / (n * n);
-    const int bx = b % n, by = (b / n) % n, bz = b / (n * n);
-    int dx = abs(ax - bx), dy = abs(ay - by), dz = abs(az - bz);
-    dx = min(dx, n - dx); dy = min(dy, n - dy); dz = min(dz, n - dz);
-    return dx <= 1 && dy <= 1 && dz <= 1;
-}
+// uniform proposal: thread 0 re-evaluates, junction cells within one cell
+struct UniformPolicy {
+    int paper;
+    __device__ void init() {}
+    __device__ int radius(const MeltDev &) const { return 1; }
+    __device__ void reeval(const DBC &C, const ViewMap &V, const SimDev &S, long long sweep, int kk, int,
+                           Attempt &out, unsigned *flags)
+    {
+        if (threadIdx.x == 0) {
+            unsigned err = 0;
+            out = evaluate(C, V, S.seed, sweep, kk, paper, err);
+            if (err) atomicOr(flags, err);
+        }
+    }
+    __device__ void after(const Attempt &, int) {}
+};
 
-// One block per melt: ordered validation and commit.
 __global__ void __launch_bounds__(256) k_db_commit(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
                                                   const double *__restrict__ x, const int *__restrict__ pid,
                                                   const int *__restrict__ cell, const int *__restrict__ start,
@@ -267,113 +137,9 @@ __global__ void __launch_bounds__(256) k_db_commit(const SimDev *__restrict__ Sp
                                                   long long sweep, unsigned *flags)
 {
     extern __shared__ int old_occ[];              // 2N ints
-    __shared__ int jcell[JCAP];
-    __shared__ int njc;
-    __shared__ Attempt a_s;
-    __shared__ int need_s, sh[6];
-    __shared__ long long n_acc, n_empty, n_re;
-    const SimDev &S = *Sp;
-    const int m = blockIdx.x;
-    if (flags[0]) {                                // a latched error stops the sweep
-        if (threadIdx.x == 0) for (int k = 0; k < 4; ++k) stats[4 * m + k] = 0;
-        return;
-    }
-    const MeltDev &md = S.melt[m];
-    const int N = md.N, off = md.off, Mp = S.Mp, tid = threadIdx.x;
-    const DBC C = make_dbc(S, *stp, m, x, pid, cell, start, list, stp->T);
-    const ViewMap V{occ, curmap};
-    if (tid == 0) { njc = 0; n_acc = n_empty = n_re = 0; }
-    __syncthreads();
-    const int k0 = koff[m], K = koff[m + 1] - k0;
-    for (int kk = 0; kk < K; ++kk) {
-        if (tid == 0) {
-            a_s = att[k0 + kk];
-            need_s = dirty[off + a_s.c * N] || ((a_s.flags & 1) && dirty[off + a_s.d * N]) || njc > JCAP - 4;
-        }
-        __syncthreads();
-        bool near = false;
-        if (!need_s) {
-            const int nj = njc;
-            for (int j = tid; j < nj; j += blockDim.x) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int p = a_s.jp[q];
-                    if (p >= 0 && cells_near(jcell[j], cell[p], md.dbcell_off, md.ndb)) near = true;
-                }
-            }
-        }
-        const bool need = __syncthreads_or(near || need_s);
-        if (need && tid == 0) {
-            unsigned err = 0;
-            a_s = evaluate(C, V, S.seed, sweep, kk, S.paper_metropolis, err);
-            if (err) atomicOr(flags, err);
-            ++n_re;
-        }
-        __syncthreads();
-        if (!(a_s.flags & 1)) {
-            if (tid == 0) ++n_empty;
-        } else if (a_s.flags & 2) {
-            const int kind = a_s.kind, A = a_s.A, B = a_s.B, pA = a_s.pA, pB = a_s.pB;
-            const int baseA = off + A * N, baseB = off + B * N;
-            for (int i = tid; i < N; i += blockDim.x) {
-                old_occ[i] = occ[baseA + i];
-                old_occ[N + i] = occ[baseB + i];
-            }
-            __syncthreads();
-            for (int i = tid; i < 2 * N; i += blockDim.x) {
-                const int s = i < N ? baseA + i : baseB + (i - N);
-                const int src = swap_slot(s, kind, A, B, pA, pB, N, off);
-                const int val = src - baseA < N && src >= baseA ? old_occ[src - baseA] : old_occ[N + src - baseB];
-                occ[s] = val;
-                curmap[val] = s;
-            }
-            __syncthreads();
-            if (tid < 2) {
-                // segment 0: A' slots pA+1..N-1 anchored at A' slot pA;
-                // segment 1: kind 0 -> B' slots pA+1..N-1 at pA; kind 1 -> B' slots 0..pB at pB+1
-                int f, an;
-                if (tid == 0) { f = occ[baseA + pA + 1]; an = occ[baseA + pA]; }
-                else if (kind == 0) { f = occ[baseB + pA + 1]; an = occ[baseB + pA]; }
-                else { f = occ[baseB + pB]; an = occ[baseB + pB + 1]; }
-#pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    sh[3 * tid + d] = -((int)rint(__ddiv_rn(__dsub_rn(x[d * Mp + f], x[d * Mp + an]), md.L))
-                                        + img[d * Mp + f] - img[d * Mp + an]);
-            }
-            __syncthreads();
-            for (int i = tid; i < 2 * N; i += blockDim.x) {
-                int seg = -1, s;
-                if (i < N) {
-                    s = baseA + i;
-                    if (i > pA) seg = 0;
-                } else {
-                    const int j = i - N;
-                    s = baseB + j;
-                    if ((kind == 0 && j > pA) || (kind == 1 && j <= pB)) seg = 1;
-                }
-                if (seg >= 0) {
-                    const int p = occ[s];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) img[d * Mp + p] += sh[3 * seg + d];
-                }
-            }
-            if (tid == 0) {
-                dirty[baseA] = 1;
-                dirty[baseB] = 1;
-                for (int q = 0; q < 4; ++q)
-                    if (a_s.jp[q] >= 0 && njc < JCAP) jcell[njc++] = cell[a_s.jp[q]];
-                ++n_acc;
-            }
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        stats[4 * m + 0] = K;
-        stats[4 * m + 1] = n_empty;
-        stats[4 * m + 2] = n_acc;
-        stats[4 * m + 3] = n_re;
-        if (n_acc) atomicOr(flags + 1, 1u);
-    }
+    UniformPolicy pol{Sp->paper_metropolis};
+    db_commit_body(pol, *Sp, *stp, x, pid, cell, start, list, koff, att, occ, curmap, img, dirty, stats, sweep,
+                   flags, old_occ);
 }
 
 // end of a sweep: box shifts into the positions (x + L*img, as one rounding of
@@ -410,15 +176,15 @@ __global__ void k_scatter(const int *__restrict__ cellid, const int *__restrict_
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
-void db_sweep(kg_ctx *c, const std::vector<long long> &K, long long *host_stats)
+void db_bin(kg_ctx *c, const std::vector<long long> &K)
 {
     cudaStream_t st = c->stream;
     const int nm = c->sim.n_melts;
-    c->launches += 7;
+    c->launches += 5;
     std::vector<int> koff(nm + 1, 0);
     for (int m = 0; m < nm; ++m) koff[m + 1] = koff[m] + (int)K[m];
     cudaMemcpyAsync(c->koff, koff.data(), sizeof(int) * (nm + 1), cudaMemcpyHostToDevice, st);
-    // 1. grid of >= 1.3 sigma cells
+    // grid of >= 1.3 sigma cells
     cudaMemsetAsync(c->dbcount, 0, sizeof(int) * c->ncell_db, st);
     k_bin_db<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->dbcell, c->dbrank, c->dbcount, c->slot_of);
     const int nb = nblk(c->ncell_db, 1024);
@@ -426,23 +192,44 @@ void db_sweep(kg_ctx *c, const std::vector<long long> &K, long long *host_stats)
     k_scan2<<<nb, 1024, 0, st>>>(c->dbstart, c->bsum, c->ncell_db, nb, nullptr);
     k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->dbcell, c->dbrank, c->dbstart, c->dblist, c->M, nullptr,
                                                nullptr, nullptr);
-    // 2. speculative evaluation
-    Attempt *att = (Attempt *)c->att;
-    if (koff[nm] > 0)
-        k_db_eval<<<nblk(koff[nm], 128), 128, 0, st>>>(c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart,
-                                                       c->dblist, c->koff, c->comp_of, c->slot_of, att, c->sweep,
-                                                       c->flags);
-    // 3. ordered commit, one block per melt
-    int maxN = 0;
-    for (int m = 0; m < nm; ++m) maxN = maxN > c->sim.melt[m].N ? maxN : c->sim.melt[m].N;
-    k_db_commit<<<nm, 256, sizeof(int) * 2 * maxN, st>>>(c->d_sim, c->d_stage, c->x, c->pid, c->dbcell,
-                                                          c->dbstart, c->dblist, c->koff, att, c->comp_of,
-                                                          c->slot_of, c->img, c->dirty, c->db_stats, c->sweep,
-                                                          c->flags);
-    // 4. box shifts into the positions; chain partners follow the new maps
+}
+
+void db_finish(kg_ctx *c, long long *host_stats)
+{
+    cudaStream_t st = c->stream;
+    c->launches += 1;
+    // box shifts into the positions; chain partners follow the new maps
     k_db_finish<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->slot_of, c->img, c->dirty);
     bonded_partners(c);
-    cudaMemcpyAsync(host_stats, c->db_stats, sizeof(long long) * 4 * nm, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(host_stats, c->db_stats, sizeof(long long) * 4 * c->sim.n_melts, cudaMemcpyDeviceToHost, st);
+}
+
+int db_max_chain_len(const kg_ctx *c)
+{
+    int maxN = 0;
+    for (int m = 0; m < c->sim.n_melts; ++m) maxN = maxN > c->sim.melt[m].N ? maxN : c->sim.melt[m].N;
+    return maxN;
+}
+
+void db_sweep(kg_ctx *c, const std::vector<long long> &K, long long *host_stats)
+{
+    cudaStream_t st = c->stream;
+    const int nm = c->sim.n_melts;
+    long long tot = 0;
+    for (long long k : K) tot += k;
+    db_bin(c, K);
+    // speculative evaluation
+    Attempt *att = (Attempt *)c->att;
+    if (tot > 0)
+        k_db_eval<<<nblk(tot, 128), 128, 0, st>>>(c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart,
+                                                  c->dblist, c->koff, c->comp_of, c->slot_of, att, c->sweep,
+                                                  c->flags);
+    // ordered commit, one block per melt
+    k_db_commit<<<nm, 256, sizeof(int) * 2 * db_max_chain_len(c), st>>>(
+        c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart, c->dblist, c->koff, att, c->comp_of, c->slot_of,
+        c->img, c->dirty, c->db_stats, c->sweep, c->flags);
+    c->launches += 2;
+    db_finish(c, host_stats);
 }
 
 }  // namespace kg

@@ -74,6 +74,26 @@ struct kg_ctx {
     int *img = nullptr, *dirty = nullptr;
     long long *db_stats = nullptr;   // [n_melts][4]
 
+    // learned proposal (kg_mlp.cu, kg_learned.cu)
+    float *mlp_master = nullptr;         // binary32 master weights [KG_MLP_NPARAM]
+    float *mlp_adam = nullptr;           // Adam moments m, v [2][KG_MLP_NPARAM]
+    float *mlp_grad = nullptr;           // gradient + loss [KG_MLP_NPARAM + 1]
+    void *mlp_blob = nullptr;            // bf16 image (kg::MlpSmem) for the tensor cores
+    void *mlp_w2t = nullptr;             // bf16 W2 transposed, [64][72] (backward)
+    long long adam_t = 0;                // Adam steps taken
+    long long train_iter = 0;            // minibatches drawn
+    double *logf = nullptr, *logt = nullptr;   // per-attempt staging of the sweep log
+    int *logn = nullptr;
+    long long log_att_cap = 0;
+    double *trainf = nullptr, *traint = nullptr;  // training ring [train_cap][24], [train_cap]
+    long long train_cap = 0;
+    long long *d_train_head = nullptr;   // rows ever appended
+    void *tr_buf = nullptr;              // minibatch work arrays
+    long long tr_rows = 0;
+    unsigned long long *bmax2 = nullptr; // longest bond squared (binary64 bits), per learned sweep
+    double *d_io = nullptr;              // device staging for host-pointer calls
+    long long d_io_cap = 0;
+
     // scratch
     double *scratch = nullptr;   // [3][Mp] doubles + [3][Mp] + [Mp] ints (gather / staging)
     unsigned *flags = nullptr;   // [0] error bits, [1] rebuild request, [3] max list length, [4] blocks done,
@@ -96,6 +116,10 @@ struct kg_ctx {
 };
 
 namespace kg {
+
+// device memory through the context's allocator (zero-filled on the context's stream)
+void *dev_alloc(kg_ctx *c, size_t bytes);
+void dev_free(kg_ctx *c, void *p);
 
 constexpr int GRAPH_STEPS = 10;          // MD steps per captured graph (even)
 
@@ -122,6 +146,22 @@ int forces_blocks(const kg_ctx *c, int melt);
 
 // kg_db.cu
 void db_sweep(kg_ctx *c, const std::vector<long long> &K, long long *host_stats /*[n_melts][4]*/);
+void db_bin(kg_ctx *c, const std::vector<long long> &K);     // attempt offsets + the >= 1.3 sigma grid
+void db_finish(kg_ctx *c, long long *host_stats);             // box shifts, chain partners, stats to host
+int db_max_chain_len(const kg_ctx *c);
+
+// kg_learned.cu
+void db_sweep_learned(kg_ctx *c, const std::vector<long long> &K, double lambda, long long *host_stats);
+bool db_proposal(kg_ctx *c, int melt, int chain, int bond, double lambda, int *h_n, int *h_ints /*[3][48]*/,
+                 double *h_f /*[48][24]*/, double *h_s /*[48]*/, double *h_pi /*[48]*/);
+
+// kg_mlp.cu
+bool mlp_ensure(kg_ctx *c);                                  // allocate; zero weights on first use
+void mlp_set(kg_ctx *c, const double *w_dev);                // FP64 device vector -> master + bf16 image
+void mlp_get(kg_ctx *c, double *w_dev);                      // master -> FP64 device vector
+void mlp_infer(kg_ctx *c, const double *f_dev, long long n, double *s_dev);
+bool mlp_grad(kg_ctx *c, const double *f_dev, const double *t_dev, long long n, double *loss_grad_dev);
+bool mlp_train(kg_ctx *c, int iters, int batch, double lr, double *loss_dev);
 
 // kg_obs.cu
 void r2n_eval(kg_ctx *c, int melt, double *out_dev);

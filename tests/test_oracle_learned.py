@@ -266,3 +266,16 @@ def test_learned_sweep_bf16_inputs():
     (att, empty, acc), _, _ = O.db_sweep_learned(p, x, u, pid, 0, 400, mlp.sparse_dyadic(2), 0.1,
                                                  bf16_inputs=True)
     assert att == 400 and acc > 0
+
+
+def test_candidate_list_matches_enumeration():
+    m, nch, N, P, states = _pick_tiny()
+    p = O.params(nch, N, m.box, 0.5, n_exp=2.0)
+    for s in sorted(states)[:10]:
+        x = np.ascontiguousarray(P[list(s)].T)
+        pid = np.array(s, dtype=np.int32)
+        for c in range(nch):
+            for b in range(N - 1):
+                got = O.db_candidates(p, x, pid, c, b)
+                assert sorted(got) == sorted(_moves_of_bond(s, P, m.box, nch, N, c, b))
+                assert len(got) == O.db_partners(p, x, pid, c, b)
