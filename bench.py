@@ -41,13 +41,19 @@ _T0 = time.time()
 def log(msg):
     """Timestamped progress on stderr (the JSON line alone goes to stdout)."""
     print(f"[bench {time.time() - _T0:8.2f}s] {msg}", file=sys.stderr, flush=True)
-# algorithmic HBM bytes per monomer per launch of the fused step kernel:
-# x r+w 48, u r+w 24 (f32) / 48 (f64), own record 16, displacement r+w 32 (mixed)
-# or gather copy r+w 64 + build position 32 (f64), list length 4, Verlet list
-# 4 * 10.25 (rho (4 pi/3)(r_c + skin)^3 neighbours at rho = 0.85, skin 0.3)
-NB_MEAN = 0.85 * 4.0 / 3.0 * np.pi * (2 ** (1 / 6) + 0.3) ** 3
-BYTES_PER_MONOMER = {"mixed": 48 + 24 + 16 + 32 + 4 + 4 * NB_MEAN,
-                     "fp64": 48 + 48 + 64 + 32 + 4 + 4 * NB_MEAN}
+# algorithmic HBM bytes per monomer per launch of the fused step kernel (the
+# per-monomer model of the hot-path scope table): x r+w 48, v r+w 24 (f32) /
+# 48 (f64), the binary32 gather mirror written and read once 32 (f64: a
+# binary64 mirror, 64), and the Verlet list, 4 bytes per neighbour with
+# rho (4 pi / 3)(r_c + skin)^3 neighbours at the skin in use.
+def nb_mean(skin):
+    return 0.85 * 4.0 / 3.0 * np.pi * (2 ** (1 / 6) + skin) ** 3
+
+
+def bytes_per_monomer(precision, skin):
+    return (48 + 24 + 32 if precision == "mixed" else 48 + 48 + 64) + 4 * nb_mean(skin)
+
+
 # DRAM bytes per monomer of the mixed step kernel from an ncu capture, and the
 # hash of kg_md.cu they were taken on (reported as null once the source changes)
 NCU_TRAFFIC = {"bytes_per_monomer": None, "kg_md_sha1": None}
@@ -347,7 +353,8 @@ def run_ours(args, world, rank, local):
     if rank != 0:
         return
     avg_ms = step_ms / max(n_launch, 1)
-    bpm = BYTES_PER_MONOMER[args.precision]
+    run_skin = tuning["skin"] if tuning else args.skin
+    bpm = bytes_per_monomer(args.precision, run_skin)
     achieved = bpm * m.M / (avg_ms * 1e-3) / 1e9
     peak, src = peaks()
     traffic = None

@@ -93,6 +93,7 @@ StageDev make_stage(const kg_params &p, const kg_stage &s)
     d.T = p.T;
     d.amp = p.gamma > 0 ? std::sqrt(2.0 * p.gamma * p.T / s.dt) : 0.0;
     d.nf = (float)n; d.c1f = (float)d.c1; d.c2f = (float)d.c2; d.kfenef = (float)d.kfene;
+    d.c2x6f = (float)(6.0 * d.c2); d.c1xnf = (float)(n * d.c1);
     d.R0sqf = (float)d.R0sq; d.dtf = (float)d.dt; d.gammaf = (float)d.gamma; d.ampf = (float)d.amp;
     const double rn = std::nearbyint(n);
     if (std::fabs(n - rn) < 1e-12 && rn >= 1 && rn <= 64) { d.nkind = 1; d.nint = (int)rn; }
@@ -261,17 +262,19 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
         if (md.nc < 3 || md.ndb < 3) return fail(KG_ERR_INVALID_ARG);
         md.h = ml.box / md.nc; md.invh = 1.0 / md.h;
         md.nbk = (md.nc + 3) / 4;
-        {   // binary32 wrapped-position prefilter: per-component error <= 4 L 2^-24
-            const double dd = std::sqrt(3.0) * 4.0 * ml.box * std::ldexp(1.0, -24);
-            const double band = 2.0 * (2.0 * rl * dd + dd * dd + 1e-6 * rl * rl);
-            md.nl_lo = (float)(rl * rl - band);
-            md.nl_hi = (float)(rl * rl + band);
-            md.Lf_wrap = (float)ml.box;
-            md.invLf = (float)(1.0 / ml.box);
+        md.hf = (float)md.h;
+        md.invLf = (float)(1.0 / ml.box);
+        {   // binary32 prefilter of the Verlet build on cell offsets (k_nlist):
+            // the offsets (<= h), the shifted own offset (<= 2h) and the
+            // difference (<= 3h) are rounded once each, and h itself once, so a
+            // component is off by at most 9 h 2^-24; the band is twice the
+            // resulting bound on r^2 near the cutoff.
+            const double ec = 9.0 * md.h * std::ldexp(1.0, -24);
+            const double er2 = 2.0 * rl * std::sqrt(3.0) * ec + 3.0 * ec * ec + 4.0 * rl * rl * std::ldexp(1.0, -24);
+            md.nl_lo = (float)(rl * rl - 2.0 * er2);
+            md.nl_hi = (float)(rl * rl + 2.0 * er2);
         }
-        md.ncc = std::max(md.nc, 16);
-        if (md.ncc > (1 << kg::CODE_BITS)) return fail(KG_ERR_INVALID_ARG);
-        md.hc = ml.box / md.ncc; md.invhc = 1.0 / md.hc; md.hcf = (float)md.hc;
+        if (md.nc > (1 << kg::CODE_BITS)) return fail(KG_ERR_INVALID_ARG);
         md.hdb = ml.box / md.ndb; md.invhdb = 1.0 / md.hdb;
         md.cell_off = (int)ncell;
         md.dbcell_off = (int)ndbcell;
@@ -279,7 +282,7 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
         ndbcell += (long long)md.ndb * md.ndb * md.ndb;
         M += md.M;
     }
-    if (M >= (1LL << 30) || ncell >= (1LL << 30) || ndbcell >= (1LL << 30)) return fail(KG_ERR_INVALID_ARG);
+    if (M >= (1LL << kg::IDX_BITS) || ncell >= (1LL << 30) || ndbcell >= (1LL << 30)) return fail(KG_ERR_INVALID_ARG);
     c->M = (int)M;
     c->Mp = (int)((M + 31) / 32 * 32);
     c->ncell_md = (int)ncell;
@@ -309,10 +312,12 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->pid = (int *)A(Mp * sizeof(int));
     c->recb = (float4 *)A(Mp * sizeof(float4));
     c->recs = (float4 *)A(Mp * sizeof(float4));
-    c->wpos = (float4 *)A(Mp * sizeof(float4));
+    c->shtab = (float4 *)A((size_t)kg::SHIFT_SLOTS * kg::MAX_MELTS * sizeof(float4));
     if (c->precision == KG_MIXED) {
-        c->dlt[0] = (float4 *)A(Mp * sizeof(float4));
-        c->dlt[1] = (float4 *)A(Mp * sizeof(float4));
+        for (int b = 0; b < 2; ++b) {
+            c->dlt[b] = (float4 *)A(Mp * sizeof(float4));
+            c->pg[b] = (float4 *)A(Mp * sizeof(float4));
+        }
     } else {
         c->pos64[0] = (double4_32a *)A(Mp * sizeof(double4_32a));
         c->pos64[1] = (double4_32a *)A(Mp * sizeof(double4_32a));
@@ -325,7 +330,7 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->clist = (int *)A(Mp * sizeof(int));
     const size_t nbs = (size_t)std::max(c->ncell_md, c->ncell_db) / 1024 + 2;
     c->bsum = (int *)A(nbs * sizeof(int));
-    c->nl = (int *)A((size_t)c->maxnb * Mp * sizeof(int));
+    c->nl = (unsigned *)A((size_t)c->maxnb * Mp * sizeof(unsigned));
     c->nn = (int *)A(Mp * sizeof(int));
     c->dbcell = (int *)A(Mp * sizeof(int));
     c->dbrank = (int *)A(Mp * sizeof(int));
@@ -352,6 +357,18 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     if (!ok) return fail(KG_ERR_OOM);
     if (cudaMemcpyAsync(c->d_sim, &c->sim, sizeof(SimDev), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return fail(KG_ERR_CUDA);
+    {   // image shift of each stencil code q: (q % 3 - 1, q / 3 % 3 - 1, q / 9 - 1) * h, as the build uses it
+        std::vector<float4> sh((size_t)kg::SHIFT_SLOTS * kg::MAX_MELTS, make_float4(0.f, 0.f, 0.f, 0.f));
+        for (int m = 0; m < p->n_melts; ++m)
+            for (int q = 0; q < 27; ++q) {
+                const float h = S.melt[m].hf;
+                sh[(size_t)kg::SHIFT_SLOTS * m + q] =
+                    make_float4((float)(q % 3 - 1) * h, (float)((q / 3) % 3 - 1) * h, (float)(q / 9 - 1) * h, 0.f);
+            }
+        if (cudaMemcpyAsync(c->shtab, sh.data(), sh.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
+            return fail(KG_ERR_CUDA);
+    }
     const int nb = (int)((Mp + 255) / 256);
     k_iota<<<nb, 256, 0, c->stream>>>(c->slot_of, (int)Mp, 0);
     k_iota<<<nb, 256, 0, c->stream>>>(c->comp_of, (int)Mp, 0);
@@ -370,7 +387,8 @@ void kg_destroy(kg_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    void *bufs[] = {c->d_sim, c->d_stage, c->x, c->u, c->pid, c->recb, c->recs, c->wpos, c->dlt[0], c->dlt[1], c->pos64[0],
+    void *bufs[] = {c->d_sim, c->d_stage, c->x, c->u, c->pid, c->recb, c->recs, c->shtab, c->dlt[0], c->dlt[1],
+                    c->pg[0], c->pg[1], c->pos64[0],
                     c->pos64[1], c->xb, c->cellid, c->rank, c->ccount, c->cstart, c->clist, c->bsum, c->nl,
                     c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->att, c->koff, c->slot_of,
                     c->comp_of, c->bp, c->img, c->dirty, c->db_stats, c->scratch, c->flags, c->fout, c->partials,
@@ -974,12 +992,13 @@ kg_status kg_get_nlist(kg_ctx *c, int melt, int *offs, int *nbr, long long cap, 
     kg::rebuild_md(c);
     const MeltDev &md = c->sim.melt[melt];
     const size_t Mm = md.M, Mp = c->Mp;
-    std::vector<int> nn(Mm), nl((size_t)c->maxnb * Mm), comp(Mm), slot(Mm);
+    std::vector<int> nn(Mm), comp(Mm), slot(Mm);
+    std::vector<unsigned> nl((size_t)c->maxnb * Mm);
     KG_TRY(cudaMemcpyAsync(nn.data(), c->nn + md.off, Mm * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     KG_TRY(cudaMemcpyAsync(comp.data(), c->comp_of + md.off, Mm * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     KG_TRY(cudaMemcpyAsync(slot.data(), c->slot_of + md.off, Mm * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     for (int k = 0; k < c->maxnb; ++k)
-        KG_TRY(cudaMemcpyAsync(nl.data() + (size_t)k * Mm, c->nl + (size_t)k * Mp + md.off, Mm * sizeof(int),
+        KG_TRY(cudaMemcpyAsync(nl.data() + (size_t)k * Mm, c->nl + (size_t)k * Mp + md.off, Mm * sizeof(unsigned),
                                cudaMemcpyDeviceToHost, c->stream));
     if ((s = read_flags(c, pinned_flags())) != KG_OK) return s;
     long long tot = 0;
@@ -988,7 +1007,7 @@ kg_status kg_get_nlist(kg_ctx *c, int melt, int *offs, int *nbr, long long cap, 
         offs[i] = (int)tot;
         row.clear();
         const size_t j = (size_t)(comp[i] - md.off);
-        for (int k = 0; k < nn[j]; ++k) row.push_back(slot[nl[k * Mm + j] - md.off] - md.off);
+        for (int k = 0; k < nn[j]; ++k) row.push_back(slot[(int)(nl[k * Mm + j] & kg::IDX_MASK) - md.off] - md.off);
         std::sort(row.begin(), row.end());
         if (tot + (long long)row.size() > cap) return KG_ERR_CAPACITY;
         std::copy(row.begin(), row.end(), nbr + tot);

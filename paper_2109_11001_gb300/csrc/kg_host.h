@@ -50,10 +50,11 @@ struct kg_ctx {
     long long graph_replays = 0;
     long long sort_interval = 200;
     int block = 128;             // threads per block of the fused step kernel
-    float4 *recb = nullptr;
-    float4 *wpos = nullptr;      // wrapped binary32 positions (Verlet-list build)
-    float4 *recs = nullptr;      // the same in cell order
-    float4 *dlt[2] = {nullptr, nullptr};
+    float4 *recb = nullptr;      // build records: offset from the Verlet-cell corner, cell coordinates
+    float4 *recs = nullptr;      // the same in cell order (Verlet-list build)
+    float4 *dlt[2] = {nullptr, nullptr};   // (mixed) displacement since the build
+    float4 *pg[2] = {nullptr, nullptr};    // (mixed) gather records recb + dlt
+    float4 *shtab = nullptr;     // image shift of each stencil code, SHIFT_SLOTS per melt
     double4_32a *pos64[2] = {nullptr, nullptr};
     double4_32a *xb = nullptr;
     int cur = 0;                 // ping-pong index of the gather buffer in use
@@ -63,7 +64,8 @@ struct kg_ctx {
     int *cellid = nullptr, *rank = nullptr, *ccount = nullptr, *cstart = nullptr, *clist = nullptr;
     int *bsum = nullptr;         // scan block sums (shared by both grids)
     int maxnb = 0;
-    int *nl = nullptr, *nn = nullptr;
+    unsigned *nl = nullptr;      // entries j | stencil code << IDX_BITS
+    int *nn = nullptr;
 
     // double-bridging
     int ncell_db = 0;

@@ -4,12 +4,15 @@
 //   x        double[3][Mp]   canonical unwrapped positions (SoA)
 //   u        float[3][Mp] (mixed) / double[3][Mp] (FP64): state velocity v_{n-1/2}
 //   pid      int[Mp]         particle ids carried through double-bridging swaps
-//   recb     float4[Mp]      build-time position record: offset from its cell
-//                            corner on the "code grid" + packed cell code
+//   recb     float4[Mp]      build-time position record: offset from the corner
+//                            of its Verlet-grid cell + packed cell coordinates
 //   dlt[2]   float4[Mp]      (mixed) displacement since the last build, ping-pong
+//   pg[2]    float4[Mp]      (mixed) gather record of the step: recb + dlt, code
 //   pos64[2] double4_32a[Mp] (FP64) gather copy of the positions, ping-pong
 //   xb       double4_32a[Mp] (FP64) positions at the last build
-//   nl       int[maxnb][Mp]  Verlet list, column-major (coalesced per k)
+//   nl       uint[maxnb][Mp] Verlet list, column-major (coalesced per k); an
+//                            entry is j | q << IDX_BITS, q the stencil cell
+//                            (image shift) of j relative to the owner's cell
 //   nn       int[Mp]         list lengths
 // Mp is the total slot count rounded up to a multiple of 32.
 #pragma once
@@ -22,6 +25,9 @@ constexpr int MAX_MELTS = 64;
 constexpr int CODE_BITS = 10;           // cells per axis on the code grid <= 1024
 constexpr int CODE_MASK = (1 << CODE_BITS) - 1;
 constexpr int MAX_CELL_OCC = 1024;      // a cell holding more monomers is reported, never scanned
+constexpr int IDX_BITS = 27;            // Verlet-list entry: index bits, then the 5-bit stencil code
+constexpr unsigned IDX_MASK = (1u << IDX_BITS) - 1u;
+constexpr int SHIFT_SLOTS = 32;         // shift-table entries per melt (27 used)
 
 // device error / status word bits
 enum : unsigned {
@@ -36,18 +42,15 @@ enum : unsigned {
 struct MeltDev {
     int off, M, N, n_ch;          // slots [off, off+M): chain c, position i -> off + c*N + i
     double L, invL, kappa;
-    float Lf, kappaf;
+    float Lf, invLf, kappaf;
     // Verlet-list cell grid (cells >= r_c + skin), numbered brick-major
     // (4x4x4-cell bricks) so that a block of consecutive monomers in cell
-    // order has a compact neighbourhood
+    // order has a compact neighbourhood; the position records are offsets
+    // from the corners of these cells
     int nc, nbk, cell_off;
     double h, invh;
+    float hf;
     float nl_lo, nl_hi;      // binary32 prefilter: r^2 < nl_lo in, r^2 >= nl_hi out
-    float Lf_wrap, invLf;
-    // code grid of the position records (>= 16 cells per axis)
-    int ncc;
-    double hc, invhc;
-    float hcf;
     // double-bridging grid (cells >= db_bond_max)
     int ndb, dbcell_off;
     double hdb, invhdb;
@@ -60,6 +63,7 @@ struct StageDev {
     double qmin, r2star, ustar;  // continuation beyond r*^2 = (1 - qmin) R0^2 (qmin > 0)
     double dt, gamma, T, amp;  // amp = sqrt(2 gamma T / dt)
     float nf, c1f, c2f, kfenef, R0sqf, dtf, gammaf, ampf, qminf, r2starf, ustarf;
+    float c2x6f, c1xnf;      // 6 c2 and n c1: fr = (6 c2 r^-6 - n c1 r^-n) / r^2
     int nkind;               // 0: general n, 1: integer n, 2: n = 5.75, 3: n = 6.5
     int nint;
 };
@@ -189,17 +193,28 @@ __device__ __forceinline__ void md_cell_xyz(const MeltDev &md, int cell, int &cx
     cz = ((b / (md.nbk * md.nbk)) << 2) | (l >> 4);
 }
 
-// Minimum-image vector from record i to record j (binary32): the code grid
-// carries the integer part, so no large-magnitude value enters the sum.
-__device__ __forceinline__ float3 rec_rel(float4 bi, float4 di, float4 bj, float4 dj, int ncc, float hc)
+// Minimum-image vector from gather record i to gather record j (binary32):
+// p = offset from the build-time cell corner + displacement, w = packed cell
+// coordinates.  The cell difference, wrapped to the nearest image, carries
+// the integer part, so no large-magnitude value enters the sum.  The wrap is
+// unambiguous while |true cell difference| < nc/2, which holds when nc >= 11
+// for every pair closer than 6 sigma (two bonds at the 2 R0 error limit,
+// cells >= 1.37 sigma, up to half a skin of drift each); smaller grids (small
+// boxes) finish with an explicit minimum image of the small vector.
+__device__ __forceinline__ float3 rec_rel(float4 pi, float4 pj, int nc, float h, float L, float invL)
 {
-    const unsigned ci = __float_as_uint(bi.w), cj = __float_as_uint(bj.w);
-    const int dkx = wrap_dk((int)(cj & CODE_MASK) - (int)(ci & CODE_MASK), ncc);
-    const int dky = wrap_dk((int)((cj >> CODE_BITS) & CODE_MASK) - (int)((ci >> CODE_BITS) & CODE_MASK), ncc);
-    const int dkz = wrap_dk((int)(cj >> (2 * CODE_BITS)) - (int)(ci >> (2 * CODE_BITS)), ncc);
-    return make_float3((bj.x - bi.x) + (dj.x - di.x) + (float)dkx * hc,
-                       (bj.y - bi.y) + (dj.y - di.y) + (float)dky * hc,
-                       (bj.z - bi.z) + (dj.z - di.z) + (float)dkz * hc);
+    const unsigned ci = __float_as_uint(pi.w), cj = __float_as_uint(pj.w);
+    const int dkx = wrap_dk((int)(cj & CODE_MASK) - (int)(ci & CODE_MASK), nc);
+    const int dky = wrap_dk((int)((cj >> CODE_BITS) & CODE_MASK) - (int)((ci >> CODE_BITS) & CODE_MASK), nc);
+    const int dkz = wrap_dk((int)(cj >> (2 * CODE_BITS)) - (int)(ci >> (2 * CODE_BITS)), nc);
+    float3 d = make_float3((pj.x - pi.x) + (float)dkx * h, (pj.y - pi.y) + (float)dky * h,
+                           (pj.z - pi.z) + (float)dkz * h);
+    if (nc < 11) {
+        d.x -= L * rintf(d.x * invL);
+        d.y -= L * rintf(d.y * invL);
+        d.z -= L * rintf(d.z * invL);
+    }
+    return d;
 }
 
 }  // namespace kg

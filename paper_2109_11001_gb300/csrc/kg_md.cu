@@ -25,10 +25,12 @@ namespace kg {
 template <bool ENERGY>
 __device__ __forceinline__ float mlj_fr(const StageDev &st, float r2, float &U)
 {
-    const float ir2 = __frcp_rn(r2);
+    const float ir2 = __fdividef(1.0f, r2);
     const float ir6 = ir2 * ir2 * ir2;
     float rn;
-    if (st.nkind == 1) {
+    if (st.nint == 12) {                 // WCA (Eq. 2): the production potential
+        rn = ir6 * ir6;
+    } else if (st.nkind == 1) {
         float p = 1.0f;
         for (int k = 0; k < (st.nint >> 1); ++k) p *= ir2;
         if (st.nint & 1) p *= rsqrtf(r2);
@@ -41,7 +43,7 @@ __device__ __forceinline__ float mlj_fr(const StageDev &st, float r2, float &U)
         rn = exp2f(-0.5f * st.nf * log2f(r2));
     }
     if (ENERGY) U = st.c1f * rn - st.c2f * ir6 + 1.0f;
-    return (6.0f * st.c2f * ir6 - st.nf * st.c1f * rn) * ir2;
+    return (st.c2x6f * ir6 - st.c1xnf * rn) * ir2;
 }
 
 template <bool ENERGY>
@@ -93,24 +95,39 @@ __device__ __forceinline__ float flog(float a) { return logf(a); }
 __device__ __forceinline__ double flog(double a) { return log(a); }
 __device__ __forceinline__ float frsqrt(float a) { return rsqrtf(a); }
 __device__ __forceinline__ double frsqrt(double a) { return rsqrt(a); }
+__device__ __forceinline__ float frcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double frcp(double a) { return 1.0 / a; }
 
 // ---------------------------------------------------------------------------
 // position access policies
 // ---------------------------------------------------------------------------
+// binary32 gather records p = offset from the build-time cell corner +
+// displacement since the build (w: packed cell coordinates).  A Verlet-list
+// entry carries the image shift of its pair (the stencil code), so a listed
+// pair costs one gather and one table lookup; chain partners, which are not
+// in the list, take the shift from the cell codes.
 struct GeoMixed {
     using T = float;
     using T3 = float3;
-    const float4 *__restrict__ recb;
-    const float4 *__restrict__ dlt;
-    int ncc;
-    float hc;
-    float4 bi, di;
-    __device__ __forceinline__ void melt(const MeltDev &md) { ncc = md.ncc; hc = md.hcf; }
-    __device__ __forceinline__ void self(int s) { bi = __ldg(recb + s); di = __ldg(dlt + s); }
-    __device__ __forceinline__ float3 rel(int j) const
+    const float4 *__restrict__ pg;
+    const float4 *__restrict__ shtab;    // SHIFT_SLOTS shift vectors per melt
+    const float4 *__restrict__ sht;
+    int nc;
+    float h, L, invL;
+    float4 pi;
+    __device__ __forceinline__ void melt(const MeltDev &md, int m)
     {
-        return rec_rel(bi, di, __ldg(recb + j), __ldg(dlt + j), ncc, hc);
+        nc = md.nc; h = md.hf; L = md.Lf; invL = md.invLf;
+        sht = shtab + SHIFT_SLOTS * m;
     }
+    __device__ __forceinline__ void self(int s) { pi = __ldg(pg + s); }
+    __device__ __forceinline__ float3 rel_nl(unsigned e) const
+    {
+        const float4 pj = __ldg(pg + (e & IDX_MASK));
+        const float4 sh = __ldg(sht + (e >> IDX_BITS));
+        return make_float3((pj.x - pi.x) + sh.x, (pj.y - pi.y) + sh.y, (pj.z - pi.z) + sh.z);
+    }
+    __device__ __forceinline__ float3 rel(int j) const { return rec_rel(pi, __ldg(pg + j), nc, h, L, invL); }
 };
 
 struct GeoF64 {
@@ -119,7 +136,7 @@ struct GeoF64 {
     const double4_32a *__restrict__ pos;
     double L, invL;
     double4_32a pi;
-    __device__ __forceinline__ void melt(const MeltDev &md) { L = md.L; invL = md.invL; }
+    __device__ __forceinline__ void melt(const MeltDev &md, int) { L = md.L; invL = md.invL; }
     __device__ __forceinline__ void self(int s) { pi = pos[s]; }
     __device__ __forceinline__ double3 rel(int j) const
     {
@@ -130,7 +147,26 @@ struct GeoF64 {
         dz -= L * rint(dz * invL);
         return make_double3(dx, dy, dz);
     }
+    __device__ __forceinline__ double3 rel_nl(unsigned e) const { return rel((int)(e & IDX_MASK)); }
 };
+
+template <bool ENERGY, typename T, typename T3>
+__device__ __forceinline__ void pair_term(const StageDev &st, T rc2, T3 d, T3 &F, double *e)
+{
+    const T r2 = dot3(d, d);
+    if (!ENERGY) {                       // branch-free: a warp evaluates the force for some lane anyway
+        T U;
+        T fr = mlj_fr<false>(st, r2, U);
+        fr = r2 < rc2 ? fr : (T)0;
+        F.x += fr * d.x; F.y += fr * d.y; F.z += fr * d.z;
+    } else if (r2 < rc2) {
+        T U;
+        const T fr = mlj_fr<ENERGY>(st, r2, U);
+        F.x += fr * d.x; F.y += fr * d.y; F.z += fr * d.z;
+        e[0] += 0.5 * (double)U;
+        e[3] -= 0.5 * (double)(fr * r2);
+    }
+}
 
 // Conservative force on slot s (chain position i of N) and, with ENERGY, its
 // shares of the energies: e[0] pair (1/2 per pair), e[1] bond (1/2 per bond),
@@ -138,25 +174,27 @@ struct GeoF64 {
 template <bool ENERGY, class G>
 __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, const StageDev &st,
                                                    const MeltDev &md, int s, int4 bp,
-                                                   const int *__restrict__ nl, int cnt,
+                                                   const unsigned *__restrict__ nl, int cnt,
                                                    double *e, unsigned &err)
 {
     using T = typename G::T;
     using T3 = typename G::T3;
     T3 F = mk<T>(0, 0, 0);
     const T rc2 = (T)S.rc2;
-    // pairs (Verlet list, both directions stored)
-    for (int k = 0; k < cnt; ++k) {
-        const int j = __ldg(nl + (size_t)k * S.Mp + s);
-        const T3 d = g.rel(j);
-        const T r2 = dot3(d, d);
-        if (r2 < rc2) {
-            T U;
-            const T fr = mlj_fr<ENERGY>(st, r2, U);
-            F.x += fr * d.x; F.y += fr * d.y; F.z += fr * d.z;
-            if (ENERGY) { e[0] += 0.5 * (double)U; e[3] -= 0.5 * (double)(fr * r2); }
-        }
+    // pairs (Verlet list, both directions stored), four entries in flight
+    const unsigned *__restrict__ col = nl + s;
+    const size_t Mp = (size_t)S.Mp;
+    int k = 0;
+    for (; k + 4 <= cnt; k += 4) {
+        const unsigned e0 = __ldg(col + k * Mp), e1 = __ldg(col + (k + 1) * Mp);
+        const unsigned e2 = __ldg(col + (k + 2) * Mp), e3 = __ldg(col + (k + 3) * Mp);
+        const T3 d0 = g.rel_nl(e0), d1 = g.rel_nl(e1), d2 = g.rel_nl(e2), d3 = g.rel_nl(e3);
+        pair_term<ENERGY>(st, rc2, d0, F, e);
+        pair_term<ENERGY>(st, rc2, d1, F, e);
+        pair_term<ENERGY>(st, rc2, d2, F, e);
+        pair_term<ENERGY>(st, rc2, d3, F, e);
     }
+    for (; k < cnt; ++k) pair_term<ENERGY>(st, rc2, g.rel_nl(__ldg(col + k * Mp)), F, e);
     // chain neighbours: bp = (s-2, s-1, s+1, s+2) along the chain, -1 past an end
     const bool hm2 = bp.x >= 0, hm1 = bp.y >= 0, hp1 = bp.z >= 0, hp2 = bp.w >= 0;
     T3 rm2 = mk<T>(0, 0, 0), rm1 = mk<T>(0, 0, 0), rp1 = mk<T>(0, 0, 0), rp2 = mk<T>(0, 0, 0);
@@ -174,13 +212,13 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
             const T qmin = st_c<T>(st, 5);
             T q = (T)1 - r2 / R0sq, fr, Uf = 0;
             if (qmin > (T)0 && q < qmin) {           // continuation beyond r* (kg_params.fene_qmin)
-                fr = kf / qmin;
+                fr = kf * frcp(qmin);
                 if (!(r2 < (T)4 * R0sq)) err |= ERR_OVERSTRETCH;
                 if (ENERGY) Uf = st_c<T>(st, 7) + kf * (r2 - st_c<T>(st, 6)) / ((T)2 * qmin);
             } else {
                 if (!(r2 < R0sq)) err |= ERR_OVERSTRETCH;
                 q = fmax(q, (T)1e-6);                    // finite even when flagged
-                fr = kf / q;
+                fr = kf * frcp(q);
                 if (ENERGY) Uf = (T)-0.5 * kf * R0sq * flog(q);
             }
             T U = 0;
@@ -198,22 +236,25 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
         const T3 Bm2 = sub3(rm1, rm2), Bm1 = mk<T>(-rm1.x, -rm1.y, -rm1.z), B0 = rp1, Bp1 = sub3(rp2, rp1);
         if (hm1 && hp1) {                    // vertex s: force kappa (g1 - g2)
             const T l1 = dot3(Bm1, Bm1), l2 = dot3(B0, B0), inv = frsqrt(l1 * l2), cs = dot3(Bm1, B0) * inv;
-            F.x += kap * ((B0.x * inv - cs * Bm1.x / l1) - (Bm1.x * inv - cs * B0.x / l2));
-            F.y += kap * ((B0.y * inv - cs * Bm1.y / l1) - (Bm1.y * inv - cs * B0.y / l2));
-            F.z += kap * ((B0.z * inv - cs * Bm1.z / l1) - (Bm1.z * inv - cs * B0.z / l2));
+            const T c1 = cs * frcp(l1), c2 = cs * frcp(l2);
+            F.x += kap * ((B0.x * inv - c1 * Bm1.x) - (Bm1.x * inv - c2 * B0.x));
+            F.y += kap * ((B0.y * inv - c1 * Bm1.y) - (Bm1.y * inv - c2 * B0.y));
+            F.z += kap * ((B0.z * inv - c1 * Bm1.z) - (Bm1.z * inv - c2 * B0.z));
             if (ENERGY) e[2] += (double)kap * (1.0 - (double)cs);
         }
         if (hp2) {                           // vertex s+1, s is its first end: -kappa g1
             const T l1 = dot3(B0, B0), l2 = dot3(Bp1, Bp1), inv = frsqrt(l1 * l2), cs = dot3(B0, Bp1) * inv;
-            F.x -= kap * (Bp1.x * inv - cs * B0.x / l1);
-            F.y -= kap * (Bp1.y * inv - cs * B0.y / l1);
-            F.z -= kap * (Bp1.z * inv - cs * B0.z / l1);
+            const T c1 = cs * frcp(l1);
+            F.x -= kap * (Bp1.x * inv - c1 * B0.x);
+            F.y -= kap * (Bp1.y * inv - c1 * B0.y);
+            F.z -= kap * (Bp1.z * inv - c1 * B0.z);
         }
         if (hm2) {                           // vertex s-1, s is its last end: +kappa g2
             const T l1 = dot3(Bm2, Bm2), l2 = dot3(Bm1, Bm1), inv = frsqrt(l1 * l2), cs = dot3(Bm2, Bm1) * inv;
-            F.x += kap * (Bm2.x * inv - cs * Bm1.x / l2);
-            F.y += kap * (Bm2.y * inv - cs * Bm1.y / l2);
-            F.z += kap * (Bm2.z * inv - cs * Bm1.z / l2);
+            const T c2 = cs * frcp(l2);
+            F.x += kap * (Bm2.x * inv - c2 * Bm1.x);
+            F.y += kap * (Bm2.y * inv - c2 * Bm1.y);
+            F.z += kap * (Bm2.z * inv - c2 * Bm1.z);
         }
     }
     return F;
@@ -224,12 +265,13 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
 // F_n = F_c - gamma u + sqrt(2 gamma T / dt) g_n,  g_n = Philox normals.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_step_mixed(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
-                                                   double *__restrict__ x, float *__restrict__ u,
-                                                   const float4 *__restrict__ recb, const float4 *__restrict__ dcur,
-                                                   float4 *__restrict__ dnext, const int *__restrict__ nl,
-                                                   const int *__restrict__ nn, const int *__restrict__ slot_of,
-                                                   const int4 *__restrict__ bp, unsigned *__restrict__ flags,
-                                                   const long long *__restrict__ stepp)
+                                                   const float4 *__restrict__ shtab, double *__restrict__ x,
+                                                   float *__restrict__ u, const float4 *__restrict__ recb,
+                                                   const float4 *__restrict__ dcur, float4 *__restrict__ dnext,
+                                                   const float4 *__restrict__ pcur, float4 *__restrict__ pnext,
+                                                   const unsigned *__restrict__ nl, const int *__restrict__ nn,
+                                                   const int *__restrict__ slot_of, const int4 *__restrict__ bp,
+                                                   unsigned *__restrict__ flags, const long long *__restrict__ stepp)
 {
     if (flags[0]) return;                  // a latched error stops the run
     const SimDev &S = *Sp;
@@ -243,8 +285,11 @@ __global__ void __launch_bounds__(256) k_step_mixed(const SimDev *__restrict__ S
         const int m = melt_of(S, slot);
         const MeltDev &md = S.melt[m];
         const int rel = slot - md.off;
-        GeoMixed g{recb, dcur, md.ncc, md.hcf};
-        g.self(s);
+        GeoMixed g{pcur, shtab};
+        g.melt(md, m);
+        // own record rebuilt from its parts: the same bits the last step wrote to pcur
+        const float4 rb = __ldg(recb + s), dc = dcur[s];
+        g.pi = make_float4(rb.x + dc.x, rb.y + dc.y, rb.z + dc.z, rb.w);
         float3 F = force_on<false>(g, S, st, md, s, __ldg(bp + s), nl, __ldg(nn + s), nullptr, err);
         const float3 gn = gauss3_f(draw(S.seed, m, 0, (unsigned long long)step, (uint32_t)rel));
         const int Mp = S.Mp;
@@ -256,9 +301,10 @@ __global__ void __launch_bounds__(256) k_step_mixed(const SimDev *__restrict__ S
         x[s] += st.dt * (double)v.x;
         x[Mp + s] += st.dt * (double)v.y;
         x[2 * Mp + s] += st.dt * (double)v.z;
-        float4 d = g.di;
+        float4 d = dc;
         d.x += st.dtf * v.x; d.y += st.dtf * v.y; d.z += st.dtf * v.z;
         dnext[s] = d;
+        pnext[s] = make_float4(rb.x + d.x, rb.y + d.y, rb.z + d.z, rb.w);
         rebuild = d.x * d.x + d.y * d.y + d.z * d.z > S.half_skin2f;
         if (!isfinite(v.x + v.y + v.z)) err |= ERR_NONFINITE;
     }
@@ -269,7 +315,7 @@ __global__ void __launch_bounds__(256) k_step_mixed(const SimDev *__restrict__ S
 __global__ void __launch_bounds__(256) k_step_f64(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
                                                  double *__restrict__ x, double *__restrict__ u,
                                                  const double4_32a *__restrict__ pcur, double4_32a *__restrict__ pnext,
-                                                 const double4_32a *__restrict__ xb, const int *__restrict__ nl,
+                                                 const double4_32a *__restrict__ xb, const unsigned *__restrict__ nl,
                                                  const int *__restrict__ nn, const int *__restrict__ slot_of,
                                                  const int4 *__restrict__ bp, unsigned *__restrict__ flags,
                                                  const long long *__restrict__ stepp)
@@ -286,7 +332,7 @@ __global__ void __launch_bounds__(256) k_step_f64(const SimDev *__restrict__ Sp,
         const int m = melt_of(S, slot);
         const MeltDev &md = S.melt[m];
         const int rel = slot - md.off;
-        GeoF64 g{pcur, md.L, md.invL};
+        GeoF64 g{pcur, md.L, md.invL, {}};
         g.self(s);
         double3 F = force_on<false>(g, S, st, md, s, __ldg(bp + s), nl, __ldg(nn + s), nullptr, err);
         const double3 gn = gauss3_d(draw(S.seed, m, 0, (unsigned long long)step, (uint32_t)rel));
@@ -312,13 +358,14 @@ __global__ void __launch_bounds__(256) k_step_f64(const SimDev *__restrict__ Sp,
 // rebuild chain: each kernel returns at once unless flags[1] requests a
 // rebuild; the last block of k_nlist to finish clears the request
 // ---------------------------------------------------------------------------
-// records on the code grid, gather buffer reset, Verlet-grid cell + rank
+// build records (offset from the Verlet-cell corner + cell coordinates),
+// gather buffers reset, Verlet-grid cell + rank within it
 __global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, const double *__restrict__ x,
                                                float4 *__restrict__ recb, float4 *__restrict__ dcur,
-                                               double4_32a *__restrict__ pcur, double4_32a *__restrict__ xb,
-                                               int *__restrict__ cellid, int *__restrict__ rank,
-                                               int *__restrict__ count, const int *__restrict__ slot_of,
-                                               float4 *__restrict__ wpos, unsigned *__restrict__ flags)
+                                               float4 *__restrict__ pgcur, double4_32a *__restrict__ pcur,
+                                               double4_32a *__restrict__ xb, int *__restrict__ cellid,
+                                               int *__restrict__ rank, int *__restrict__ count,
+                                               const int *__restrict__ slot_of, unsigned *__restrict__ flags)
 {
     if (!flags[1] || flags[0]) return;
     const SimDev &S = *Sp;
@@ -331,24 +378,24 @@ __global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, c
         return;
     }
     float off[3];
-    int code[3], cell[3];
-    double xs[3], ws[3];
+    int cell[3];
+    double xs[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double xd = x[d * Mp + s];
         xs[d] = xd;
-        const int K = (int)floor(xd * md.invhc);          // |x| / h < 2^31 (unwrapped cell)
-        off[d] = (float)(xd - (double)K * md.hc);
-        int km = K % md.ncc;
-        if (km < 0) km += md.ncc;
-        code[d] = km;
         const double w = xd - md.L * floor(xd * md.invL);
-        ws[d] = w;
         int c = (int)(w * md.invh);
-        cell[d] = c < 0 ? 0 : (c >= md.nc ? md.nc - 1 : c);
+        c = c < 0 ? 0 : (c >= md.nc ? md.nc - 1 : c);
+        cell[d] = c;
+        off[d] = (float)(w - (double)c * md.h);
     }
-    recb[s] = make_float4(off[0], off[1], off[2], __uint_as_float(pack_code(code[0], code[1], code[2])));
-    if (dcur) dcur[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 rb = make_float4(off[0], off[1], off[2], __uint_as_float(pack_code(cell[0], cell[1], cell[2])));
+    recb[s] = rb;
+    if (dcur) {
+        dcur[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        pgcur[s] = make_float4(rb.x + 0.f, rb.y + 0.f, rb.z + 0.f, rb.w);
+    }
     if (pcur) {
         const double4_32a p = make_double4_32a(xs[0], xs[1], xs[2], 0.0);
         pcur[s] = p;
@@ -357,7 +404,6 @@ __global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, c
     const int c = md_cell(md, cell[0], cell[1], cell[2]);
     cellid[s] = c;
     rank[s] = atomicAdd(count + c, 1);
-    wpos[s] = make_float4((float)ws[0], (float)ws[1], (float)ws[2], 0.f);
 }
 
 // DB grid: cell of each particle from its wrapped position (cells >= 1.3 sigma)
@@ -437,8 +483,8 @@ __global__ void __launch_bounds__(1024) k_scan2(int *__restrict__ out, const int
     }
 }
 
-// slot list in cell order; with recb, the wrapped positions are copied into
-// the same order (recs) so that a cell's candidates are one contiguous run
+// slot list in cell order; with recb, the build records are copied into the
+// same order (recs) so that a cell's candidates are one contiguous run
 __global__ void __launch_bounds__(256) k_scatter(const int *__restrict__ cellid, const int *__restrict__ rank,
                                                 const int *__restrict__ start, int *__restrict__ list, int M,
                                                 const unsigned *__restrict__ flags,
@@ -476,85 +522,90 @@ __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start,
     }
 }
 
-// Verlet list: all t != s, not 1-2 bonded, with r^2 < (r_c + skin)^2.  The
-// binary32 record distance decides every pair outside a band of relative
-// width 1e-5 around the cutoff (its error is below 2e-6); pairs inside the band
-// are decided by the binary64 distance evaluated exactly as
-// ((dx*dx + dy*dy) + dz*dz), dx = d - L rint(d/L).
 // Verlet list of monomer s: every t != s, not 1-2 bonded, with r^2 < (r_c +
-// skin)^2.  The binary32 distance of wrapped positions decides every pair
-// outside a band around the cutoff that bounds its rounding error (nl_lo,
-// nl_hi, from L); pairs inside the band are decided by the binary64 distance
-// ((dx*dx + dy*dy) + dz*dz), dx = d - L rint(d/L), exactly as the definition.
-__device__ __forceinline__ void nlist_row(const SimDev &S, const double *__restrict__ x,
-                                          const float4 *__restrict__ wpos, const float4 *__restrict__ wps,
-                                          const int *__restrict__ cellid, const int *__restrict__ start,
-                                          const int *__restrict__ list, int *__restrict__ nl, int *__restrict__ nn,
-                                          unsigned *__restrict__ flags, const int *__restrict__ slot_of,
-                                          const int4 *__restrict__ bpa, int s)
-{
-    const MeltDev &md = S.melt[melt_of(S, slot_of[s])];
-    const int4 bp = bpa[s];                                  // 1-2 bonded partners: bp.y, bp.z
-    const float4 wi = __ldg(wpos + s);
-    const float L = md.Lf_wrap, invL = md.invLf;
-    int cx, cy, cz;
-    md_cell_xyz(md, cellid[s], cx, cy, cz);
-    const int nc = md.nc;
-    const int xm = cx ? cx - 1 : nc - 1, xp = cx + 1 < nc ? cx + 1 : 0;
-    const int ym = cy ? cy - 1 : nc - 1, yp = cy + 1 < nc ? cy + 1 : 0;
-    const int zm = cz ? cz - 1 : nc - 1, zp = cz + 1 < nc ? cz + 1 : 0;
-    // the 27 cells as one flattened stream of candidates, so that a warp runs
-    // about the largest lane's total count instead of the largest count per cell
-    int cnt = 0, ci = 0, k = 0, e = 0;
-    for (;;) {
-        while (k >= e) {
-            if (ci == 27) goto done;
-            const int q = ci++;
-            const int xx = (q % 3) == 0 ? xm : ((q % 3) == 1 ? cx : xp);
-            const int yy = ((q / 3) % 3) == 0 ? ym : (((q / 3) % 3) == 1 ? cy : yp);
-            const int zz = (q / 9) == 0 ? zm : ((q / 9) == 1 ? cz : zp);
-            const int cell = md_cell(md, xx, yy, zz);
-            k = start[cell];
-            e = start[cell + 1];
-            if (e - k > MAX_CELL_OCC) {
-                atomicOr(flags, ERR_NL_CAPACITY);
-                k = e;
-            }
-        }
-        const float4 wj = __ldg(wps + k);
-        float ex = wj.x - wi.x, ey = wj.y - wi.y, ez = wj.z - wi.z;
-        ex -= L * rintf(ex * invL);
-        ey -= L * rintf(ey * invL);
-        ez -= L * rintf(ez * invL);
-        const float r2 = ex * ex + ey * ey + ez * ez;
-        const int kk = k++;
-        if (r2 >= md.nl_hi) continue;
-        const int t = __ldg(list + kk);
-        if (t == s || t == bp.y || t == bp.z) continue;
-        if (r2 >= md.nl_lo && !(dist2_exact(x, S.Mp, md.L, s, t) < S.rl2)) continue;
-        if (cnt < S.maxnb) nl[(size_t)cnt * S.Mp + s] = t;
-        ++cnt;
-    }
-done:
-    nn[s] = cnt < S.maxnb ? cnt : S.maxnb;
-    if (cnt > S.maxnb) {
-        atomicOr(flags, ERR_NL_CAPACITY);
-        atomicMax(flags + 3, (unsigned)cnt);
-    }
-}
+// skin)^2.  Candidates come from the 27 cells around the cell of s; a
+// candidate j of stencil cell (dx, dy, dz) lies at off_j - (off_s - (dx, dy,
+// dz) h) from s with no wrap, because that cell's image sits at (c_s + d) h.
+// This binary32 value decides every pair outside the band [nl_lo, nl_hi),
+// which bounds its rounding error; pairs inside the band are decided by the
+// binary64 distance ((dx*dx + dy*dy) + dz*dz), dx = d - L rint(d/L), exactly
+// as the definition.  Each entry stores j with its stencil code q, the image
+// shift of the pair until the next build.
+//
+// A warp walks the 27 stencil cells in lockstep: for cell q every lane runs
+// the warp's largest count of that cell, lanes past their own count idle, and
+// the candidate test, exclusions and list append need no divergent control
+// flow except for the rare binary64 band check.  The candidate's record and
+// compute index are loaded together.
+constexpr int NL_BLOCK = 128;
 
-__global__ void __launch_bounds__(128, 8) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
-                                              const float4 *__restrict__ wpos, const float4 *__restrict__ wps,
-                                              const int *__restrict__ cellid,
-                                              const int *__restrict__ start, const int *__restrict__ list,
-                                              int *__restrict__ nl, int *__restrict__ nn,
-                                              unsigned *__restrict__ flags, const int *__restrict__ slot_of,
-                                              const int4 *__restrict__ bp)
+__global__ void __launch_bounds__(NL_BLOCK, 6) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
+                                                   const float4 *__restrict__ recb, const float4 *__restrict__ recs,
+                                                   const int *__restrict__ start, const int *__restrict__ list,
+                                                   unsigned *__restrict__ nl, int *__restrict__ nn,
+                                                   unsigned *__restrict__ flags, const int *__restrict__ slot_of,
+                                                   const int4 *__restrict__ bpa)
 {
     if (!flags[1] || flags[0]) return;
+    constexpr unsigned FULL = 0xffffffffu;
     const SimDev &S = *Sp;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < S.M) nlist_row(S, x, wpos, wps, cellid, start, list, nl, nn, flags, slot_of, bp, s);
+    const int s = blockIdx.x * NL_BLOCK + threadIdx.x;
+    const bool live = s < S.M;
+    const int sv = live ? s : S.M - 1;                       // idle lanes read valid memory, write nothing
+    const MeltDev &md = S.melt[melt_of(S, slot_of[sv])];
+    const int4 bp = bpa[sv];                                 // 1-2 bonded partners: bp.y, bp.z
+    const float4 ri = __ldg(recb + sv);
+    const unsigned code = __float_as_uint(ri.w);
+    const int cx = (int)(code & CODE_MASK), cy = (int)((code >> CODE_BITS) & CODE_MASK);
+    const int cz = (int)(code >> (2 * CODE_BITS));
+    const int nc = md.nc;
+    const float h = md.hf, lo = md.nl_lo, hi = md.nl_hi;
+    const int maxnb = S.maxnb;
+    const size_t Mp = (size_t)S.Mp;
+    unsigned *__restrict__ out = nl + s;
+    int cnt = 0;
+#pragma unroll 1
+    for (int q = 0; q < 27; ++q) {
+        const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = q / 9 - 1;
+        int xx = cx + dx, yy = cy + dy, zz = cz + dz;
+        xx = xx < 0 ? nc - 1 : (xx >= nc ? 0 : xx);
+        yy = yy < 0 ? nc - 1 : (yy >= nc ? 0 : yy);
+        zz = zz < 0 ? nc - 1 : (zz >= nc ? 0 : zz);
+        const int cell = md_cell(md, xx, yy, zz);
+        const int k0 = start[cell];
+        int n = live ? start[cell + 1] - k0 : 0;
+        if (n > MAX_CELL_OCC) {
+            atomicOr(flags, ERR_NL_CAPACITY);
+            n = 0;
+        }
+        const int nmax = __reduce_max_sync(FULL, n);
+        const float ox = ri.x - (float)dx * h, oy = ri.y - (float)dy * h, oz = ri.z - (float)dz * h;
+        const unsigned tag = (unsigned)q << IDX_BITS;
+        for (int j = 0; j < nmax; ++j) {
+            const bool valid = j < n;
+            float4 rj = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            int t = -1;
+            if (valid) {
+                rj = __ldg(recs + k0 + j);
+                t = __ldg(list + k0 + j);
+            }
+            const float ex = rj.x - ox, ey = rj.y - oy, ez = rj.z - oz;
+            const float r2 = ex * ex + ey * ey + ez * ez;
+            bool take = r2 < hi && t != s && t != bp.y && t != bp.z;
+            if (take && r2 >= lo) take = dist2_exact(x, S.Mp, md.L, s, t) < S.rl2;   // rare: inside the band
+            if (take) {
+                if (cnt < maxnb) out[(size_t)cnt * Mp] = (unsigned)t | tag;
+                ++cnt;
+            }
+        }
+    }
+    if (live) {
+        nn[s] = cnt < maxnb ? cnt : maxnb;
+        if (cnt > maxnb) {
+            atomicOr(flags, ERR_NL_CAPACITY);
+            atomicMax(flags + 3, (unsigned)cnt);
+        }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -574,7 +625,7 @@ __global__ void __launch_bounds__(128, 8) k_nlist(const SimDev *__restrict__ Sp,
 template <class G>
 __global__ void __launch_bounds__(128) k_forces(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
                                                G g, const void *__restrict__ uptr, int lo, int hi,
-                                               const int *__restrict__ nl, const int *__restrict__ nn,
+                                               const unsigned *__restrict__ nl, const int *__restrict__ nn,
                                                const int *__restrict__ slot_of, const int4 *__restrict__ bp,
                                                double *__restrict__ Fout, double *__restrict__ part,
                                                unsigned *__restrict__ flags, long long step)
@@ -591,7 +642,7 @@ __global__ void __launch_bounds__(128) k_forces(const SimDev *__restrict__ Sp, c
         const MeltDev &md = S.melt[m];
         const int rel = slot - md.off;
         G gg = g;
-        gg.melt(md);
+        gg.melt(md, m);
         gg.self(s);
         const auto F = force_on<true>(gg, S, st, md, s, bp[s], nl, __ldg(nn + s), e, err);
         const int Mp = S.Mp;
@@ -804,25 +855,26 @@ static void launch_rebuild(kg_ctx *c, cudaStream_t st)
 {
     const bool mixed = c->precision == KG_MIXED;
     k_bin_md<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->recb, mixed ? c->dlt[c->cur] : nullptr,
-                                              mixed ? nullptr : c->pos64[c->cur], c->xb, c->cellid, c->rank,
-                                              c->ccount, c->slot_of, c->wpos, c->flags);
+                                              mixed ? c->pg[c->cur] : nullptr, mixed ? nullptr : c->pos64[c->cur],
+                                              c->xb, c->cellid, c->rank, c->ccount, c->slot_of, c->flags);
     const int nb = nblk(c->ncell_md, 1024);
     k_scan1<<<nb, 1024, 0, st>>>(c->ccount, c->cstart, c->bsum, c->ncell_md, c->flags);
     k_scan2<<<nb, 1024, 0, st>>>(c->cstart, c->bsum, c->ncell_md, nb, c->flags);
-    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->cellid, c->rank, c->cstart, c->clist, c->M, c->flags, c->wpos,
+    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->cellid, c->rank, c->cstart, c->clist, c->M, c->flags, c->recb,
                                                c->recs);
     k_cellsort<<<nblk(c->ncell_md, 256), 256, 0, st>>>(c->cstart, c->clist, c->recs, c->ccount, c->ncell_md,
                                                        c->flags);
-    k_nlist<<<nblk(c->M, 128), 128, 0, st>>>(c->d_sim, c->x, c->wpos, c->recs, c->cellid, c->cstart, c->clist, c->nl,
-                                             c->nn, c->flags, c->slot_of, c->bp);
+    k_nlist<<<nblk(c->M, NL_BLOCK), NL_BLOCK, 0, st>>>(c->d_sim, c->x, c->recb, c->recs, c->cstart, c->clist,
+                                                       c->nl, c->nn, c->flags, c->slot_of, c->bp);
 }
 
 static void launch_step_kernel(kg_ctx *c, cudaStream_t st, int cur)
 {
     const int nb = nblk(c->M, c->block);
     if (c->precision == KG_MIXED)
-        k_step_mixed<<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->x, (float *)c->u, c->recb, c->dlt[cur],
-                                         c->dlt[cur ^ 1], c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
+        k_step_mixed<<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->shtab, c->x, (float *)c->u, c->recb,
+                                              c->dlt[cur], c->dlt[cur ^ 1], c->pg[cur], c->pg[cur ^ 1], c->nl,
+                                              c->nn, c->slot_of, c->bp, c->flags, c->d_step);
     else
         k_step_f64<<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->x, (double *)c->u, c->pos64[cur], c->pos64[cur ^ 1],
                                        c->xb, c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
@@ -960,7 +1012,7 @@ void forces_eval(kg_ctx *c, int melt, long long step, double *F_dev, double *par
     const MeltDev &md = c->sim.melt[melt];
     ++c->launches;
     if (c->precision == KG_MIXED) {
-        GeoMixed g{c->recb, c->dlt[c->cur], 0, 0.f, {}, {}};
+        GeoMixed g{c->pg[c->cur], c->shtab};
         k_forces<GeoMixed><<<nb, 128, 0, c->stream>>>(c->d_sim, c->d_stage, g, c->u, md.off, md.off + md.M,
                                                      c->nl, c->nn, c->slot_of, c->bp, F_dev, part_dev, c->flags, step);
     } else {
