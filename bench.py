@@ -32,6 +32,8 @@ if ROOT not in sys.path:
 
 MD_PER_STEP = 50
 DT = 0.01
+DB_BUDGET = 0.1          # attempts per monomer per sweep for the double-bridging metric
+DB_SWEEPS = 5
 # FENE continuation beyond r* = R0 sqrt(1 - q) for the soft stages of long
 # runs (the log term of Eq. 3 is kept below r*; see kg_params.fene_qmin)
 FENE_QMIN = 0.01
@@ -343,6 +345,26 @@ def run_ours(args, world, rank, local):
     t_e2e = allmax(world, time.perf_counter() - t0)
     log(f"e2e {t_e2e:.3f} s")
 
+    # double-bridging throughput at a fixed attempt budget: M/10 attempts per
+    # sweep on the equilibrated melt (uniform proposal), sweeps back to back
+    kg.kg_db_sweep(ctx, DB_BUDGET)
+    torch.cuda.synchronize()
+    barrier(world)
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    db_acc = db_att = db_re = 0
+    d0.record(stream)
+    for _ in range(DB_SWEEPS):
+        st = kg.kg_db_sweep(ctx, DB_BUDGET)
+        db_acc += st.accepted
+        db_att += st.attempted
+        db_re += st.reevaluated
+    d1.record(stream)
+    torch.cuda.synchronize()
+    t_db = allmax(world, d0.elapsed_time(d1) / 1e3)
+    db_acc_all = allsum(world, float(db_acc))
+    db_att_all = allsum(world, float(db_att))
+    log(f"db budget: {DB_SWEEPS} sweeps, {db_att} attempts, {db_acc} accepted, {db_re} re-evaluated, {t_db * 1e3:.1f} ms")
+
     # secondary: the same step in plain binary64 on this GPU (single rank), and
     # the learned double-bridging proposal against the uniform one
     sec = lsec = None
@@ -376,7 +398,13 @@ def run_ours(args, world, rank, local):
                    "precision": args.precision, "replicas": world, "autotuned": tuning,
                    "skin": tuning["skin"] if tuning else args.skin,
                    "l2": "inputs larger than L2 (working set > 129 MB), no flush"},
-        "accepted_db_moves_per_s": acc_all / t_max,
+        "accepted_db_moves_per_s": db_acc_all / t_db,
+        "db": {"attempts_per_sweep": int(round(DB_BUDGET * m.M)), "sweeps": DB_SWEEPS * world,
+               "attempted": int(db_att_all), "accepted": int(db_acc_all), "reevaluated": int(db_re),
+               "accepted_per_s": db_acc_all / t_db, "attempts_per_s": db_att_all / t_db,
+               "ms_per_sweep": t_db * 1e3 / DB_SWEEPS, "proposal": "uniform",
+               "timing": "CUDA events around back-to-back sweeps, stats read after each"},
+        "accepted_db_moves_per_s_in_step": acc_all / t_max,
         "db_attempts_per_step": att / args.steps,
         "roofline": {"bound": "hbm", "kernel": "k_step_" + args.precision, "achieved": achieved, "peak": peak,
                      "timing": "CUDA events around each step-kernel launch, bench steps after the timed region",

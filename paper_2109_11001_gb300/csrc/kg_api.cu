@@ -276,6 +276,18 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
         }
         if (md.nc > (1 << kg::CODE_BITS)) return fail(KG_ERR_INVALID_ARG);
         md.hdb = ml.box / md.ndb; md.invhdb = 1.0 / md.hdb;
+        md.hdbf = (float)md.hdb;
+        if (md.ndb > (1 << kg::CODE_BITS)) return fail(KG_ERR_INVALID_ARG);
+        if (md.ndb >= 11) {   // same error model as the Verlet prefilter, around db_bond_max^2
+            const double lim = p->db_bond_max;
+            const double ec = 9.0 * md.hdb * std::ldexp(1.0, -24);
+            const double er2 = 2.0 * lim * std::sqrt(3.0) * ec + 3.0 * ec * ec + 4.0 * lim * lim * std::ldexp(1.0, -24);
+            md.db_lo = (float)(lim * lim - 2.0 * er2);
+            md.db_hi = (float)(lim * lim + 2.0 * er2);
+        } else {              // small grids: every pair takes the binary64 distance
+            md.db_lo = 0.0f;
+            md.db_hi = 3.0e38f;
+        }
         md.cell_off = (int)ncell;
         md.dbcell_off = (int)ndbcell;
         ncell += 64LL * md.nbk * md.nbk * md.nbk;
@@ -337,6 +349,8 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->dbcount = (int *)A((size_t)c->ncell_db * sizeof(int));
     c->dbstart = (int *)A(((size_t)c->ncell_db + 1) * sizeof(int));
     c->dblist = (int *)A(Mp * sizeof(int));
+    c->dbrec = (float4 *)A(Mp * sizeof(float4));
+    c->dbmark = (int *)A((size_t)c->ncell_db * sizeof(int));
     c->koff = (int *)A((kg::MAX_MELTS + 1) * sizeof(int));
     c->slot_of = (int *)A(Mp * sizeof(int));
     c->comp_of = (int *)A(Mp * sizeof(int));
@@ -390,7 +404,8 @@ void kg_destroy(kg_ctx *c)
     void *bufs[] = {c->d_sim, c->d_stage, c->x, c->u, c->pid, c->recb, c->recs, c->shtab, c->dlt[0], c->dlt[1],
                     c->pg[0], c->pg[1], c->pos64[0],
                     c->pos64[1], c->xb, c->cellid, c->rank, c->ccount, c->cstart, c->clist, c->bsum, c->nl,
-                    c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->att, c->koff, c->slot_of,
+                    c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->dbrec, c->dbmark, c->att,
+                    c->koff, c->slot_of,
                     c->comp_of, c->bp, c->img, c->dirty, c->db_stats, c->scratch, c->flags, c->fout, c->partials,
                     c->r2tmp, c->hist, c->mlp_master, c->mlp_adam, c->mlp_grad, c->mlp_blob, c->mlp_w2t,
                     c->logf, c->logt, c->logn, c->trainf, c->traint, c->d_train_head, c->tr_buf, c->bmax2,

@@ -12,20 +12,24 @@
 //
 // GPU organisation of one sweep:
 //   1. bin every monomer on a grid of >= 1.3 sigma cells (positions do not move
-//      during a sweep: swaps only relabel slots);
+//      during a sweep: swaps only relabel slots) and write its binary32 record
+//      there; the 1.3 sigma criterion is decided on the records outside a
+//      rounding band and in binary64 inside it, so decisions are exact;
 //   2. k_db_eval: every attempt evaluated in parallel against the pre-sweep
-//      topology (one thread each).  A "monomer" here is its compute index; the
-//      topology is the pair of maps slot -> monomer (comp_of) and monomer ->
-//      slot (slot_of);
-//   3. k_db_commit: one block per melt walks the attempts in order.  An attempt
-//      is re-evaluated against the current topology when an earlier accepted
-//      swap in the sweep touched one of its two chains, or put a junction
-//      monomer (whose bonds changed) within one cell of a monomer whose
-//      neighbourhood it scanned.  Nothing else an evaluation reads can change:
-//      swaps preserve positions, the bonds inside moved segments, and the
-//      lengths of the two pieces on either side of every bond.  Accepted swaps
-//      rewrite the two maps for the slots of their two chains and add box
-//      shifts to a per-monomer counter;
+//      topology, one warp each (the 27 cells of a partner scan on its lanes).
+//      A "monomer" here is its compute index; the topology is the pair of
+//      maps slot -> monomer (comp_of) and monomer -> slot (slot_of);
+//   3. k_db_commit: one block per melt takes the attempts in order.  An
+//      attempt is re-evaluated against the current topology when an earlier
+//      accepted swap in the sweep touched one of its two chains, or put a
+//      junction monomer (whose bonds changed) within one cell of a monomer
+//      whose neighbourhood it scanned.  Nothing else an evaluation reads can
+//      change: swaps preserve positions, the bonds inside moved segments, and
+//      the lengths of the two pieces on either side of every bond.  The block
+//      skips runs of unaffected rejected attempts with a block-wide scan and
+//      re-evaluates up to one affected attempt per warp at a time (the shared
+//      walk in kg_db.cuh).  Accepted swaps rewrite the two maps for the slots
+//      of their two chains and add box shifts to a per-monomer counter;
 //   4. k_db_finish: the box shifts are added to the positions in place; no
 //      monomer data moves (the maps are the topology).
 #include <cuda_runtime.h>
@@ -34,10 +38,13 @@
 
 namespace kg {
 
+// One attempt, one warp (the partner scans are warp-wide; lane 0 forms dE
+// and the decision in binary64 and broadcasts the record).
 template <class V>
-__device__ Attempt evaluate(const DBC &C, const V &v, unsigned long long seed, long long sweep, int k,
+__device__ Attempt evaluate(const DBC &C, const V &v, WarpCand &wc, unsigned long long seed, long long sweep, int k,
                             int paper, unsigned &err)
 {
+    const int lane = threadIdx.x & 31;
     const MeltDev &md = C.md;
     const int N = md.N, off = md.off;
     Attempt a;
@@ -54,92 +61,112 @@ __device__ Attempt evaluate(const DBC &C, const V &v, unsigned long long seed, l
     a.c = c;
     a.jp[0] = v.occ(off + c * N + b);
     a.jp[1] = v.occ(off + c * N + b + 1);
-    Cand list[CAND_CAP];
-    const int n1 = count_partners(C, v, c, b, list);
-    if (n1 == 0) return a;
-    if (n1 < 0 || n1 > CAND_CAP) { err |= ERR_DB_CAPACITY; return a; }
-    for (int i = 1; i < n1; ++i) {                      // order by (key, key2)
-        const Cand t = list[i];
-        int j = i - 1;
-        while (j >= 0 && (list[j].key > t.key || (list[j].key == t.key && list[j].key2 > t.key2))) {
-            list[j + 1] = list[j];
-            --j;
-        }
-        list[j + 1] = t;
-    }
-    const Cand m = list[mul_hi64(((unsigned long long)r2.y << 32) | r2.x, (unsigned long long)n1)];
+    const int n1 = warp_partners<true>(C, v, c, b, wc, err);
+    if (n1 <= 0) return a;                              // empty, or a capacity error (flagged)
+    const Cand m = wc.cand[mul_hi64(((unsigned long long)r2.y << 32) | r2.x, (unsigned long long)n1)];
     a.flags = 1;
     a.d = m.d;
     a.jp[2] = v.occ(off + m.d * N + m.q);
     a.jp[3] = v.occ(off + m.d * N + m.q + 1);
-    const int n2 = count_partners(C, v, m.d, m.q, (Cand *)nullptr);
-    if (n2 <= 0) { err |= n2 < 0 ? ERR_DB_CAPACITY : ERR_DB_INTERNAL; a.flags = 1; return a; }
+    const int n2 = warp_partners<false>(C, v, m.d, m.q, wc, err);
+    if (n2 <= 0) { err |= n2 < 0 ? ERR_DB_CAPACITY : ERR_DB_INTERNAL; return a; }
     const int A = c < m.d ? c : m.d, B = c < m.d ? m.d : c;
     const int pA = A == c ? b : m.q, pB = A == c ? m.q : b;
     a.kind = m.kind; a.A = A; a.B = B; a.pA = pA; a.pB = pB;
     const ViewMove<V> w{v, m.kind, A, B, pA, pB, N, off};
-    double dE = bond_fene(C, w, A, pA) + bond_fene(C, w, B, pB) - bond_fene(C, v, A, pA) - bond_fene(C, v, B, pB);
-    dE += bend(C, w, A, pA) + bend(C, w, A, pA + 1) + bend(C, w, B, pB) + bend(C, w, B, pB + 1);
-    dE -= bend(C, v, A, pA) + bend(C, v, A, pA + 1) + bend(C, v, B, pB) + bend(C, v, B, pB + 1);
-    const int r1 = count_partners(C, w, A, pA, (Cand *)nullptr);
-    const int rr2 = count_partners(C, w, B, pB, (Cand *)nullptr);
-    if (r1 <= 0 || rr2 <= 0) { err |= (r1 < 0 || rr2 < 0) ? ERR_DB_CAPACITY : ERR_DB_INTERNAL; a.flags = 1; return a; }
-    const double ratio = (1.0 / r1 + 1.0 / rr2) / (1.0 / n1 + 1.0 / n2);
-    double acc = exp(-dE / C.T);
-    if (!paper) acc *= ratio;
-    if (uacc < acc) a.flags |= 2;
+    const int r1 = warp_partners<false>(C, w, A, pA, wc, err);
+    const int rr2 = warp_partners<false>(C, w, B, pB, wc, err);
+    if (r1 <= 0 || rr2 <= 0) { err |= (r1 < 0 || rr2 < 0) ? ERR_DB_CAPACITY : ERR_DB_INTERNAL; return a; }
+    int acc_bit = 0;
+    if (lane == 0) {
+        double dE = bond_fene(C, w, A, pA) + bond_fene(C, w, B, pB) - bond_fene(C, v, A, pA) - bond_fene(C, v, B, pB);
+        dE += bend(C, w, A, pA) + bend(C, w, A, pA + 1) + bend(C, w, B, pB) + bend(C, w, B, pB + 1);
+        dE -= bend(C, v, A, pA) + bend(C, v, A, pA + 1) + bend(C, v, B, pB) + bend(C, v, B, pB + 1);
+        const double ratio = (1.0 / r1 + 1.0 / rr2) / (1.0 / n1 + 1.0 / n2);
+        double acc = exp(-dE / C.T);
+        if (!paper) acc *= ratio;
+        acc_bit = uacc < acc;
+    }
+    if (__shfl_sync(FULL_MASK, acc_bit, 0)) a.flags |= 2;
     return a;
 }
 
-__global__ void __launch_bounds__(128) k_db_eval(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
-                                                const double *__restrict__ x, const int *__restrict__ pid,
-                                                const int *__restrict__ cell, const int *__restrict__ start,
-                                                const int *__restrict__ list, const int *__restrict__ koff,
-                                                const int *__restrict__ comp_of, const int *__restrict__ slot_of,
-                                                Attempt *__restrict__ att, long long sweep, unsigned *flags)
+constexpr int EVAL_WARPS_U = 4;                 // attempts (warps) per block of k_db_eval
+
+__global__ void __launch_bounds__(32 * EVAL_WARPS_U) k_db_eval(const SimDev *__restrict__ Sp,
+                                                              const StageDev *__restrict__ stp,
+                                                              const double *__restrict__ x,
+                                                              const int *__restrict__ pid,
+                                                              const int *__restrict__ cell,
+                                                              const int *__restrict__ start,
+                                                              const int *__restrict__ list,
+                                                              const float4 *__restrict__ rec,
+                                                              const int *__restrict__ koff,
+                                                              const int *__restrict__ comp_of,
+                                                              const int *__restrict__ slot_of,
+                                                              Attempt *__restrict__ att, long long sweep,
+                                                              unsigned *flags)
 {
-    if (flags[0]) return;                          // a latched error stops the sweep
+    __shared__ WarpCand wcs[EVAL_WARPS_U];
+    if (flags[0]) return;                          // a latched error stops the sweep (no block barrier follows)
     const SimDev &S = *Sp;
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * EVAL_WARPS_U + warp;
     if (g >= koff[S.n_melts]) return;
     int m = 0;
     while (g >= koff[m + 1]) ++m;
-    const DBC C = make_dbc(S, *stp, m, x, pid, cell, start, list, stp->T);
+    const DBC C = make_dbc(S, *stp, m, x, pid, cell, start, list, rec, stp->T);
     unsigned err = 0;
-    att[g] = evaluate(C, ViewMap{comp_of, slot_of}, S.seed, sweep, g - koff[m], S.paper_metropolis, err);
-    if (err) atomicOr(flags, err);
+    const Attempt a = evaluate(C, ViewMap{comp_of, slot_of}, wcs[warp], S.seed, sweep, g - koff[m],
+                               S.paper_metropolis, err);
+    if (lane == 0) {
+        att[g] = a;
+        if (err) atomicOr(flags, err);
+    }
 }
 
-// uniform proposal: thread 0 re-evaluates, junction cells within one cell
+// uniform proposal: any warp re-evaluates, junction cells within one cell
 struct UniformPolicy {
     int paper;
+    WarpCand *wc;                                  // one per warp of the block
     __device__ void init() {}
     __device__ int radius(const MeltDev &) const { return 1; }
-    __device__ void reeval(const DBC &C, const ViewMap &V, const SimDev &S, long long sweep, int kk, int,
+    __device__ int batch() const { return 32; }
+    __device__ void reeval(const DBC &C, const ViewMap &V, const SimDev &S, long long sweep, int kk, int, int warp,
                            Attempt &out, unsigned *flags)
     {
-        if (threadIdx.x == 0) {
-            unsigned err = 0;
-            out = evaluate(C, V, S.seed, sweep, kk, paper, err);
+        unsigned err = 0;
+        const Attempt a = evaluate(C, V, wc[warp], S.seed, sweep, kk, paper, err);
+        if ((threadIdx.x & 31) == 0) {
+            out = a;
             if (err) atomicOr(flags, err);
         }
     }
-    __device__ void after(const Attempt &, int) {}
 };
 
-__global__ void __launch_bounds__(256) k_db_commit(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
-                                                  const double *__restrict__ x, const int *__restrict__ pid,
-                                                  const int *__restrict__ cell, const int *__restrict__ start,
-                                                  const int *__restrict__ list, const int *__restrict__ koff,
-                                                  const Attempt *__restrict__ att, int *__restrict__ occ,
-                                                  int *__restrict__ curmap, int *__restrict__ img,
-                                                  int *__restrict__ dirty, long long *__restrict__ stats,
-                                                  long long sweep, unsigned *flags)
+constexpr int COMMIT_THREADS_U = 512;
+
+__global__ void __launch_bounds__(COMMIT_THREADS_U) k_db_commit(const SimDev *__restrict__ Sp,
+                                                               const StageDev *__restrict__ stp,
+                                                               const double *__restrict__ x,
+                                                               const int *__restrict__ pid,
+                                                               const int *__restrict__ cell,
+                                                               const int *__restrict__ start,
+                                                               const int *__restrict__ list,
+                                                               const float4 *__restrict__ rec,
+                                                               const int *__restrict__ koff,
+                                                               const Attempt *__restrict__ att, int *__restrict__ occ,
+                                                               int *__restrict__ curmap, int *__restrict__ img,
+                                                               int *__restrict__ dirty, int *__restrict__ mark,
+                                                               int stamp, long long *__restrict__ stats,
+                                                               long long sweep, unsigned *flags, int maxN)
 {
-    extern __shared__ int old_occ[];              // 2N ints
-    UniformPolicy pol{Sp->paper_metropolis};
-    db_commit_body(pol, *Sp, *stp, x, pid, cell, start, list, koff, att, occ, curmap, img, dirty, stats, sweep,
-                   flags, old_occ);
+    extern __shared__ __align__(16) unsigned char smem[];
+    int *old_occ = reinterpret_cast<int *>(smem);            // 2N ints
+    WarpCand *wc = reinterpret_cast<WarpCand *>(smem + ((sizeof(int) * 2 * (size_t)maxN + 15) & ~(size_t)15));
+    UniformPolicy pol{Sp->paper_metropolis, wc};
+    db_commit_body(pol, *Sp, *stp, x, pid, cell, start, list, rec, koff, att, occ, curmap, img, dirty, mark, stamp,
+                   stats, sweep, flags, old_occ);
 }
 
 // end of a sweep: box shifts into the positions (x + L*img, as one rounding of
@@ -164,7 +191,8 @@ __global__ void __launch_bounds__(256) k_db_finish(const SimDev *__restrict__ Sp
 
 // kg_md.cu
 __global__ void k_bin_db(const SimDev *__restrict__ Sp, const double *__restrict__ x, int *__restrict__ cellid,
-                         int *__restrict__ rank, int *__restrict__ count, const int *__restrict__ slot_of);
+                         int *__restrict__ rank, int *__restrict__ count, const int *__restrict__ slot_of,
+                         float4 *__restrict__ rec);
 __global__ void k_scan1(const int *__restrict__ in, int *__restrict__ out, int *__restrict__ bsum, int n,
                         const unsigned *__restrict__ flags);
 __global__ void k_scan2(int *__restrict__ out, const int *__restrict__ bsum, int n, int nblk,
@@ -186,7 +214,8 @@ void db_bin(kg_ctx *c, const std::vector<long long> &K)
     cudaMemcpyAsync(c->koff, koff.data(), sizeof(int) * (nm + 1), cudaMemcpyHostToDevice, st);
     // grid of >= 1.3 sigma cells
     cudaMemsetAsync(c->dbcount, 0, sizeof(int) * c->ncell_db, st);
-    k_bin_db<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->dbcell, c->dbrank, c->dbcount, c->slot_of);
+    k_bin_db<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->dbcell, c->dbrank, c->dbcount, c->slot_of,
+                                              c->dbrec);
     const int nb = nblk(c->ncell_db, 1024);
     k_scan1<<<nb, 1024, 0, st>>>(c->dbcount, c->dbstart, c->bsum, c->ncell_db, nullptr);
     k_scan2<<<nb, 1024, 0, st>>>(c->dbstart, c->bsum, c->ncell_db, nb, nullptr);
@@ -202,6 +231,15 @@ void db_finish(kg_ctx *c, long long *host_stats)
     k_db_finish<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->slot_of, c->img, c->dirty);
     bonded_partners(c);
     cudaMemcpyAsync(host_stats, c->db_stats, sizeof(long long) * 4 * c->sim.n_melts, cudaMemcpyDeviceToHost, st);
+}
+
+int next_stamp(kg_ctx *c)
+{
+    if (++c->db_stamp >= 0x3fffffff) {          // stamps wrap: start the marks afresh
+        cudaMemsetAsync(c->dbmark, 0, sizeof(int) * c->ncell_db, c->stream);
+        c->db_stamp = 1;
+    }
+    return c->db_stamp;
 }
 
 int db_max_chain_len(const kg_ctx *c)
@@ -221,13 +259,18 @@ void db_sweep(kg_ctx *c, const std::vector<long long> &K, long long *host_stats)
     // speculative evaluation
     Attempt *att = (Attempt *)c->att;
     if (tot > 0)
-        k_db_eval<<<nblk(tot, 128), 128, 0, st>>>(c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart,
-                                                  c->dblist, c->koff, c->comp_of, c->slot_of, att, c->sweep,
-                                                  c->flags);
+        k_db_eval<<<nblk(tot, EVAL_WARPS_U), 32 * EVAL_WARPS_U, 0, st>>>(
+            c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart, c->dblist, c->dbrec, c->koff, c->comp_of,
+            c->slot_of, att, c->sweep, c->flags);
     // ordered commit, one block per melt
-    k_db_commit<<<nm, 256, sizeof(int) * 2 * db_max_chain_len(c), st>>>(
-        c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart, c->dblist, c->koff, att, c->comp_of, c->slot_of,
-        c->img, c->dirty, c->db_stats, c->sweep, c->flags);
+    const int maxN = db_max_chain_len(c);
+    const size_t sm = ((sizeof(int) * 2 * (size_t)maxN + 15) & ~(size_t)15) +
+                      sizeof(WarpCand) * (COMMIT_THREADS_U / 32);
+    cudaFuncSetAttribute(k_db_commit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_db_commit<<<nm, COMMIT_THREADS_U, sm, st>>>(c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart,
+                                                  c->dblist, c->dbrec, c->koff, att, c->comp_of, c->slot_of, c->img,
+                                                  c->dirty, c->dbmark, next_stamp(c), c->db_stats, c->sweep,
+                                                  c->flags, maxN);
     c->launches += 2;
     db_finish(c, host_stats);
 }

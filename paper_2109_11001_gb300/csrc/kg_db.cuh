@@ -9,7 +9,6 @@
 namespace kg {
 
 constexpr int CAND_CAP = 48;
-constexpr int JCAP = 4096;
 
 struct Cand {
     int key, key2, kind, d, q;
@@ -22,6 +21,7 @@ struct DBC {
     const int *__restrict__ cell;
     const int *__restrict__ start;
     const int *__restrict__ list;
+    const float4 *__restrict__ rec;    // binary32 records on the 1.3 sigma grid (k_bin_db)
     MeltDev md;
     int melt;
     double lim2, kfene, R0, T, qmin, nexp;
@@ -61,46 +61,95 @@ struct ViewMove {
 
 __device__ __forceinline__ double d2(const DBC &C, int a, int b) { return dist2_exact(C.x, C.Mp, C.md.L, a, b); }
 
-// |P(b)| for bond (chain c, index b) in view v; fills `out` (<= CAND_CAP) if given.
-template <class V>
-__device__ int count_partners(const DBC &C, const V &v, int c, int b, Cand *out)
+// Swap-bond criterion d2(a, b) <= 1.3^2, decided exactly: the binary32 record
+// distance settles every pair outside the band [db_lo, db_hi), which bounds
+// its rounding error; pairs inside it take the binary64 distance.
+__device__ __forceinline__ bool within(const DBC &C, int a, int b)
 {
+    const float3 d = rec_rel(__ldg(C.rec + a), __ldg(C.rec + b), C.md.ndb, C.md.hdbf, C.md.Lf, C.md.invLf);
+    const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+    if (r2 < C.md.db_lo) return true;
+    if (r2 >= C.md.db_hi) return false;
+    return d2(C, a, b) <= C.lim2;
+}
+
+// per-warp candidate scratch of one partner enumeration
+struct __align__(16) WarpCand {
+    Cand tmp[CAND_CAP];
+    Cand cand[CAND_CAP];
+    int n;
+};
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// Admissible partners P(b) of bond (c, b) in view v, one warp: lane q < 27
+// scans stencil cell q around the bond's lower monomer.  With ORDER the list
+// is left in wc.cand ordered by (key, key2) (the monomer ids of the monomer
+// that would bond to the drawn bond's lower end and of the partner bond's
+// other monomer).  Returns |P|, or -1 (error bit set) on a capacity overflow.
+template <bool ORDER, class V>
+__device__ int warp_partners(const DBC &C, const V &v, int c, int b, WarpCand &wc, unsigned &err)
+{
+    const int lane = threadIdx.x & 31;
     const MeltDev &md = C.md;
     const int N = md.N;
     const int us = md.off + c * N + b;
     const int pu = v.occ(us), pw = v.occ(us + 1);
-    if (d2(C, pu, pw) > C.lim2) return 0;
-    const int n = md.ndb, c0 = C.cell[pu] - md.dbcell_off;
-    const int cx = c0 % n, cy = (c0 / n) % n, cz = c0 / (n * n);
-    int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int cell = md.dbcell_off + (((cz + dz + n) % n) * n + (cy + dy + n) % n) * n + (cx + dx + n) % n;
-                const int b0 = C.start[cell], e = C.start[cell + 1];
-                if (e - b0 > MAX_CELL_OCC) return -1;                  // caller reports capacity
-                for (int k = b0; k < e; ++k) {
-                    const int t = C.list[k];
-                    const int ts = v.cur(t), r = ts - md.off, d = r / N, i = r - d * N;
-                    if (d == c) continue;
-                    if (d2(C, pu, t) > C.lim2) continue;
-                    if (i == b + 1) {                          // kind 0: t = D_{b+1}
-                        const int up = v.occ(md.off + d * N + b);
-                        if (d2(C, up, pw) <= C.lim2 && d2(C, up, t) <= C.lim2) {
-                            if (out && cnt < CAND_CAP) out[cnt] = Cand{C.pid[t], C.pid[up], 0, d, b};
-                            ++cnt;
-                        }
+    if (!within(C, pu, pw)) return 0;
+    if (lane == 0) wc.n = 0;
+    __syncwarp();
+    bool bad = false;
+    if (lane < 27) {
+        const int n = md.ndb, c0 = C.cell[pu] - md.dbcell_off;
+        const int cx = c0 % n, cy = (c0 / n) % n, cz = c0 / (n * n);
+        const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+        const int cell = md.dbcell_off + (((cz + dz + n) % n) * n + (cy + dy + n) % n) * n + (cx + dx + n) % n;
+        const int b0 = C.start[cell], e = C.start[cell + 1];
+        if (e - b0 > MAX_CELL_OCC) {
+            bad = true;
+        } else {
+            for (int k = b0; k < e; ++k) {
+                const int t = C.list[k];
+                const int ts = v.cur(t), r = ts - md.off, d = r / N, i = r - d * N;
+                if (d == c) continue;
+                if (i != b + 1 && i != N - 2 - b) continue;   // neither kind can use t
+                if (!within(C, pu, t)) continue;
+                if (i == b + 1) {                          // kind 0: t = D_{b+1}
+                    const int up = v.occ(md.off + d * N + b);
+                    if (within(C, up, pw) && within(C, up, t)) {
+                        const int pos = atomicAdd(&wc.n, 1);
+                        if (ORDER && pos < CAND_CAP) wc.tmp[pos] = Cand{C.pid[t], C.pid[up], 0, d, b};
                     }
-                    if (i == N - 2 - b) {                      // kind 1: t = D_q, q = N-2-b
-                        const int t1 = v.occ(ts + 1);
-                        if (d2(C, t1, pw) <= C.lim2 && d2(C, t, t1) <= C.lim2) {
-                            if (out && cnt < CAND_CAP) out[cnt] = Cand{C.pid[t], C.pid[t1], 1, d, i};
-                            ++cnt;
-                        }
+                }
+                if (i == N - 2 - b) {                      // kind 1: t = D_q, q = N-2-b
+                    const int t1 = v.occ(ts + 1);
+                    if (within(C, t1, pw) && within(C, t, t1)) {
+                        const int pos = atomicAdd(&wc.n, 1);
+                        if (ORDER && pos < CAND_CAP) wc.tmp[pos] = Cand{C.pid[t], C.pid[t1], 1, d, i};
                     }
                 }
             }
-    return cnt;
+        }
+    }
+    __syncwarp();
+    const int n = wc.n;
+    if (__any_sync(FULL_MASK, bad) || n > CAND_CAP) {
+        err |= ERR_DB_CAPACITY;
+        return -1;
+    }
+    if (ORDER) {
+        for (int j = lane; j < n; j += 32) {       // rank by the (unique) key pair
+            const Cand cj = wc.tmp[j];
+            int r = 0;
+            for (int i = 0; i < n; ++i) {
+                const Cand ci = wc.tmp[i];
+                r += (ci.key < cj.key) || (ci.key == cj.key && ci.key2 < cj.key2);
+            }
+            wc.cand[r] = cj;
+        }
+        __syncwarp();
+    }
+    return n;
 }
 
 // FENE log term of a bond of length r (kg_params.fene_qmin continuation beyond r*)
@@ -148,99 +197,129 @@ __device__ double bend(const DBC &C, const V &v, int chain, int i)
 
 __device__ __forceinline__ DBC make_dbc(const SimDev &S, const StageDev &st, int m, const double *x,
                                         const int *pid, const int *cell, const int *start, const int *list,
-                                        double T)
+                                        const float4 *rec, double T)
 {
     DBC C;
-    C.x = x; C.Mp = S.Mp; C.pid = pid; C.cell = cell; C.start = start; C.list = list;
+    C.x = x; C.Mp = S.Mp; C.pid = pid; C.cell = cell; C.start = start; C.list = list; C.rec = rec;
     C.md = S.melt[m]; C.melt = m; C.lim2 = S.db_lim2; C.kfene = st.kfene; C.R0 = sqrt(st.R0sq); C.T = T; C.qmin = st.qmin;
     C.nexp = st.n;
     return C;
 }
 
-// cells a and b at most R cells apart along every axis (periodic)
-__device__ __forceinline__ bool cells_near(int a, int b, int off, int n, int R)
-{
-    a -= off; b -= off;
-    const int ax = a % n, ay = (a / n) % n, az = a / (n * n);
-    const int bx = b % n, by = (b / n) % n, bz = b / (n * n);
-    int dx = abs(ax - bx), dy = abs(ay - by), dz = abs(az - bz);
-    dx = min(dx, n - dx); dy = min(dy, n - dy); dz = min(dz, n - dz);
-    return dx <= R && dy <= R && dz <= R;
-}
-
 // Ordered validation and commit, one block per melt (P: re-evaluation policy).
-// An attempt is re-evaluated against the current topology when an earlier
-// accepted swap of the sweep touched one of its two chains, or put a junction
-// monomer within P::radius cells of one of the attempt's junction monomers.
-// P provides: init (block-wide, before the walk), radius, and reeval (called
-// by every thread; it leaves the new record in `out`).
+// An attempt's speculative record is stale when an earlier accepted swap of
+// the sweep touched one of its two chains or put a junction monomer within
+// P::radius cells of one of the attempt's junction monomers (cells carry the
+// sweep's stamp in `mark`).  The walk finds the next attempts that are stale
+// or accepted with a block-wide scan, re-evaluates up to one stale attempt
+// per warp against the current topology, then takes them in order: the
+// re-evaluations before the first acceptance are final, the first accepted
+// swap is committed, and the scan resumes after it.  The result is that of
+// the strictly sequential loop over attempts.  P provides init (block-wide),
+// radius, batch (the most warps that may re-evaluate at once) and reeval (one
+// whole warp; lane 0 leaves the new record in `out`).
 template <class P>
 __device__ void db_commit_body(P &pol, const SimDev &S, const StageDev &stg, const double *__restrict__ x,
                                const int *__restrict__ pid, const int *__restrict__ cell,
                                const int *__restrict__ start, const int *__restrict__ list,
-                               const int *__restrict__ koff, const Attempt *__restrict__ att,
-                               int *__restrict__ occ, int *__restrict__ curmap, int *__restrict__ img,
-                               int *__restrict__ dirty, long long *__restrict__ stats, long long sweep,
-                               unsigned *flags, int *old_occ)
+                               const float4 *__restrict__ rec, const int *__restrict__ koff,
+                               const Attempt *__restrict__ att, int *__restrict__ occ, int *__restrict__ curmap,
+                               int *__restrict__ img, int *__restrict__ dirty, int *__restrict__ mark, int stamp,
+                               long long *__restrict__ stats, long long sweep, unsigned *flags, int *old_occ)
 {
-    __shared__ int jcell[JCAP];
-    __shared__ int njc;
-    __shared__ Attempt a_s;
-    __shared__ int need_s, sh[6];
-    __shared__ long long n_acc, n_empty, n_re;
+    constexpr int MAXB = 32;
+    __shared__ Attempt bres[MAXB];
+    __shared__ int bidx[MAXB], bstale[MAXB], wcnt[32];
+    __shared__ int nb_s, sh[6];
+    __shared__ unsigned long long n_acc, n_empty, n_re;
+    __shared__ long long empty_adj;
     __shared__ int stop_s;
-    const int m = blockIdx.x;
-    if (threadIdx.x == 0) stop_s = flags[0] != 0;  // one reading for the whole block
+    const int m = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    if (tid == 0) stop_s = flags[0] != 0;          // one reading for the whole block
     __syncthreads();
     if (stop_s) {                                  // a latched error stops the sweep
-        if (threadIdx.x == 0) for (int k = 0; k < 4; ++k) stats[4 * m + k] = 0;
+        if (tid == 0) for (int k = 0; k < 4; ++k) stats[4 * m + k] = 0;
         return;
     }
     const MeltDev &md = S.melt[m];
-    const int N = md.N, off = md.off, Mp = S.Mp, tid = threadIdx.x;
-    const DBC C = make_dbc(S, stg, m, x, pid, cell, start, list, stg.T);
+    const int N = md.N, off = md.off, Mp = S.Mp;
+    const DBC C = make_dbc(S, stg, m, x, pid, cell, start, list, rec, stg.T);
     const ViewMap V{occ, curmap};
     pol.init();
     const int R = pol.radius(md);
-    if (tid == 0) { njc = 0; n_acc = n_empty = n_re = 0; }
+    const int B = min(min(nw, pol.batch()), MAXB);
+    if (tid == 0) { n_acc = n_empty = n_re = 0; empty_adj = 0; }
     __syncthreads();
     const int k0 = koff[m], K = koff[m + 1] - k0;
-    for (int kk = 0; kk < K; ++kk) {
-        if (tid == 0) {
-            a_s = att[k0 + kk];
-            need_s = dirty[off + a_s.c * N] || ((a_s.flags & 1) && dirty[off + a_s.d * N]) || njc > JCAP - 4;
-        }
+    {   // empty proposals among the speculative records (corrected as re-evaluations are adopted)
+        unsigned long long e = 0;
+        for (int k = tid; k < K; k += blockDim.x) e += !(att[k0 + k].flags & 1);
+        atomicAdd(&n_empty, e);
+    }
+    int pos = 0;
+    while (pos < K) {
+        // 1. the next (up to B) stale or accepted attempts at or after pos, in order
+        if (tid == 0) nb_s = 0;
         __syncthreads();
-        bool near = false;
-        if (!need_s) {
-            const int nj = njc;
-            for (int j = tid; j < nj; j += blockDim.x) {
+        for (int base = pos;; base += blockDim.x) {
+            const int k = base + tid;
+            bool inter = false, stale = false;
+            if (k < K) {
+                const Attempt &a = att[k0 + k];
+                stale = dirty[off + a.c * N] || ((a.flags & 1) && dirty[off + a.d * N]);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int p = a_s.jp[q];
-                    if (p >= 0 && cells_near(jcell[j], cell[p], md.dbcell_off, md.ndb, R)) near = true;
-                }
+                for (int q = 0; q < 4; ++q)
+                    if (a.jp[q] >= 0 && mark[cell[a.jp[q]]] == stamp) stale = true;
+                inter = stale || (a.flags & 2);
             }
-        }
-        const bool need = __syncthreads_or(near || need_s);
-        if (need) {
-            pol.reeval(C, V, S, sweep, kk, k0 + kk, a_s, flags);
-            if (tid == 0) ++n_re;
-        }
-        __syncthreads();
-        if (!(a_s.flags & 1)) {
-            if (tid == 0) ++n_empty;
-        } else if (a_s.flags & 2) {
-            const int kind = a_s.kind, A = a_s.A, B = a_s.B, pA = a_s.pA, pB = a_s.pB;
-            const int baseA = off + A * N, baseB = off + B * N;
-            for (int i = tid; i < N; i += blockDim.x) {
-                old_occ[i] = occ[baseA + i];
-                old_occ[N + i] = occ[baseB + i];
+            const unsigned bal = __ballot_sync(FULL_MASK, inter);
+            if (lane == 0) wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int before = nb_s;
+            for (int w = 0; w < warp; ++w) before += wcnt[w];
+            const int o = before + __popc(bal & ((1u << lane) - 1u));
+            if (inter && o < B) {
+                bidx[o] = k;
+                bstale[o] = stale;
             }
             __syncthreads();
-            for (int i = tid; i < 2 * N; i += blockDim.x) {
-                const int s = i < N ? baseA + i : baseB + (i - N);
-                const int src = swap_slot(s, kind, A, B, pA, pB, N, off);
+            if (tid == 0) {
+                int tot = nb_s;
+                for (int w = 0; w < nw; ++w) tot += wcnt[w];
+                nb_s = min(tot, B);
+            }
+            __syncthreads();
+            if (nb_s >= B || base + (int)blockDim.x >= K) break;
+        }
+        const int nb = nb_s;
+        if (nb == 0) break;                        // everything after pos is final as evaluated
+        // 2. stale ones re-evaluated against the current topology, one warp each
+        if (warp < nb) {
+            const int k = bidx[warp];
+            if (bstale[warp]) pol.reeval(C, V, S, sweep, k, k0 + k, warp, bres[warp], flags);
+            else if (lane == 0) bres[warp] = att[k0 + k];
+        }
+        __syncthreads();
+        // 3. in order: adopt the re-evaluations up to the first acceptance and commit it
+        int next = bidx[nb - 1] + 1;
+        for (int i = 0; i < nb; ++i) {
+            const Attempt a = bres[i];
+            if (bstale[i] && tid == 0) {
+                ++n_re;
+                empty_adj += (long long)!(a.flags & 1) - (long long)!(att[k0 + bidx[i]].flags & 1);
+            }
+            if (!(a.flags & 2)) continue;
+            const int kind = a.kind, A = a.A, Bc = a.B, pA = a.pA, pB = a.pB;
+            const int baseA = off + A * N, baseB = off + Bc * N;
+            for (int j = tid; j < N; j += blockDim.x) {
+                old_occ[j] = occ[baseA + j];
+                old_occ[N + j] = occ[baseB + j];
+            }
+            __syncthreads();
+            for (int j = tid; j < 2 * N; j += blockDim.x) {
+                const int s = j < N ? baseA + j : baseB + (j - N);
+                const int src = swap_slot(s, kind, A, Bc, pA, pB, N, off);
                 const int val = src - baseA < N && src >= baseA ? old_occ[src - baseA] : old_occ[N + src - baseB];
                 occ[s] = val;
                 curmap[val] = s;
@@ -259,15 +338,15 @@ __device__ void db_commit_body(P &pol, const SimDev &S, const StageDev &stg, con
                                         + img[d * Mp + f] - img[d * Mp + an]);
             }
             __syncthreads();
-            for (int i = tid; i < 2 * N; i += blockDim.x) {
+            for (int j = tid; j < 2 * N; j += blockDim.x) {
                 int seg = -1, s;
-                if (i < N) {
-                    s = baseA + i;
-                    if (i > pA) seg = 0;
+                if (j < N) {
+                    s = baseA + j;
+                    if (j > pA) seg = 0;
                 } else {
-                    const int j = i - N;
-                    s = baseB + j;
-                    if ((kind == 0 && j > pA) || (kind == 1 && j <= pB)) seg = 1;
+                    const int jj = j - N;
+                    s = baseB + jj;
+                    if ((kind == 0 && jj > pA) || (kind == 1 && jj <= pB)) seg = 1;
                 }
                 if (seg >= 0) {
                     const int p = occ[s];
@@ -275,22 +354,37 @@ __device__ void db_commit_body(P &pol, const SimDev &S, const StageDev &stg, con
                     for (int d = 0; d < 3; ++d) img[d * Mp + p] += sh[3 * seg + d];
                 }
             }
+            // stamp the cells within R of the four junction monomers
+            const int n = md.ndb, W = 2 * R + 1;
+            for (int q = 0; q < 4; ++q) {
+                const int p = a.jp[q];
+                if (p < 0) continue;
+                const int c0 = cell[p] - md.dbcell_off;
+                const int cx = c0 % n, cy = (c0 / n) % n, cz = c0 / (n * n);
+                for (int t = tid; t < W * W * W; t += blockDim.x) {
+                    const int dx = t % W - R, dy = (t / W) % W - R, dz = t / (W * W) - R;
+                    const int xx = ((cx + dx) % n + n) % n, yy = ((cy + dy) % n + n) % n;
+                    const int zz = ((cz + dz) % n + n) % n;
+                    mark[md.dbcell_off + (zz * n + yy) * n + xx] = stamp;
+                }
+            }
             if (tid == 0) {
                 dirty[baseA] = 1;
                 dirty[baseB] = 1;
-                for (int q = 0; q < 4; ++q)
-                    if (a_s.jp[q] >= 0 && njc < JCAP) jcell[njc++] = cell[a_s.jp[q]];
                 ++n_acc;
             }
+            next = bidx[i] + 1;
+            break;
         }
-        pol.after(a_s, k0 + kk);
+        pos = next;
         __syncthreads();
     }
+    __syncthreads();
     if (tid == 0) {
         stats[4 * m + 0] = K;
-        stats[4 * m + 1] = n_empty;
-        stats[4 * m + 2] = n_acc;
-        stats[4 * m + 3] = n_re;
+        stats[4 * m + 1] = (long long)n_empty + empty_adj;
+        stats[4 * m + 2] = (long long)n_acc;
+        stats[4 * m + 3] = (long long)n_re;
         if (n_acc) atomicOr(flags + 1, 1u);
     }
 }

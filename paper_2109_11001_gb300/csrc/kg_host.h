@@ -70,6 +70,9 @@ struct kg_ctx {
     // double-bridging
     int ncell_db = 0;
     int *dbcell = nullptr, *dbrank = nullptr, *dbcount = nullptr, *dbstart = nullptr, *dblist = nullptr;
+    float4 *dbrec = nullptr;     // binary32 records on the DB grid (swap-bond prefilter)
+    int *dbmark = nullptr;       // per DB cell: stamp of the last sweep that changed bonds near it
+    int db_stamp = 0;
     void *att = nullptr;         // kg::Attempt[att_cap]
     long long att_cap = 0;
     int *koff = nullptr;         // [n_melts+1] attempt offsets
@@ -151,6 +154,7 @@ void db_sweep(kg_ctx *c, const std::vector<long long> &K, long long *host_stats 
 void db_bin(kg_ctx *c, const std::vector<long long> &K);     // attempt offsets + the >= 1.3 sigma grid
 void db_finish(kg_ctx *c, long long *host_stats);             // box shifts, chain partners, stats to host
 int db_max_chain_len(const kg_ctx *c);
+int next_stamp(kg_ctx *c);                                    // stamp of a new sweep's cell marks
 
 // kg_learned.cu
 void db_sweep_learned(kg_ctx *c, const std::vector<long long> &K, double lambda, long long *host_stats);

@@ -51,9 +51,11 @@ struct MeltDev {
     double h, invh;
     float hf;
     float nl_lo, nl_hi;      // binary32 prefilter: r^2 < nl_lo in, r^2 >= nl_hi out
-    // double-bridging grid (cells >= db_bond_max)
+    // double-bridging grid (cells >= db_bond_max); binary32 records on it decide
+    // the swap-bond criterion outside the band [db_lo, db_hi) around db_bond_max^2
     int ndb, dbcell_off;
     double hdb, invhdb;
+    float hdbf, db_lo, db_hi;
 };
 
 // Parameters of the current potential stage (Eqs. 6, 9, 10) and thermostat.

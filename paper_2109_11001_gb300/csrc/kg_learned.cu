@@ -45,84 +45,18 @@ struct LearnedArgs {
     double *logf, *logt;                // per-attempt log staging (null: no log)
     int *logn;
     const unsigned long long *bmax2;    // longest bond squared, binary64 bits
+    const float4 *rec;                  // binary32 records on the DB grid (swap-bond prefilter)
 };
 
 // per-warp shared scratch of one proposal evaluation
-struct __align__(16) WarpProp {
+struct __align__(16) WarpProp : WarpCand {
     double pi[CAND_CAP];
     double dE[CAND_CAP];
     float s[CAND_CAP];
-    Cand tmp[CAND_CAP];
-    Cand cand[CAND_CAP];
     __nv_bfloat16 F[CAND_CAP * S1];     // features of the candidates, bf16 rows
-    int n;
 };
 
 constexpr unsigned FULL = 0xffffffffu;
-
-// Admissible partners of bond (c, b) in view v, ordered by (key, key2), in
-// wp.cand.  Returns |P|, or -1 (error bit set) on a capacity overflow.
-template <class V>
-__device__ int warp_partners(const DBC &C, const V &v, int c, int b, WarpProp &wp, unsigned &err)
-{
-    const int lane = threadIdx.x & 31;
-    const MeltDev &md = C.md;
-    const int N = md.N;
-    const int us = md.off + c * N + b;
-    const int pu = v.occ(us), pw = v.occ(us + 1);
-    if (d2(C, pu, pw) > C.lim2) return 0;
-    if (lane == 0) wp.n = 0;
-    __syncwarp();
-    bool bad = false;
-    if (lane < 27) {
-        const int n = md.ndb, c0 = C.cell[pu] - md.dbcell_off;
-        const int cx = c0 % n, cy = (c0 / n) % n, cz = c0 / (n * n);
-        const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
-        const int cell = md.dbcell_off + (((cz + dz + n) % n) * n + (cy + dy + n) % n) * n + (cx + dx + n) % n;
-        const int b0 = C.start[cell], e = C.start[cell + 1];
-        if (e - b0 > MAX_CELL_OCC) {
-            bad = true;
-        } else {
-            for (int k = b0; k < e; ++k) {
-                const int t = C.list[k];
-                const int ts = v.cur(t), r = ts - md.off, d = r / N, i = r - d * N;
-                if (d == c) continue;
-                if (d2(C, pu, t) > C.lim2) continue;
-                if (i == b + 1) {                          // kind 0: t = D_{b+1}
-                    const int up = v.occ(md.off + d * N + b);
-                    if (d2(C, up, pw) <= C.lim2 && d2(C, up, t) <= C.lim2) {
-                        const int pos = atomicAdd(&wp.n, 1);
-                        if (pos < CAND_CAP) wp.tmp[pos] = Cand{C.pid[t], C.pid[up], 0, d, b};
-                    }
-                }
-                if (i == N - 2 - b) {                      // kind 1: t = D_q, q = N-2-b
-                    const int t1 = v.occ(ts + 1);
-                    if (d2(C, t1, pw) <= C.lim2 && d2(C, t, t1) <= C.lim2) {
-                        const int pos = atomicAdd(&wp.n, 1);
-                        if (pos < CAND_CAP) wp.tmp[pos] = Cand{C.pid[t], C.pid[t1], 1, d, i};
-                    }
-                }
-            }
-        }
-    }
-    __syncwarp();
-    const int n = wp.n;
-    if (__any_sync(FULL, bad) || n > CAND_CAP) {
-        err |= ERR_DB_CAPACITY;
-        return -1;
-    }
-    for (int j = lane; j < n; j += 32) {           // rank by the (unique) key pair
-        const Cand cj = wp.tmp[j];
-        int r = 0;
-        for (int i = 0; i < n; ++i) {
-            const Cand ci = wp.tmp[i];
-            r += (ci.key < cj.key) || (ci.key == cj.key && ci.key2 < cj.key2);
-        }
-        wp.cand[r] = cj;
-    }
-    __syncwarp();
-    return n;
-}
 
 __device__ __forceinline__ void sort4(double *v)
 {
@@ -204,7 +138,7 @@ __device__ int proposal(const DBC &C, const V &v, const MlpSmem &W, WarpProp &wp
                         int b, bool features, long long log_att, unsigned &err)
 {
     const int lane = threadIdx.x & 31;
-    const int n = warp_partners(C, v, c, b, wp, err);
+    const int n = warp_partners<true>(C, v, c, b, wp, err);
     if (n <= 0) return n;
     const bool net = la.lambda < 1.0;
     if (net || features) {
@@ -368,7 +302,7 @@ __global__ void __launch_bounds__(32 * EVAL_WARPS) k_dbl_eval(const SimDev *__re
     if (g >= koff[S.n_melts]) return;
     int m = 0;
     while (g >= koff[m + 1]) ++m;
-    const DBC C = make_dbc(S, *stp, m, x, pid, cell, start, list, stp->T);
+    const DBC C = make_dbc(S, *stp, m, x, pid, cell, start, list, la.rec, stp->T);
     unsigned err = 0;
     const Attempt a = learned_eval(C, ViewMap{comp_of, slot_of}, W, wps[warp], la, S.seed, sweep, g - koff[m], g, err);
     if (lane == 0) {
@@ -377,11 +311,14 @@ __global__ void __launch_bounds__(32 * EVAL_WARPS) k_dbl_eval(const SimDev *__re
     }
 }
 
-// learned proposal: warp 0 re-evaluates; the reach of an evaluation sets the radius
+// learned proposal: up to LEARN_BATCH warps re-evaluate at once; the reach of
+// an evaluation sets the radius
+constexpr int LEARN_BATCH = 4;
+
 struct LearnedPolicy {
     LearnedArgs la;
     MlpSmem *W;
-    WarpProp *wp;
+    WarpProp *wp;                                  // LEARN_BATCH of them
     double lim;                                    // swap bond limit (1.3)
     __device__ void init()
     {
@@ -396,19 +333,17 @@ struct LearnedPolicy {
         const double reach = 2.0 * lim + 3.0 * fmax(bmax, lim);
         return (int)ceil(reach * md.invhdb) + 1;
     }
-    __device__ void reeval(const DBC &C, const ViewMap &V, const SimDev &S, long long sweep, int kk, int g,
+    __device__ int batch() const { return LEARN_BATCH; }
+    __device__ void reeval(const DBC &C, const ViewMap &V, const SimDev &S, long long sweep, int kk, int g, int warp,
                            Attempt &out, unsigned *flags)
     {
-        if (threadIdx.x < 32) {
-            unsigned err = 0;
-            const Attempt a = learned_eval(C, V, *W, *wp, la, S.seed, sweep, kk, g, err);
-            if (threadIdx.x == 0) {
-                out = a;
-                if (err) atomicOr(flags, err);
-            }
+        unsigned err = 0;
+        const Attempt a = learned_eval(C, V, *W, wp[warp], la, S.seed, sweep, kk, g, err);
+        if ((threadIdx.x & 31) == 0) {
+            out = a;
+            if (err) atomicOr(flags, err);
         }
     }
-    __device__ void after(const Attempt &, int) {}
 };
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -419,16 +354,17 @@ __global__ void __launch_bounds__(256) k_dbl_commit(const SimDev *__restrict__ S
                                                    const int *__restrict__ list, const int *__restrict__ koff,
                                                    const Attempt *__restrict__ att, int *__restrict__ occ,
                                                    int *__restrict__ curmap, int *__restrict__ img,
-                                                   int *__restrict__ dirty, long long *__restrict__ stats,
-                                                   long long sweep, unsigned *flags, LearnedArgs la, int maxN)
+                                                   int *__restrict__ dirty, int *__restrict__ mark, int stamp,
+                                                   long long *__restrict__ stats, long long sweep, unsigned *flags,
+                                                   LearnedArgs la, int maxN)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     int *old_occ = reinterpret_cast<int *>(smem);
     const size_t o1 = align16(sizeof(int) * 2 * (size_t)maxN);
     LearnedPolicy pol{la, reinterpret_cast<MlpSmem *>(smem + o1),
                       reinterpret_cast<WarpProp *>(smem + o1 + sizeof(MlpSmem)), sqrt(Sp->db_lim2)};
-    db_commit_body(pol, *Sp, *stp, x, pid, cell, start, list, koff, att, occ, curmap, img, dirty, stats, sweep,
-                   flags, old_occ);
+    db_commit_body(pol, *Sp, *stp, x, pid, cell, start, list, la.rec, koff, att, occ, curmap, img, dirty, mark,
+                   stamp, stats, sweep, flags, old_occ);
 }
 
 // longest bond of all melts, squared, as ordered binary64 bits
@@ -510,7 +446,7 @@ __global__ void __launch_bounds__(32) k_dbl_proposal(const SimDev *__restrict__ 
     mlp_load(W, la.w);
     __syncthreads();
     const SimDev &S = *Sp;
-    const DBC C = make_dbc(S, *stp, melt, x, pid, cell, start, list, stp->T);
+    const DBC C = make_dbc(S, *stp, melt, x, pid, cell, start, list, la.rec, stp->T);
     unsigned err = 0;
     // log rows of "attempt" 0 go to out_d[0 .. 48*24) (features) and out_d[48*24 ..) (targets)
     la.logf = out_d;
@@ -554,6 +490,7 @@ static LearnedArgs make_args(kg_ctx *c, double lambda, bool log)
     la.logt = log ? c->logt : nullptr;
     la.logn = log ? c->logn : nullptr;
     la.bmax2 = c->bmax2;
+    la.rec = c->dbrec;
     return la;
 }
 
@@ -576,11 +513,11 @@ void db_sweep_learned(kg_ctx *c, const std::vector<long long> &K, double lambda,
             att, c->sweep, c->flags, la);
     }
     const int maxN = db_max_chain_len(c);
-    const size_t sm = align16(sizeof(int) * 2 * (size_t)maxN) + sizeof(MlpSmem) + sizeof(WarpProp);
+    const size_t sm = align16(sizeof(int) * 2 * (size_t)maxN) + sizeof(MlpSmem) + LEARN_BATCH * sizeof(WarpProp);
     cudaFuncSetAttribute(k_dbl_commit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_dbl_commit<<<nm, 256, sm, st>>>(c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart, c->dblist, c->koff,
-                                      att, c->comp_of, c->slot_of, c->img, c->dirty, c->db_stats, c->sweep,
-                                      c->flags, la, maxN);
+                                      att, c->comp_of, c->slot_of, c->img, c->dirty, c->dbmark, next_stamp(c),
+                                      c->db_stats, c->sweep, c->flags, la, maxN);
     c->launches += 3;
     if (log && tot > 0) {
         k_log_append<<<1, 1024, 0, st>>>(c->logn, (int)tot, c->logf, c->logt, c->trainf, c->traint, c->train_cap,

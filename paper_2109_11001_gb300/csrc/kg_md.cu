@@ -406,23 +406,30 @@ __global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, c
     rank[s] = atomicAdd(count + c, 1);
 }
 
-// DB grid: cell of each particle from its wrapped position (cells >= 1.3 sigma)
+// DB grid: cell of each particle from its wrapped position (cells >= 1.3
+// sigma), and its binary32 record (offset from the cell corner, cell
+// coordinates) for the swap-bond prefilter
 __global__ void __launch_bounds__(256) k_bin_db(const SimDev *__restrict__ Sp, const double *__restrict__ x,
                                                int *__restrict__ cellid, int *__restrict__ rank,
-                                               int *__restrict__ count, const int *__restrict__ slot_of)
+                                               int *__restrict__ count, const int *__restrict__ slot_of,
+                                               float4 *__restrict__ rec)
 {
     const SimDev &S = *Sp;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S.M) return;
     const MeltDev &md = S.melt[melt_of(S, slot_of[s])];
     int cell[3];
+    float off[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double xd = x[d * S.Mp + s];
         const double w = xd - md.L * floor(xd * md.invL);
         int c = (int)(w * md.invhdb);
-        cell[d] = c < 0 ? 0 : (c >= md.ndb ? md.ndb - 1 : c);
+        c = c < 0 ? 0 : (c >= md.ndb ? md.ndb - 1 : c);
+        cell[d] = c;
+        off[d] = (float)(w - (double)c * md.hdb);
     }
+    rec[s] = make_float4(off[0], off[1], off[2], __uint_as_float(pack_code(cell[0], cell[1], cell[2])));
     const int c = md.dbcell_off + (cell[2] * md.ndb + cell[1]) * md.ndb + cell[0];
     cellid[s] = c;
     rank[s] = atomicAdd(count + c, 1);
