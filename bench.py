@@ -274,12 +274,14 @@ def run_ours(args, world, rank, local):
         step0, sweep0 = kg.kg_get_counters(ctx)
         best = kg.kg_autotune(params, [xs], [vs], kg.stage(12.0, -1, DT), 100, local, stream.cuda_stream,
                               kg.torch_allocator())
-        tuning = {"skin": best.skin, "block_size": best.block_size, "trials": best.trials,
+        tuning = {"skin": best.skin, "block_size": best.block_size,
+                  "threads_per_monomer": best.threads_per_monomer, "trials": best.trials,
                   "ms_per_md_step": best.ms_per_step}
         log(f"autotune: {tuning}")
         kg.kg_destroy(ctx)
         params = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=prec, seed=11 + rank,
-                                fene_qmin=FENE_QMIN, skin=best.skin, block_size=best.block_size)
+                                fene_qmin=FENE_QMIN, skin=best.skin, block_size=best.block_size,
+                                threads_per_monomer=best.threads_per_monomer)
         ctx = kg.kg_create(params, local, stream.cuda_stream, kg.torch_allocator())
         kg.kg_set_potential_schedule(ctx, [kg.stage(12.0, 10 ** 15, DT)])
         kg.kg_load_config(ctx, 0, xs, vs)

@@ -100,6 +100,9 @@ typedef struct {
                                  or 256 (<= 0: 128); results do not depend on it        */
     int precision;            /* KG_FP64 or KG_MIXED                                    */
     int flags;                /* KG_FLAG_*                                              */
+    int threads_per_monomer;  /* threads sharing one monomer's step in KG_MIXED: 1 or 2
+                                 (<= 0: 1; KG_FP64 always uses 1); results do not
+                                 depend on it beyond binary32 summation order           */
 } kg_params;
 
 /* One stage of the potential schedule (Eqs. 6, 9, 10, 19-20). */
@@ -211,13 +214,15 @@ typedef struct {
     int block_size;       /* threads per block of the fused step kernel                */
     double ms_per_step;   /* measured wall time of one MD step with these settings     */
     int trials;           /* configurations timed                                       */
+    int threads_per_monomer;  /* 1 or 2 (KG_MIXED; always 1 for KG_FP64)                */
 } kg_tuning;
 
 /* Autotuner: for the melts of *p in the states x[m], v[m] ((3, M_m) arrays,
  * host or device; v may be NULL) under `stage`, time trial_steps MD steps
  * (graph-captured, after a warm-up of the same length) for every candidate
- * skin in {0.25, 0.3, 0.4, 0.5, 0.6} and block size in {64, 128, 256}, each in
- * a scratch context of its own; return the fastest in *best.  The settings do
+ * skin in {0.25, 0.3, 0.4, 0.5, 0.6}, block size in {64, 128, 256} and, for
+ * KG_MIXED, threads per monomer in {1, 2}, each in a scratch context of its
+ * own; return the fastest in *best.  The settings do
  * not change results beyond floating-point summation order.  Synchronises. */
 kg_status kg_autotune(const kg_params *p, const double *const *x, const double *const *v,
                       const kg_stage *stage, int trial_steps, int device, void *stream,

@@ -42,7 +42,8 @@ class kg_params(C.Structure):
                 ("gamma", C.c_double), ("R0", C.c_double), ("l0", C.c_double),
                 ("db_bond_max", C.c_double), ("r_mc", C.c_double), ("skin", C.c_double),
                 ("fene_qmin", C.c_double), ("seed", C.c_ulonglong), ("sort_interval", C.c_int),
-                ("block_size", C.c_int), ("precision", C.c_int), ("flags", C.c_int)]
+                ("block_size", C.c_int), ("precision", C.c_int), ("flags", C.c_int),
+                ("threads_per_monomer", C.c_int)]
 
 
 class kg_stage(C.Structure):
@@ -59,7 +60,8 @@ class kg_obs(C.Structure):
 
 
 class kg_tuning(C.Structure):
-    _fields_ = [("skin", C.c_double), ("block_size", C.c_int), ("ms_per_step", C.c_double), ("trials", C.c_int)]
+    _fields_ = [("skin", C.c_double), ("block_size", C.c_int), ("ms_per_step", C.c_double), ("trials", C.c_int),
+                ("threads_per_monomer", C.c_int)]
 
 
 class kg_db_stats(C.Structure):
@@ -301,11 +303,12 @@ def kg_strerror(status):
 # ---- convenience: parameter construction ----
 
 def make_params(melts, precision=KG_MIXED, seed=1, T=1.0, gamma=1.0, R0=1.5, l0=0.960897, db_bond_max=1.3,
-                r_mc=1e-3, skin=0.3, flags=0, fene_qmin=0.0, sort_interval=0, block_size=0):
+                r_mc=1e-3, skin=0.3, flags=0, fene_qmin=0.0, sort_interval=0, block_size=0,
+                threads_per_monomer=0):
     """melts: iterable of (n_chains, chain_len, box, kappa)."""
     arr = (kg_melt * len(melts))(*[kg_melt(int(a), int(b), float(c), float(d)) for a, b, c, d in melts])
     p = kg_params(len(melts), arr, T, gamma, R0, l0, db_bond_max, r_mc, skin, float(fene_qmin), int(seed),
-                  int(sort_interval), int(block_size), int(precision), int(flags))
+                  int(sort_interval), int(block_size), int(precision), int(flags), int(threads_per_monomer))
     p._keep = arr
     return p
 

@@ -232,6 +232,9 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->sort_interval = p->sort_interval > 0 ? p->sort_interval : 200;
     c->block = p->block_size > 0 ? p->block_size : 128;
     if (c->block != 64 && c->block != 128 && c->block != 256) { delete c; return KG_ERR_INVALID_ARG; }
+    c->tpm = p->threads_per_monomer > 0 ? p->threads_per_monomer : 1;
+    if (c->tpm != 1 && c->tpm != 2) { delete c; return KG_ERR_INVALID_ARG; }
+    if (p->precision != KG_MIXED) c->tpm = 1;
     c->precision = p->precision;
     if (allocator && allocator->alloc && allocator->free) { c->alloc = *allocator; c->have_alloc = true; }
     auto fail = [&](kg_status s) { kg_destroy(c); return s; };
@@ -949,6 +952,8 @@ kg_status kg_autotune(const kg_params *p, const double *const *x, const double *
     if (!p || !x || !stage || !best || trial_steps < kg::GRAPH_STEPS) return KG_ERR_INVALID_ARG;
     const double skins[] = {0.25, 0.3, 0.4, 0.5, 0.6};
     const int blocks[] = {64, 128, 256};
+    const int tpms[] = {1, 2};
+    const int ntpm = p->precision == KG_MIXED ? 2 : 1;
     best->ms_per_step = 1e300;
     best->trials = 0;
     cudaEvent_t e0, e1;
@@ -956,10 +961,12 @@ kg_status kg_autotune(const kg_params *p, const double *const *x, const double *
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KG_ERR_CUDA;
     kg_status out = KG_OK;
     for (double skin : skins) {
-        for (int blk : blocks) {
+        for (int bt = 0; bt < 3 * ntpm; ++bt) {
+            const int blk = blocks[bt % 3], tpm = tpms[bt / 3];
             kg_params q = *p;
             q.skin = skin;
             q.block_size = blk;
+            q.threads_per_monomer = tpm;
             kg_ctx *c = nullptr;
             kg_status s = kg_create(&c, &q, device, stream, allocator);
             if (s == KG_ERR_INVALID_ARG) continue;               // this skin does not fit the box
@@ -987,6 +994,7 @@ kg_status kg_autotune(const kg_params *p, const double *const *x, const double *
                 best->ms_per_step = per;
                 best->skin = skin;
                 best->block_size = blk;
+                best->threads_per_monomer = tpm;
             }
         }
         if (out != KG_OK) break;

@@ -50,6 +50,7 @@ struct kg_ctx {
     long long graph_replays = 0;
     long long sort_interval = 200;
     int block = 128;             // threads per block of the fused step kernel
+    int tpm = 1;                 // threads per monomer of the mixed step kernel (1 or 2)
     float4 *recb = nullptr;      // build records: offset from the Verlet-cell corner, cell coordinates
     float4 *recs = nullptr;      // the same in cell order (Verlet-list build)
     float4 *dlt[2] = {nullptr, nullptr};   // (mixed) displacement since the build

@@ -168,33 +168,39 @@ __device__ __forceinline__ void pair_term(const StageDev &st, T rc2, T3 d, T3 &F
     }
 }
 
-// Conservative force on slot s (chain position i of N) and, with ENERGY, its
-// shares of the energies: e[0] pair (1/2 per pair), e[1] bond (1/2 per bond),
-// e[2] bending (the angle whose vertex is s), e[3] virial (1/2 per pair/bond).
+// Pair forces on s from its Verlet-list entries k = k0, k0 + stride, ...
+// (both directions are stored), four entries in flight.
 template <bool ENERGY, class G>
-__device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, const StageDev &st,
-                                                   const MeltDev &md, int s, int4 bp,
-                                                   const unsigned *__restrict__ nl, int cnt,
-                                                   double *e, unsigned &err)
+__device__ __forceinline__ void pair_forces(const G &g, const SimDev &S, const StageDev &st, int s,
+                                            const unsigned *__restrict__ nl, int cnt, int k0, int stride,
+                                            typename G::T3 &F, double *e)
 {
     using T = typename G::T;
     using T3 = typename G::T3;
-    T3 F = mk<T>(0, 0, 0);
     const T rc2 = (T)S.rc2;
-    // pairs (Verlet list, both directions stored), four entries in flight
-    const unsigned *__restrict__ col = nl + s;
-    const size_t Mp = (size_t)S.Mp;
-    int k = 0;
-    for (; k + 4 <= cnt; k += 4) {
-        const unsigned e0 = __ldg(col + k * Mp), e1 = __ldg(col + (k + 1) * Mp);
-        const unsigned e2 = __ldg(col + (k + 2) * Mp), e3 = __ldg(col + (k + 3) * Mp);
+    const size_t Mp = (size_t)S.Mp, step = (size_t)stride * Mp;
+    const unsigned *__restrict__ col = nl + s + (size_t)k0 * Mp;
+    int k = k0;
+    for (; k + 3 * stride < cnt; k += 4 * stride, col += 4 * step) {
+        const unsigned e0 = __ldg(col), e1 = __ldg(col + step);
+        const unsigned e2 = __ldg(col + 2 * step), e3 = __ldg(col + 3 * step);
         const T3 d0 = g.rel_nl(e0), d1 = g.rel_nl(e1), d2 = g.rel_nl(e2), d3 = g.rel_nl(e3);
         pair_term<ENERGY>(st, rc2, d0, F, e);
         pair_term<ENERGY>(st, rc2, d1, F, e);
         pair_term<ENERGY>(st, rc2, d2, F, e);
         pair_term<ENERGY>(st, rc2, d3, F, e);
     }
-    for (; k < cnt; ++k) pair_term<ENERGY>(st, rc2, g.rel_nl(__ldg(col + k * Mp)), F, e);
+    for (; k < cnt; k += stride, col += step) pair_term<ENERGY>(st, rc2, g.rel_nl(__ldg(col)), F, e);
+}
+
+// Bond (Eq. 10) and bending (Eq. 4) forces on s from its chain partners.
+template <bool ENERGY, class G>
+__device__ __forceinline__ void bonded_forces(const G &g, const StageDev &st, const MeltDev &md,
+                                              typename G::T rc2, int4 bp, typename G::T3 &F, double *e,
+                                              unsigned &err)
+{
+    using T = typename G::T;
+    using T3 = typename G::T3;
     // chain neighbours: bp = (s-2, s-1, s+1, s+2) along the chain, -1 past an end
     const bool hm2 = bp.x >= 0, hm1 = bp.y >= 0, hp1 = bp.z >= 0, hp2 = bp.w >= 0;
     T3 rm2 = mk<T>(0, 0, 0), rm1 = mk<T>(0, 0, 0), rp1 = mk<T>(0, 0, 0), rp2 = mk<T>(0, 0, 0);
@@ -257,6 +263,21 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
             F.z += kap * (Bm2.z * inv - c2 * Bm1.z);
         }
     }
+}
+
+// Conservative force on slot s (chain position i of N) and, with ENERGY, its
+// shares of the energies: e[0] pair (1/2 per pair), e[1] bond (1/2 per bond),
+// e[2] bending (the angle whose vertex is s), e[3] virial (1/2 per pair/bond).
+template <bool ENERGY, class G>
+__device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, const StageDev &st,
+                                                   const MeltDev &md, int s, int4 bp,
+                                                   const unsigned *__restrict__ nl, int cnt,
+                                                   double *e, unsigned &err)
+{
+    using T = typename G::T;
+    typename G::T3 F = mk<T>(0, 0, 0);
+    pair_forces<ENERGY>(g, S, st, s, nl, cnt, 0, 1, F, e);
+    bonded_forces<ENERGY>(g, st, md, (T)S.rc2, bp, F, e, err);
     return F;
 }
 
@@ -264,6 +285,12 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
 // fused MD step: forces at x_n, then u <- u + dt F_n, x <- x + dt u
 // F_n = F_c - gamma u + sqrt(2 gamma T / dt) g_n,  g_n = Philox normals.
 // ---------------------------------------------------------------------------
+// TPM threads per monomer (1 or 2, adjacent lanes): the lanes split the
+// Verlet list (entries k = sub, sub + TPM, ...); with two, lane 0 adds the
+// bonded terms and lane 1 draws the noise while the other works, the forces
+// are combined with a shuffle, and lane 0 writes the binary32 state while
+// lane 1 writes the binary64 positions.
+template <int TPM>
 __global__ void __launch_bounds__(256) k_step_mixed(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
                                                    const float4 *__restrict__ shtab, double *__restrict__ x,
                                                    float *__restrict__ u, const float4 *__restrict__ recb,
@@ -277,36 +304,57 @@ __global__ void __launch_bounds__(256) k_step_mixed(const SimDev *__restrict__ S
     const SimDev &S = *Sp;
     const StageDev &st = *stp;
     const long long step = *stepp;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = t / TPM, sub = t % TPM;
+    const bool live = s < S.M;
     bool rebuild = false;
     unsigned err = 0;
-    if (s < S.M) {
+    float3 F = make_float3(0.f, 0.f, 0.f), gn = make_float3(0.f, 0.f, 0.f);
+    float4 rb = make_float4(0.f, 0.f, 0.f, 0.f), dc = rb;
+    if (live) {
         const int slot = __ldg(slot_of + s);
         const int m = melt_of(S, slot);
         const MeltDev &md = S.melt[m];
-        const int rel = slot - md.off;
         GeoMixed g{pcur, shtab};
         g.melt(md, m);
         // own record rebuilt from its parts: the same bits the last step wrote to pcur
-        const float4 rb = __ldg(recb + s), dc = dcur[s];
+        rb = __ldg(recb + s);
+        dc = dcur[s];
         g.pi = make_float4(rb.x + dc.x, rb.y + dc.y, rb.z + dc.z, rb.w);
-        float3 F = force_on<false>(g, S, st, md, s, __ldg(bp + s), nl, __ldg(nn + s), nullptr, err);
-        const float3 gn = gauss3_f(draw(S.seed, m, 0, (unsigned long long)step, (uint32_t)rel));
+        pair_forces<false>(g, S, st, s, nl, __ldg(nn + s), sub, TPM, F, nullptr);
+        if (sub == 0) bonded_forces<false>(g, st, md, S.rc2f, __ldg(bp + s), F, nullptr, err);
+        if (sub == TPM - 1)
+            gn = gauss3_f(draw(S.seed, m, 0, (unsigned long long)step, (uint32_t)(slot - md.off)));
+    }
+    if (TPM == 2) {                        // every lane takes part: s is shared by lanes 2i, 2i+1
+        F.x += __shfl_xor_sync(0xffffffffu, F.x, 1);
+        F.y += __shfl_xor_sync(0xffffffffu, F.y, 1);
+        F.z += __shfl_xor_sync(0xffffffffu, F.z, 1);
+        const int src = (threadIdx.x & 31) | 1;
+        gn.x = __shfl_sync(0xffffffffu, gn.x, src);
+        gn.y = __shfl_sync(0xffffffffu, gn.y, src);
+        gn.z = __shfl_sync(0xffffffffu, gn.z, src);
+    }
+    if (live) {
         const int Mp = S.Mp;
         float3 v = make_float3(u[s], u[Mp + s], u[2 * Mp + s]);
         v.x += st.dtf * (F.x - st.gammaf * v.x + st.ampf * gn.x);
         v.y += st.dtf * (F.y - st.gammaf * v.y + st.ampf * gn.y);
         v.z += st.dtf * (F.z - st.gammaf * v.z + st.ampf * gn.z);
-        u[s] = v.x; u[Mp + s] = v.y; u[2 * Mp + s] = v.z;
-        x[s] += st.dt * (double)v.x;
-        x[Mp + s] += st.dt * (double)v.y;
-        x[2 * Mp + s] += st.dt * (double)v.z;
-        float4 d = dc;
-        d.x += st.dtf * v.x; d.y += st.dtf * v.y; d.z += st.dtf * v.z;
-        dnext[s] = d;
-        pnext[s] = make_float4(rb.x + d.x, rb.y + d.y, rb.z + d.z, rb.w);
-        rebuild = d.x * d.x + d.y * d.y + d.z * d.z > S.half_skin2f;
-        if (!isfinite(v.x + v.y + v.z)) err |= ERR_NONFINITE;
+        if (sub == TPM - 1) {
+            x[s] += st.dt * (double)v.x;
+            x[Mp + s] += st.dt * (double)v.y;
+            x[2 * Mp + s] += st.dt * (double)v.z;
+        }
+        if (sub == 0) {
+            u[s] = v.x; u[Mp + s] = v.y; u[2 * Mp + s] = v.z;
+            float4 d = dc;
+            d.x += st.dtf * v.x; d.y += st.dtf * v.y; d.z += st.dtf * v.z;
+            dnext[s] = d;
+            pnext[s] = make_float4(rb.x + d.x, rb.y + d.y, rb.z + d.z, rb.w);
+            rebuild = d.x * d.x + d.y * d.y + d.z * d.z > S.half_skin2f;
+            if (!isfinite(v.x + v.y + v.z)) err |= ERR_NONFINITE;
+        }
     }
     if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(flags + 1, 1u);
     if (err) atomicOr(flags, err);
@@ -878,10 +926,14 @@ static void launch_rebuild(kg_ctx *c, cudaStream_t st)
 static void launch_step_kernel(kg_ctx *c, cudaStream_t st, int cur)
 {
     const int nb = nblk(c->M, c->block);
-    if (c->precision == KG_MIXED)
-        k_step_mixed<<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->shtab, c->x, (float *)c->u, c->recb,
-                                              c->dlt[cur], c->dlt[cur ^ 1], c->pg[cur], c->pg[cur ^ 1], c->nl,
-                                              c->nn, c->slot_of, c->bp, c->flags, c->d_step);
+    if (c->precision == KG_MIXED && c->tpm == 2)
+        k_step_mixed<2><<<nblk(2LL * c->M, c->block), c->block, 0, st>>>(
+            c->d_sim, c->d_stage, c->shtab, c->x, (float *)c->u, c->recb, c->dlt[cur], c->dlt[cur ^ 1], c->pg[cur],
+            c->pg[cur ^ 1], c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
+    else if (c->precision == KG_MIXED)
+        k_step_mixed<1><<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->shtab, c->x, (float *)c->u, c->recb,
+                                                 c->dlt[cur], c->dlt[cur ^ 1], c->pg[cur], c->pg[cur ^ 1], c->nl,
+                                                 c->nn, c->slot_of, c->bp, c->flags, c->d_step);
     else
         k_step_f64<<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->x, (double *)c->u, c->pos64[cur], c->pos64[cur ^ 1],
                                        c->xb, c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);

@@ -32,10 +32,10 @@ def kg():
 
 
 @contextlib.contextmanager
-def context(kg, melts, precision, seed=11, schedule=None, flags=0):
+def context(kg, melts, precision, seed=11, schedule=None, flags=0, **kw):
     import torch
     p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa) for m in melts], precision=precision,
-                       seed=seed, flags=flags)
+                       seed=seed, flags=flags, **kw)
     ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
     try:
         if schedule is not None:
@@ -102,6 +102,28 @@ def test_trajectory_10_steps(kg, precision, n_exp, dt):
     assert np.abs(x - xo).max() < 1e-4
     if precision == 0:
         assert np.abs(x - xo).max() < 1e-9
+
+
+@pytest.mark.parametrize("case", ["cfg1", "ragged"])
+@pytest.mark.parametrize("block", [64, 256])
+def test_two_threads_per_monomer(kg, case, block):
+    """Mixed step with two threads per monomer (split Verlet list, shuffled
+    forces): 10 steps against the oracle at the trajectory bar, and against
+    the one-thread kernel, which differs only in binary32 summation order."""
+    m = CASES[case]()
+    dt = 0.002
+    out = {}
+    for tpm in (1, 2):
+        with context(kg, [m], 1, schedule=[kg.stage(2.0, 100, dt)], threads_per_monomer=tpm,
+                     block_size=block) as ctx:
+            kg.kg_step(ctx, 10)
+            x = np.zeros_like(m.x)
+            kg.kg_get_config(ctx, 0, x)
+            out[tpm] = x
+    xo, uo = m.x.copy(), m.v.copy()
+    O.run(oparams(m, 2.0, dt=dt), xo, uo, 0, 10)
+    assert np.abs(out[2] - xo).max() < 1e-4
+    assert np.abs(out[2] - out[1]).max() < 1e-5
 
 
 def _db_case(kappa=0.5, seed=31, n_chains=40, N=20):
@@ -334,4 +356,5 @@ def test_autotune_returns_a_working_setting(kg):
     best = kg.kg_autotune(p, [m.x], [m.v], kg.stage(2.0, -1, 0.002), 20, 0,
                           torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
     assert best.trials >= 6 and best.block_size in (64, 128, 256) and 0.25 <= best.skin <= 0.6
+    assert best.threads_per_monomer in (1, 2)
     assert 0 < best.ms_per_step < 100
