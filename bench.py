@@ -385,7 +385,8 @@ def run_ours(args, world, rank, local):
     achieved = bpm * m.M / (avg_ms * 1e-3) / 1e9
     peak, src = peaks()
     traffic = None
-    if NCU_TRAFFIC["bytes_per_monomer"] and NCU_TRAFFIC["kg_md_sha1"] == src_sha1():
+    if (NCU_TRAFFIC["bytes_per_monomer"] and NCU_TRAFFIC["kg_md_sha1"] == src_sha1()
+            and args.precision == "mixed" and abs(run_skin - 0.5) < 1e-12):
         traffic = NCU_TRAFFIC["bytes_per_monomer"] * m.M
     log("oracle sample")
     t_md, t_db = oracle_sample(m, 2, 8)
