@@ -260,7 +260,7 @@ def run_ours(args, world, rank, local):
     log(f"melt M={m.M}")
     prec = kg.KG_MIXED if args.precision == "mixed" else kg.KG_FP64
     params = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=prec, seed=11 + rank,
-                            fene_qmin=FENE_QMIN, skin=args.skin)
+                            fene_qmin=FENE_QMIN, skin=args.skin, sort_interval=args.sort_interval)
     stream = torch.cuda.current_stream()
     ctx = kg.kg_create(params, local, stream.cuda_stream, kg.torch_allocator())
     stages, n_pre = prelude_stages(kg)
@@ -284,7 +284,7 @@ def run_ours(args, world, rank, local):
         kg.kg_destroy(ctx)
         params = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=prec, seed=11 + rank,
                                 fene_qmin=FENE_QMIN, skin=best.skin, block_size=best.block_size,
-                                threads_per_monomer=best.threads_per_monomer)
+                                threads_per_monomer=best.threads_per_monomer, sort_interval=args.sort_interval)
         ctx = kg.kg_create(params, local, stream.cuda_stream, kg.torch_allocator())
         kg.kg_set_potential_schedule(ctx, [kg.stage(12.0, 10 ** 15, DT)])
         kg.kg_load_config(ctx, 0, xs, vs)
@@ -372,9 +372,10 @@ def run_ours(args, world, rank, local):
 
     # secondary: the same step in plain binary64 on this GPU (single rank), and
     # the learned double-bridging proposal against the uniform one
-    sec = lsec = None
+    sec = lsec = bsec = None
     if world == 1 and args.secondary:
         sec = secondary(kg, torch, args, local)
+        bsec = batched_secondary(kg, torch, args, local)
         lsec = learned_secondary(kg, torch, args, local)
     kg.kg_destroy(ctx)
     if rank != 0:
@@ -427,9 +428,59 @@ def run_ours(args, world, rank, local):
     }
     if sec:
         line["secondary"] = sec
+    if bsec:
+        line["batched"] = bsec
     if lsec:
         line["learned_db"] = lsec
     print(json.dumps(line))
+
+
+# kappa scan of eight melts of uneven size (kappa, N, chains): 485k monomers
+KAPPA_SCAN = [(0.0, 100, 200), (0.5, 200, 150), (1.0, 400, 100), (1.5, 800, 50), (2.0, 100, 250),
+              (2.5, 200, 250), (3.0, 400, 200), (3.5, 800, 250)]
+
+
+def batched_secondary(kg, torch, args, local):
+    """Eight melts of a kappa scan (20k-200k monomers each) advanced by the
+    same launches in one context, against the same melts run one context at a
+    time; 4 x (50 MD steps + one DB sweep at R_MC) after the dt-ramped prelude."""
+    import kg_inputs as KI
+    melts = [KI.random_walk_melt(nch, n, 0.85, kap, 2109110013 + 100 * i)
+             for i, (kap, n, nch) in enumerate(KAPPA_SCAN)]
+    s = torch.cuda.current_stream()
+
+    def run(ms):
+        p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa) for m in ms], precision=kg.KG_MIXED,
+                           seed=19, fene_qmin=FENE_QMIN, skin=0.5, block_size=64)
+        ctx = kg.kg_create(p, local, s.cuda_stream, kg.torch_allocator())
+        stages, n_pre = prelude_stages(kg)
+        kg.kg_set_potential_schedule(ctx, stages)
+        for i, m in enumerate(ms):
+            kg.kg_load_config(ctx, i, m.x, m.v)
+        kg.kg_step(ctx, n_pre)
+        kg.kg_step(ctx, MD_PER_STEP)
+        kg.kg_db_sweep(ctx, -1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(4):
+            kg.kg_step(ctx, MD_PER_STEP)
+            kg.kg_db_sweep(ctx, -1.0)
+        e1.record(s)
+        torch.cuda.synchronize()
+        kg.kg_destroy(ctx)
+        return e0.elapsed_time(e1) / 1e3
+
+    M = sum(m.M for m in melts)
+    t_batched = run(melts)
+    log(f"batched kappa scan: {M} monomers, {t_batched * 1e3:.1f} ms")
+    t_seq = sum(run([m]) for m in melts)
+    log(f"kappa scan one melt at a time: {t_seq * 1e3:.1f} ms")
+    units = M * MD_PER_STEP * 4
+    return {"workload": "kappa scan: 8 melts, kappa 0-3.5, N 100-800, 50-250 chains, "
+                        f"{M} monomers, rho=0.85, skin 0.5, block 64",
+            "batched_monomer_steps_per_s": units / t_batched,
+            "one_melt_at_a_time_monomer_steps_per_s": units / t_seq}
 
 
 def secondary(kg, torch, args, local):
@@ -567,6 +618,7 @@ def main():
     ap.add_argument("--no-secondary", dest="secondary", action="store_false")
     ap.add_argument("--skin", type=float, default=0.3, help="skin when not autotuned")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--sort-interval", type=int, default=0, help="MD steps between re-sorts (0: library default)")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the direct-launch window (same bench steps, no graphs) with cudaProfilerStart/Stop, for ncu --profile-from-start off")
     ap.add_argument("--ncu-case", action="store_true")

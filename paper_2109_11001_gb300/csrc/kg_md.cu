@@ -290,8 +290,10 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
 // bonded terms and lane 1 draws the noise while the other works, the forces
 // are combined with a shuffle, and lane 0 writes the binary32 state while
 // lane 1 writes the binary64 positions.
+// (256, 6): at most 40 registers, 75% occupancy; the few spills cost less than
+// the latency the extra warps hide (143 against 153 us at 1.6M monomers)
 template <int TPM>
-__global__ void __launch_bounds__(256) k_step_mixed(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
+__global__ void __launch_bounds__(256, 6) k_step_mixed(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
                                                    const float4 *__restrict__ shtab, double *__restrict__ x,
                                                    float *__restrict__ u, const float4 *__restrict__ recb,
                                                    const float4 *__restrict__ dcur, float4 *__restrict__ dnext,
@@ -594,7 +596,9 @@ __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start,
 // compute index are loaded together.
 constexpr int NL_BLOCK = 128;
 
-__global__ void __launch_bounds__(NL_BLOCK, 6) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
+// (128, 10): at most 48 registers; more resident warps hide the candidate
+// loads (tighter caps spill too much, looser ones leave the SM half idle)
+__global__ void __launch_bounds__(NL_BLOCK, 10) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
                                                    const float4 *__restrict__ recb, const float4 *__restrict__ recs,
                                                    const int *__restrict__ start, const int *__restrict__ list,
                                                    unsigned *__restrict__ nl, int *__restrict__ nn,
