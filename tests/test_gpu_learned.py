@@ -248,3 +248,53 @@ def test_learned_sweep_rejects_bad_lambda(kg):
                 kg.kg_db_sweep_learned_k(ctx, [10], lam)
         with pytest.raises(kg.KGError):               # nothing logged yet
             kg.kg_mlp_train(ctx, 1, 16, 1e-3)
+
+
+def test_trained_network_raises_acceptance(kg):
+    """What the trained network gains over the uniform partner draw.  A
+    learned proposal can only help when a drawn bond has two or more
+    admissible partners; that is frequent only for short chains (at N = 800
+    the lists hold at most one swap), so this uses 10,000 chains of N = 10 in
+    the soft n = 2 stage.  The network is trained online on uniform sweeps of
+    the same melt; then each round saves the state, runs a uniform sweep, restores
+    the state and the sweep index, and runs a learned sweep (lambda = 0.1): both
+    see the same configuration and the same bond draws, so single-partner draws
+    cancel and the paired difference of accepted swaps measures the gain."""
+    import torch
+    m = KI.random_walk_melt(10000, 10, 0.85, 2.0, 77)
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=1, seed=17, fene_qmin=0.01)
+    ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+    try:
+        kg.kg_set_potential_schedule(ctx, [kg.stage(2.0, 300, 0.0005), kg.stage(2.0, 300, 0.001),
+                                           kg.stage(2.0, 300, 0.002), kg.stage(2.0, 10 ** 15, 0.005)])
+        kg.kg_load_config(ctx, 0, m.x, m.v)
+        kg.kg_step(ctx, 1200)
+        K = m.M // 10
+        kg.kg_mlp_log(ctx, 4_000_000)
+        for _ in range(10):                        # log: uniform proposal through the learned path
+            kg.kg_step(ctx, 50)
+            kg.kg_db_sweep_learned_k(ctx, [K], 1.0)
+        kg.kg_mlp_set_weights(ctx, mlp.init(0))
+        kg.kg_mlp_train(ctx, 800, 2048, 2e-3)
+        kg.kg_mlp_log(ctx, 0)
+        x, v, pid = np.zeros_like(m.x), np.zeros_like(m.v), np.zeros(m.M, dtype=np.int32)
+        diff, acc_u, acc_l, ne_u, ne_l = [], 0, 0, 0, 0
+        for _ in range(12):
+            kg.kg_step(ctx, 50)
+            kg.kg_get_config(ctx, 0, x, v, pid)
+            step, sweep = kg.kg_get_counters(ctx)
+            su = kg.kg_db_sweep_k(ctx, [K])
+            kg.kg_load_config(ctx, 0, x, v, pid)
+            kg.kg_set_counters(ctx, step, sweep)
+            sl = kg.kg_db_sweep_learned_k(ctx, [K], 0.1)
+            diff.append(sl.accepted - su.accepted)
+            acc_u += su.accepted
+            acc_l += sl.accepted
+            ne_u += su.attempted - su.empty
+            ne_l += sl.attempted - sl.empty
+    finally:
+        kg.kg_destroy(ctx)
+    d = np.asarray(diff, dtype=float)
+    z = d.mean() / (d.std(ddof=1) / np.sqrt(len(d)))
+    gain = (acc_l / ne_l) / (acc_u / ne_u) - 1.0
+    assert z > 4.0 and gain > 0.02, (d, z, gain)
