@@ -272,6 +272,39 @@ def test_full_size_80k(kg):
     assert st.accepted == acc and np.array_equal(pid, pido)
 
 
+def test_full_size_1600k(kg):
+    """The benchmark melt (1000 chains x 1600, 1.6M monomers, kappa = 3.5) in
+    the benchmark's launch configuration (mixed precision, skin 0.5, block 128,
+    FENE continuation q = 0.01): Verlet list bit-exact, forces, a 400-attempt
+    DB sweep (attempt, empty and accepted counts and the topology bit-exact),
+    then positions two steps later, all against the oracle on the same input."""
+    m = KI.make(5)
+    dt = 0.0005
+    with context(kg, [m], 1, schedule=[kg.stage(2.0, 100, dt)], skin=0.5, block_size=128,
+                 fene_qmin=0.01) as ctx:
+        offs, nbr = kg.kg_get_nlist(ctx, 0, m.M)
+        F = np.zeros_like(m.x)
+        kg.kg_forces(ctx, 0, F)
+        st = kg.kg_db_sweep_k(ctx, [400])
+        pid = np.zeros(m.M, dtype=np.int32)
+        kg.kg_get_config(ctx, 0, None, None, pid)
+        kg.kg_step(ctx, 2)
+        x = np.zeros_like(m.x)
+        kg.kg_get_config(ctx, 0, x)
+    q = oparams(m, 2.0, dt=dt, fene_qmin=0.01)
+    oo, on = O.nlist(q, m.x, 2.0 ** (1 / 6) + 0.5)
+    assert np.array_equal(offs, oo) and np.array_equal(nbr, on)
+    del oo, on, offs, nbr
+    Fo, _ = O.forces(q, m.x)
+    assert _force_err(F, Fo) < 1e-5
+    xo, uo, pido = m.x.copy(), m.v.copy(), np.arange(m.M, dtype=np.int32)
+    a, e, acc = O.db_sweep(q, xo, uo, pido, 0, 400)
+    assert (st.attempted, st.empty, st.accepted) == (a, e, acc)
+    assert np.array_equal(pid, pido)
+    O.run(q, xo, uo, 0, 2)
+    assert np.abs(x - xo).max() < 1e-4
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-5)])
 def test_regularised_fene_forces(kg, precision, tol):
     # a few bonds pulled past r* = R0 sqrt(1 - qmin) and past R0 itself
