@@ -304,6 +304,19 @@ kg_status kg_schedule_paper(double kappa, int chain_len, double dt, double scale
 void kg_destroy(kg_ctx *c);
 const char *kg_strerror(kg_status s);
 
+/* Monomer mean-squared displacement of `melt` (App. B, Fig. 11): kg_msd_reset
+ * records every monomer's current unwrapped position (allocates the reference,
+ * 48 bytes per monomer, on first use); kg_msd returns
+ *     msd = (1/M) sum_i |r_i(t) - r_i(t_reset)|^2
+ * in binary64, summed in a fixed order.  The box shifts that double-bridging
+ * swaps add to moved segments (to keep new bonds minimum-image) are added to
+ * the reference as well, so a swap, which relabels monomers but moves none,
+ * leaves the MSD unchanged.  Running without kg_db_sweep is the paper's
+ * core-softening-only ablation.  kg_msd synchronises; KG_ERR_INVALID_ARG
+ * before the first kg_msd_reset. */
+kg_status kg_msd_reset(kg_ctx *c, int melt);
+kg_status kg_msd(kg_ctx *c, int melt, double *msd);
+
 /* Largest n_chains * chain_len that kg_r2n_noalloc accepts. */
 #define KG_NOALLOC_MAX_MONOMERS 2097152
 

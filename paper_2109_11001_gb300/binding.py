@@ -27,7 +27,7 @@ EXPORTS = ["kg_create", "kg_load_config", "kg_get_config", "kg_set_potential_sch
            "kg_set_counters", "kg_get_nlist", "kg_forces", "kg_profile", "kg_profile_read", "kg_autotune", "kg_kn", "kg_schedule_paper", "kg_destroy",
            "kg_strerror", "kg_r2n_noalloc", "kg_mlp_set_weights", "kg_mlp_get_weights", "kg_mlp_forward",
            "kg_mlp_loss_grad", "kg_mlp_log", "kg_mlp_log_read", "kg_mlp_train", "kg_db_sweep_learned",
-           "kg_db_sweep_learned_k", "kg_db_proposal"]
+           "kg_db_sweep_learned_k", "kg_db_proposal", "kg_msd_reset", "kg_msd"]
 
 KG_MLP_NPARAM = 5825
 KG_DB_CAND_MAX = 48
@@ -115,6 +115,8 @@ def load(path: str = LIB_PATH):
         "kg_destroy": (None, [p]),
         "kg_strerror": (C.c_char_p, [i]),
         "kg_r2n_noalloc": (i, [p, ll, i, i, p, p]),
+        "kg_msd_reset": (i, [p, i]),
+        "kg_msd": (i, [p, i, C.POINTER(d)]),
         "kg_mlp_set_weights": (i, [p, p]),
         "kg_mlp_get_weights": (i, [p, p]),
         "kg_mlp_forward": (i, [p, p, ll, p]),
@@ -218,6 +220,16 @@ def kg_db_sweep_k(ctx, attempts):
     st = kg_db_stats()
     _check(load().kg_db_sweep_k(ctx, a.ctypes.data, C.byref(st)), "kg_db_sweep_k")
     return st
+
+
+def kg_msd_reset(ctx, melt):
+    return _check(load().kg_msd_reset(ctx, int(melt)), "kg_msd_reset")
+
+
+def kg_msd(ctx, melt):
+    out = C.c_double()
+    _check(load().kg_msd(ctx, int(melt), C.byref(out)), "kg_msd")
+    return out.value
 
 
 def kg_observables(ctx, melt, r2n=None, bond_hist=None, cos_hist=None, n_bins=0):

@@ -412,7 +412,7 @@ void kg_destroy(kg_ctx *c)
                     c->comp_of, c->bp, c->img, c->dirty, c->db_stats, c->scratch, c->flags, c->fout, c->partials,
                     c->r2tmp, c->hist, c->mlp_master, c->mlp_adam, c->mlp_grad, c->mlp_blob, c->mlp_w2t,
                     c->logf, c->logt, c->logn, c->trainf, c->traint, c->d_train_head, c->tr_buf, c->bmax2,
-                    c->d_io};
+                    c->d_io, c->msd_ref};
     for (void *b : bufs) dev_free(c, b);
     dev_free(c, c->d_step);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -865,6 +865,32 @@ kg_status kg_forces(kg_ctx *c, int melt, double *F, double *e4)
         for (int b = 0; b < nb; ++b)
             for (int k = 0; k < 4; ++k) e4[k] += part[(size_t)b * 5 + k];
     }
+    return KG_OK;
+}
+
+kg_status kg_msd_reset(kg_ctx *c, int melt)
+{
+    kg_status s = check_melt(c, melt);
+    if (s != KG_OK) return s;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    return kg::msd_reset(c, melt) ? KG_OK : KG_ERR_OOM;
+}
+
+kg_status kg_msd(kg_ctx *c, int melt, double *msd)
+{
+    kg_status s = check_melt(c, melt);
+    if (s != KG_OK) return s;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    if (!msd || !c->msd_ref) return KG_ERR_INVALID_ARG;
+    const int nb = kg::msd_blocks(c, melt);
+    if (nb > c->partials_cap) return KG_ERR_CAPACITY;
+    kg::msd_eval(c, melt, c->partials);
+    std::vector<double> part((size_t)nb);
+    KG_TRY(cudaMemcpyAsync(part.data(), c->partials, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if ((s = read_flags(c, pinned_flags())) != KG_OK) return s;
+    double sum = 0.0;
+    for (double v : part) sum += v;                  // block order: deterministic
+    *msd = sum / (double)c->sim.melt[melt].M;
     return KG_OK;
 }
 

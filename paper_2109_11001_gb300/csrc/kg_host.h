@@ -111,6 +111,7 @@ struct kg_ctx {
     int *hist = nullptr;         // histogram counts
     int hist_cap = 0;
     double *fout = nullptr;      // forces for kg_forces
+    double *msd_ref = nullptr;   // [3][Mp] reference positions of kg_msd (+ [3][Mp] re-sort scratch)
 
     // instrumentation
     long long launches = 0;      // kernels launched since creation
@@ -173,5 +174,9 @@ bool mlp_train(kg_ctx *c, int iters, int batch, double lr, double *loss_dev);
 // kg_obs.cu
 void r2n_eval(kg_ctx *c, int melt, double *out_dev);
 void hist_eval(kg_ctx *c, int melt, int nbins, int *out_dev);
+bool msd_reset(kg_ctx *c, int melt);                          // allocates the reference on first use
+int msd_blocks(const kg_ctx *c, int melt);
+void msd_eval(kg_ctx *c, int melt, double *part_dev);         // block partial sums of |x - ref|^2
+void msd_permute(kg_ctx *c, const int *order);                // re-sort (no-op before the first reset)
 
 }  // namespace kg

@@ -854,6 +854,7 @@ void md_sort(kg_ctx *c)
         k_sort_finish<double><<<nblk(c->M, 256), 256, 0, c->stream>>>(c->M, Mp, c->x, (double *)c->u, c->pid,
                                                                      c->slot_of, c->comp_of, sx, su, spid, sslot);
     }
+    msd_permute(c, c->clist);
     bonded_partners(c);
     static const unsigned one = 1u;
     cudaMemcpyAsync(c->flags + 1, &one, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream);

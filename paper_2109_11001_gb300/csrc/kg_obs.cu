@@ -95,6 +95,87 @@ void hist_eval(kg_ctx *c, int melt, int nbins, int *out_dev)
 }
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// monomer mean-squared displacement (App. B): ref holds, per compute index,
+// the position at the last kg_msd_reset plus every box shift a
+// double-bridging swap has since added to the unwrapped position, so
+// x - ref is the physical displacement
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_msd_reset(const double *__restrict__ x, double *__restrict__ ref, int Mp,
+                                                  int off, int M)
+{
+    const int j = off + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= off + M) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ref[(size_t)d * Mp + j] = x[(size_t)d * Mp + j];
+}
+
+// block partial sums of |x - ref|^2 in a fixed tree (deterministic)
+__global__ void __launch_bounds__(256) k_msd(const double *__restrict__ x, const double *__restrict__ ref, int Mp,
+                                            int off, int M, double *__restrict__ part)
+{
+    __shared__ double sh[256];
+    const int j = off + blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (j < off + M) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double v = x[(size_t)d * Mp + j] - ref[(size_t)d * Mp + j];
+            s += v * v;
+        }
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// re-sort of the per-monomer state: ref follows its monomers (out[j] = in[order[j]])
+__global__ void __launch_bounds__(256) k_msd_permute(const double *__restrict__ in, double *__restrict__ out,
+                                                    const int *__restrict__ order, int Mp, int M)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int o = order[j];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[(size_t)d * Mp + j] = in[(size_t)d * Mp + o];
+}
+
+static inline int nb256(long long n) { return (int)((n + 255) / 256); }
+
+bool msd_reset(kg_ctx *c, int melt)
+{
+    if (!c->msd_ref) {
+        c->msd_ref = (double *)dev_alloc(c, 6 * (size_t)c->Mp * sizeof(double));
+        if (!c->msd_ref) return false;
+    }
+    const MeltDev &md = c->sim.melt[melt];
+    ++c->launches;
+    k_msd_reset<<<nb256(md.M), 256, 0, c->stream>>>(c->x, c->msd_ref, c->Mp, md.off, md.M);
+    return true;
+}
+
+int msd_blocks(const kg_ctx *c, int melt) { return nb256(c->sim.melt[melt].M); }
+
+void msd_eval(kg_ctx *c, int melt, double *part_dev)
+{
+    const MeltDev &md = c->sim.melt[melt];
+    ++c->launches;
+    k_msd<<<nb256(md.M), 256, 0, c->stream>>>(c->x, c->msd_ref, c->Mp, md.off, md.M, part_dev);
+}
+
+void msd_permute(kg_ctx *c, const int *order)
+{
+    if (!c->msd_ref) return;
+    double *tmp = c->msd_ref + 3 * (size_t)c->Mp;
+    c->launches += 1;
+    k_msd_permute<<<nb256(c->M), 256, 0, c->stream>>>(c->msd_ref, tmp, order, c->Mp, c->M);
+    cudaMemcpyAsync(c->msd_ref, tmp, 3 * (size_t)c->Mp * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+}
+
 // <R^2(n)> without any allocation (kg_r2n_noalloc)
 // ---------------------------------------------------------------------------
 // The per-chain partial sums of k_r2n_chain live in this file-scope array

@@ -272,6 +272,42 @@ def test_full_size_80k(kg):
     assert st.accepted == acc and np.array_equal(pid, pido)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-3)])
+def test_msd_without_db_matches_oracle(kg, precision, tol):
+    """Core-softening-only ablation (no DB sweeps): the monomer MSD after 200
+    steps against its definition (1/M) sum_i |r_i(t) - r_i(0)|^2 on the
+    oracle's trajectory (relative bar: binary64 path 1e-8, mixed 1e-3, the
+    trajectories' own divergence over 200 steps)."""
+    m = KI.make(1)
+    dt = 0.002
+    with context(kg, [m], precision, schedule=[kg.stage(2.0, 10 ** 6, dt)]) as ctx:
+        kg.kg_msd_reset(ctx, 0)
+        assert kg.kg_msd(ctx, 0) == 0.0
+        kg.kg_step(ctx, 200)
+        msd = kg.kg_msd(ctx, 0)
+    xo, uo = m.x.copy(), m.v.copy()
+    O.run(oparams(m, 2.0, dt=dt), xo, uo, 0, 200)
+    want = float(((xo - m.x) ** 2).sum(axis=0).mean())
+    assert msd == pytest.approx(want, rel=tol)
+
+
+def test_msd_is_unchanged_by_db_sweeps(kg):
+    """A swap relabels monomers and shifts moved segments by box vectors but
+    moves no monomer: the MSD before and after sweeps that accept swaps agree,
+    and it still follows the monomers through a re-sort of the state."""
+    m = _db_case(kappa=0.5)
+    with context(kg, [m], 0, schedule=[kg.stage(2.0, 10 ** 6, 0.002)], sort_interval=7) as ctx:
+        kg.kg_msd_reset(ctx, 0)
+        kg.kg_step(ctx, 60)                      # crosses re-sorts
+        before = kg.kg_msd(ctx, 0)
+        acc = 0
+        for _ in range(4):
+            acc += kg.kg_db_sweep_k(ctx, [400]).accepted
+        after = kg.kg_msd(ctx, 0)
+    assert acc > 0
+    assert after == pytest.approx(before, rel=1e-12)
+
+
 def test_full_size_1600k(kg):
     """The benchmark melt (1000 chains x 1600, 1.6M monomers, kappa = 3.5) in
     the benchmark's launch configuration (mixed precision, skin 0.5, block 128,
