@@ -317,6 +317,16 @@ const char *kg_strerror(kg_status s);
 kg_status kg_msd_reset(kg_ctx *c, int melt);
 kg_status kg_msd(kg_ctx *c, int melt, double *msd);
 
+/* Kuhn length from chain statistics (Eq. 14, Sec. II.B): the l_K that
+ * minimises sum_{n = n_lo..n_hi} [r2n[n] / (n l0) - l_K (1 - l_K / (2 n l0)
+ * (1 - exp(-2 n l0 / l_K)))]^2, unweighted (the paper does not state its
+ * weighting).  r2n: host array of N values, r2n[n] = <R^2(n)> as kg_observables
+ * returns it (r2n[0] unused); n_lo, n_hi <= 0 select the paper's N/4 .. N/2.
+ * Host computation (bracketing scan on a log grid, then golden-section search
+ * in log l_K); no context, no device.  KG_ERR_INVALID_ARG on a bad range,
+ * l0 <= 0 or a non-finite value in the range. */
+kg_status kg_fit_lk(const double *r2n, int N, double l0, int n_lo, int n_hi, double *lk);
+
 /* Largest n_chains * chain_len that kg_r2n_noalloc accepts. */
 #define KG_NOALLOC_MAX_MONOMERS 2097152
 

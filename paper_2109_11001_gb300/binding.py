@@ -27,7 +27,7 @@ EXPORTS = ["kg_create", "kg_load_config", "kg_get_config", "kg_set_potential_sch
            "kg_set_counters", "kg_get_nlist", "kg_forces", "kg_profile", "kg_profile_read", "kg_autotune", "kg_kn", "kg_schedule_paper", "kg_destroy",
            "kg_strerror", "kg_r2n_noalloc", "kg_mlp_set_weights", "kg_mlp_get_weights", "kg_mlp_forward",
            "kg_mlp_loss_grad", "kg_mlp_log", "kg_mlp_log_read", "kg_mlp_train", "kg_db_sweep_learned",
-           "kg_db_sweep_learned_k", "kg_db_proposal", "kg_msd_reset", "kg_msd"]
+           "kg_db_sweep_learned_k", "kg_db_proposal", "kg_msd_reset", "kg_msd", "kg_fit_lk"]
 
 KG_MLP_NPARAM = 5825
 KG_DB_CAND_MAX = 48
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
         "kg_r2n_noalloc": (i, [p, ll, i, i, p, p]),
         "kg_msd_reset": (i, [p, i]),
         "kg_msd": (i, [p, i, C.POINTER(d)]),
+        "kg_fit_lk": (i, [p, i, d, i, i, C.POINTER(d)]),
         "kg_mlp_set_weights": (i, [p, p]),
         "kg_mlp_get_weights": (i, [p, p]),
         "kg_mlp_forward": (i, [p, p, ll, p]),
@@ -224,6 +225,14 @@ def kg_db_sweep_k(ctx, attempts):
 
 def kg_msd_reset(ctx, melt):
     return _check(load().kg_msd_reset(ctx, int(melt)), "kg_msd_reset")
+
+
+def kg_fit_lk(r2n, l0=0.960897, n_lo=0, n_hi=0):
+    """Kuhn length of Eq. 14 fitted to <R^2(n)> (r2n[n], r2n[0] unused)."""
+    r = np.ascontiguousarray(r2n, dtype=np.float64)
+    out = C.c_double()
+    _check(load().kg_fit_lk(ptr(r), len(r), float(l0), int(n_lo), int(n_hi), C.byref(out)), "kg_fit_lk")
+    return out.value
 
 
 def kg_msd(ctx, melt):

@@ -868,6 +868,48 @@ kg_status kg_forces(kg_ctx *c, int melt, double *F, double *e4)
     return KG_OK;
 }
 
+// Eq. 14: sum over n of [<R^2(n)>/(n l0) - l_K (1 - l_K/(2 n l0) (1 - exp(-2 n l0/l_K)))]^2
+static double lk_objective(const double *r2n, double l0, int lo, int hi, double lk)
+{
+    double s = 0.0;
+    for (int n = lo; n <= hi; ++n) {
+        const double a = 2.0 * n * l0 / lk;
+        const double w = lk * (1.0 - (1.0 - std::exp(-a)) / a);
+        const double y = r2n[n] / (n * l0);
+        s += (y - w) * (y - w);
+    }
+    return s;
+}
+
+kg_status kg_fit_lk(const double *r2n, int N, double l0, int n_lo, int n_hi, double *lk)
+{
+    if (!r2n || !lk || N < 3 || !(l0 > 0.0)) return KG_ERR_INVALID_ARG;
+    int lo = n_lo > 0 ? n_lo : N / 4, hi = n_hi > 0 ? n_hi : N / 2;
+    lo = std::max(lo, 1);
+    if (hi >= N || lo > hi) return KG_ERR_INVALID_ARG;
+    for (int n = lo; n <= hi; ++n)
+        if (!std::isfinite(r2n[n])) return KG_ERR_INVALID_ARG;
+    // bracket the minimum on a logarithmic grid, then golden-section search in log l_K
+    const double a0 = std::log(1e-3 * l0), a1 = std::log(1e3 * l0 * hi);
+    const int G = 400;
+    int best = 0;
+    double fbest = 1e300;
+    for (int g = 0; g <= G; ++g) {
+        const double f = lk_objective(r2n, l0, lo, hi, std::exp(a0 + (a1 - a0) * g / G));
+        if (f < fbest) { fbest = f; best = g; }
+    }
+    double a = a0 + (a1 - a0) * std::max(best - 1, 0) / G, b = a0 + (a1 - a0) * std::min(best + 1, G) / G;
+    const double r = 0.5 * (std::sqrt(5.0) - 1.0);
+    double c = b - r * (b - a), d = a + r * (b - a);
+    double fc = lk_objective(r2n, l0, lo, hi, std::exp(c)), fd = lk_objective(r2n, l0, lo, hi, std::exp(d));
+    for (int it = 0; it < 200 && b - a > 1e-14; ++it) {
+        if (fc < fd) { b = d; d = c; fd = fc; c = b - r * (b - a); fc = lk_objective(r2n, l0, lo, hi, std::exp(c)); }
+        else { a = c; c = d; fc = fd; d = a + r * (b - a); fd = lk_objective(r2n, l0, lo, hi, std::exp(d)); }
+    }
+    *lk = std::exp(0.5 * (a + b));
+    return KG_OK;
+}
+
 kg_status kg_msd_reset(kg_ctx *c, int melt)
 {
     kg_status s = check_melt(c, melt);
