@@ -317,6 +317,19 @@ const char *kg_strerror(kg_status s);
 kg_status kg_msd_reset(kg_ctx *c, int melt);
 kg_status kg_msd(kg_ctx *c, int melt, double *msd);
 
+/* Static structure factor of `melt` (App. A): S[a] = |sum_j exp(i q_a . r_j)|^2
+ * / M for q_a = 2 pi (h, k, l)_a / L, hkl a host array of nq integer triples
+ * (nq <= 65535), S host.  Phases reduced to whole turns in binary64 and
+ * evaluated in binary32; sums in binary64, fixed order.  Synchronises. */
+kg_status kg_structure_factor(kg_ctx *c, int melt, const int *hkl, int nq, double *S);
+
+/* Pair distribution of `melt` (App. A): g[b] for bins of width r_max / nbins
+ * over [0, r_max), the number of ordered pairs i != j at minimum-image distance
+ * r in the bin (binary64 distance, as the Verlet build defines it) divided by
+ * M rho 4 pi / 3 (r_hi^3 - r_lo^3), rho = M / L^3.  r_max <= L / 2,
+ * nbins <= 2048; g host.  Synchronises. */
+kg_status kg_pair_distribution(kg_ctx *c, int melt, double r_max, int nbins, double *g);
+
 /* Kuhn length from chain statistics (Eq. 14, Sec. II.B): the l_K that
  * minimises sum_{n = n_lo..n_hi} [r2n[n] / (n l0) - l_K (1 - l_K / (2 n l0)
  * (1 - exp(-2 n l0 / l_K)))]^2, unweighted (the paper does not state its

@@ -27,7 +27,8 @@ EXPORTS = ["kg_create", "kg_load_config", "kg_get_config", "kg_set_potential_sch
            "kg_set_counters", "kg_get_nlist", "kg_forces", "kg_profile", "kg_profile_read", "kg_autotune", "kg_kn", "kg_schedule_paper", "kg_destroy",
            "kg_strerror", "kg_r2n_noalloc", "kg_mlp_set_weights", "kg_mlp_get_weights", "kg_mlp_forward",
            "kg_mlp_loss_grad", "kg_mlp_log", "kg_mlp_log_read", "kg_mlp_train", "kg_db_sweep_learned",
-           "kg_db_sweep_learned_k", "kg_db_proposal", "kg_msd_reset", "kg_msd", "kg_fit_lk"]
+           "kg_db_sweep_learned_k", "kg_db_proposal", "kg_msd_reset", "kg_msd", "kg_fit_lk",
+           "kg_structure_factor", "kg_pair_distribution"]
 
 KG_MLP_NPARAM = 5825
 KG_DB_CAND_MAX = 48
@@ -118,6 +119,8 @@ def load(path: str = LIB_PATH):
         "kg_msd_reset": (i, [p, i]),
         "kg_msd": (i, [p, i, C.POINTER(d)]),
         "kg_fit_lk": (i, [p, i, d, i, i, C.POINTER(d)]),
+        "kg_structure_factor": (i, [p, i, p, i, p]),
+        "kg_pair_distribution": (i, [p, i, d, i, p]),
         "kg_mlp_set_weights": (i, [p, p]),
         "kg_mlp_get_weights": (i, [p, p]),
         "kg_mlp_forward": (i, [p, p, ll, p]),
@@ -233,6 +236,20 @@ def kg_fit_lk(r2n, l0=0.960897, n_lo=0, n_hi=0):
     out = C.c_double()
     _check(load().kg_fit_lk(ptr(r), len(r), float(l0), int(n_lo), int(n_hi), C.byref(out)), "kg_fit_lk")
     return out.value
+
+
+def kg_structure_factor(ctx, melt, hkl):
+    """S(q) for integer triples hkl (nq, 3): q = 2 pi (h, k, l) / L."""
+    h = np.ascontiguousarray(hkl, dtype=np.int32).reshape(-1, 3)
+    S = np.zeros(len(h))
+    _check(load().kg_structure_factor(ctx, int(melt), ptr(h), len(h), ptr(S)), "kg_structure_factor")
+    return S
+
+
+def kg_pair_distribution(ctx, melt, r_max, nbins):
+    g = np.zeros(int(nbins))
+    _check(load().kg_pair_distribution(ctx, int(melt), float(r_max), int(nbins), ptr(g)), "kg_pair_distribution")
+    return g
 
 
 def kg_msd(ctx, melt):

@@ -910,6 +910,56 @@ kg_status kg_fit_lk(const double *r2n, int N, double l0, int n_lo, int n_hi, dou
     return KG_OK;
 }
 
+kg_status kg_structure_factor(kg_ctx *c, int melt, const int *hkl, int nq, double *S)
+{
+    kg_status s = check_melt(c, melt);
+    if (s != KG_OK) return s;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    if (!hkl || !S || nq < 1 || nq > 65535) return KG_ERR_INVALID_ARG;
+    int *d_hkl = (int *)dev_alloc(c, sizeof(int) * 3 * (size_t)nq);
+    double *d_part = (double *)dev_alloc(c, sizeof(double) * 2 * 64 * (size_t)nq);
+    double *d_S = (double *)dev_alloc(c, sizeof(double) * (size_t)nq);
+    auto done = [&](kg_status r) { dev_free(c, d_hkl); dev_free(c, d_part); dev_free(c, d_S); return r; };
+    if (!d_hkl || !d_part || !d_S) return done(KG_ERR_OOM);
+    if (cudaMemcpyAsync(d_hkl, hkl, sizeof(int) * 3 * (size_t)nq, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return done(KG_ERR_CUDA);
+    kg::sq_eval(c, melt, d_hkl, nq, d_part, d_S);
+    if (cudaMemcpyAsync(S, d_S, sizeof(double) * (size_t)nq, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return done(KG_ERR_CUDA);
+    return done(read_flags(c, pinned_flags()));
+}
+
+kg_status kg_pair_distribution(kg_ctx *c, int melt, double r_max, int nbins, double *g)
+{
+    kg_status s = check_melt(c, melt);
+    if (s != KG_OK) return s;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    const MeltDev &md = c->sim.melt[melt];
+    if (!g || nbins < 1 || nbins > kg::GR_BINS_MAX || !(r_max > 0.0) || r_max > 0.5 * md.L)
+        return KG_ERR_INVALID_ARG;
+    unsigned long long *d_h = (unsigned long long *)dev_alloc(c, sizeof(unsigned long long) * nbins);
+    if (!d_h) return KG_ERR_OOM;
+    std::vector<long long> K(c->sim.n_melts, 0);
+    kg::db_bin(c, K);                                   // the >= 1.3 sigma grid of the current positions
+    const double dr = r_max / nbins;
+    const int R = (int)std::ceil(r_max * md.invhdb);
+    kg::gr_eval(c, melt, R, r_max, dr, nbins, d_h);
+    std::vector<unsigned long long> h(nbins);
+    kg_status out = KG_OK;
+    if (cudaMemcpyAsync(h.data(), d_h, sizeof(unsigned long long) * nbins, cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+        out = KG_ERR_CUDA;
+    if (out == KG_OK) out = read_flags(c, pinned_flags());
+    dev_free(c, d_h);
+    if (out != KG_OK) return out;
+    const double M = md.M, rho = M / (md.L * md.L * md.L), pi = 3.14159265358979323846;
+    for (int b = 0; b < nbins; ++b) {
+        const double lo = (double)b * dr, hi = (double)(b + 1) * dr;
+        g[b] = (double)h[b] / (M * rho * (4.0 / 3.0 * pi * (hi * hi * hi - lo * lo * lo)));
+    }
+    return KG_OK;
+}
+
 kg_status kg_msd_reset(kg_ctx *c, int melt)
 {
     kg_status s = check_melt(c, melt);

@@ -178,5 +178,8 @@ bool msd_reset(kg_ctx *c, int melt);                          // allocates the r
 int msd_blocks(const kg_ctx *c, int melt);
 void msd_eval(kg_ctx *c, int melt, double *part_dev);         // block partial sums of |x - ref|^2
 void msd_permute(kg_ctx *c, const int *order);                // re-sort (no-op before the first reset)
+void sq_eval(kg_ctx *c, int melt, const int *hkl_dev, int nq, double *part_dev /*[nq][64][2]*/, double *S_dev);
+void gr_eval(kg_ctx *c, int melt, int R, double r_max, double dr, int nbins, unsigned long long *hist_dev);
+constexpr int GR_BINS_MAX = 2048;
 
 }  // namespace kg

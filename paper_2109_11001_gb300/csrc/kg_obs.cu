@@ -176,6 +176,124 @@ void msd_permute(kg_ctx *c, const int *order)
     cudaMemcpyAsync(c->msd_ref, tmp, 3 * (size_t)c->Mp * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
 }
 
+// ---------------------------------------------------------------------------
+// static structure factor (App. A): S(q) = |sum_j exp(i q . r_j)|^2 / M for
+// q = 2 pi (h, k, l) / L.  The phase is reduced to [0, 1) turns in binary64
+// (so unwrapped positions of any size keep their precision) and evaluated by
+// sincospif in binary32; sums are binary64, block trees then block order.
+// ---------------------------------------------------------------------------
+constexpr int SQ_CHUNKS = 64;
+
+__global__ void __launch_bounds__(256) k_sq(const double *__restrict__ x, int Mp, int off, int M, double invL,
+                                           const int *__restrict__ hkl, double *__restrict__ part)
+{
+    __shared__ double sre[256], sim[256];
+    const int q = blockIdx.x;
+    const double h = hkl[3 * q], k = hkl[3 * q + 1], l = hkl[3 * q + 2];
+    double re = 0.0, im = 0.0;
+    for (int r = blockIdx.y * blockDim.x + threadIdx.x; r < M; r += gridDim.y * blockDim.x) {
+        const int j = off + r;
+        const double t = (h * x[j] + k * x[(size_t)Mp + j] + l * x[2 * (size_t)Mp + j]) * invL;
+        float sn, cs;
+        sincospif(2.0f * (float)(t - floor(t)), &sn, &cs);
+        re += cs;
+        im += sn;
+    }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sre[threadIdx.x] += sre[threadIdx.x + w];
+            sim[threadIdx.x] += sim[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * ((size_t)q * gridDim.y + blockIdx.y)] = sre[0];
+        part[2 * ((size_t)q * gridDim.y + blockIdx.y) + 1] = sim[0];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sq_sum(const double *__restrict__ part, int nq, int G, int M,
+                                               double *__restrict__ S)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double re = 0.0, im = 0.0;
+    for (int g = 0; g < G; ++g) {
+        re += part[2 * ((size_t)q * G + g)];
+        im += part[2 * ((size_t)q * G + g) + 1];
+    }
+    S[q] = (re * re + im * im) / (double)M;
+}
+
+void sq_eval(kg_ctx *c, int melt, const int *hkl_dev, int nq, double *part_dev, double *S_dev)
+{
+    const MeltDev &md = c->sim.melt[melt];
+    c->launches += 2;
+    k_sq<<<dim3(nq, SQ_CHUNKS), 256, 0, c->stream>>>(c->x, c->Mp, md.off, md.M, md.invL, hkl_dev, part_dev);
+    k_sq_sum<<<(nq + 255) / 256, 256, 0, c->stream>>>(part_dev, nq, SQ_CHUNKS, md.M, S_dev);
+}
+
+// ---------------------------------------------------------------------------
+// pair distribution (App. A): ordered pairs i != j with minimum-image
+// distance r < r_max, counted in bins of width dr, on the double-bridging cell
+// grid (cells >= 1.3 sigma, stencil of +-R cells, each cell once).  The
+// distance is the binary64 expression ((dx*dx + dy*dy) + dz*dz), dx = d - L
+// rint(d/L), its IEEE square root and bin floor(r / dr): integer counts, so
+// the histogram does not depend on the order of the additions.
+// ---------------------------------------------------------------------------
+constexpr int GR_MAX_BINS = 2048;
+
+__global__ void __launch_bounds__(256) k_gr(const SimDev *__restrict__ Sp, int melt, const double *__restrict__ x,
+                                           const int *__restrict__ cell, const int *__restrict__ start,
+                                           const int *__restrict__ list, int R, double r_max, double dr,
+                                           int nbins, unsigned long long *__restrict__ hist)
+{
+    __shared__ unsigned int sh[GR_MAX_BINS];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0u;
+    __syncthreads();
+    const SimDev &S = *Sp;
+    const MeltDev &md = S.melt[melt];
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < md.M) {
+        const int i = md.off + r, n = md.ndb;
+        const int c0 = cell[i] - md.dbcell_off;
+        const int cx = c0 % n, cy = (c0 / n) % n, cz = c0 / (n * n);
+        const int w = 2 * R + 1 < n ? 2 * R + 1 : n;         // each cell of the stencil once
+        const int o = 2 * R + 1 < n ? -R : 0;
+        for (int a = 0; a < w; ++a)
+            for (int b = 0; b < w; ++b)
+                for (int e = 0; e < w; ++e) {
+                    const int zz = 2 * R + 1 < n ? ((cz + o + a) % n + n) % n : a;
+                    const int yy = 2 * R + 1 < n ? ((cy + o + b) % n + n) % n : b;
+                    const int xx = 2 * R + 1 < n ? ((cx + o + e) % n + n) % n : e;
+                    const int cc = md.dbcell_off + (zz * n + yy) * n + xx;
+                    for (int k = start[cc]; k < start[cc + 1]; ++k) {
+                        const int j = list[k];
+                        if (j == i) continue;
+                        const double rr = sqrt(dist2_exact(x, S.Mp, md.L, i, j));
+                        if (!(rr < r_max)) continue;
+                        const int bin = (int)__ddiv_rn(rr, dr);
+                        if (bin < nbins) atomicAdd(&sh[bin], 1u);
+                    }
+                }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (sh[b]) atomicAdd(hist + b, (unsigned long long)sh[b]);
+}
+
+void gr_eval(kg_ctx *c, int melt, int R, double r_max, double dr, int nbins, unsigned long long *hist_dev)
+{
+    const MeltDev &md = c->sim.melt[melt];
+    ++c->launches;
+    cudaMemsetAsync(hist_dev, 0, sizeof(unsigned long long) * nbins, c->stream);
+    k_gr<<<nb256(md.M), 256, 0, c->stream>>>(c->d_sim, melt, c->x, c->dbcell, c->dbstart, c->dblist, R, r_max,
+                                             dr, nbins, hist_dev);
+}
+
 // <R^2(n)> without any allocation (kg_r2n_noalloc)
 // ---------------------------------------------------------------------------
 // The per-chain partial sums of k_r2n_chain live in this file-scope array

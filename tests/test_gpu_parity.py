@@ -13,6 +13,7 @@ import pytest
 
 import kg_inputs as KI
 import oracle as O
+from oracle import structure as SF
 
 pytestmark = pytest.mark.gpu
 
@@ -306,6 +307,28 @@ def test_msd_is_unchanged_by_db_sweeps(kg):
         after = kg.kg_msd(ctx, 0)
     assert acc > 0
     assert after == pytest.approx(before, rel=1e-12)
+
+
+def test_structure_factor_and_pair_distribution(kg):
+    """App. A observables of the 1000-monomer melt after 100 steps, against the
+    oracle's definitions on the same positions: S(q) for 300 reciprocal-lattice
+    vectors (binary32 phases: 1e-5 relative + 1e-4 absolute), g(r) counts exact."""
+    m = KI.make(1)
+    rng = np.random.default_rng(5)
+    hkl = rng.integers(-12, 13, (300, 3))
+    hkl[0] = (0, 0, 0)                                   # S(0) = M
+    with context(kg, [m], 1, schedule=[kg.stage(2.0, 10 ** 6, 0.002)]) as ctx:
+        kg.kg_step(ctx, 100)
+        S = kg.kg_structure_factor(ctx, 0, hkl)
+        g = kg.kg_pair_distribution(ctx, 0, 4.0, 80)
+        x = np.zeros_like(m.x)
+        kg.kg_get_config(ctx, 0, x)
+    assert S[0] == pytest.approx(m.M, rel=1e-6)
+    So = SF.structure_factor(x, m.box, hkl)
+    assert np.allclose(S, So, rtol=1e-5, atol=1e-4), np.abs(S - So).max()
+    go = SF.pair_distribution(x, m.box, 4.0, 80)
+    assert np.allclose(g, go, rtol=1e-12, atol=0)
+    assert g.max() > 1.5                                   # the first-neighbour peak
 
 
 def test_full_size_1600k(kg):
