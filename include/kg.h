@@ -317,6 +317,20 @@ const char *kg_strerror(kg_status s);
 kg_status kg_msd_reset(kg_ctx *c, int melt);
 kg_status kg_msd(kg_ctx *c, int melt, double *msd);
 
+/* The paper's initial state (Sec. II.B): freely rotating chains of
+ * chain_len monomers with bond length l0 and a fixed
+ * angle theta* between consecutive bonds, cos theta* = (r - 1) / (r + 1),
+ * r = l_K / l0 from Eq. 12 (Eq. 13 as printed is garbled; this inverts the
+ * FR relation l_K / l0 = (1 + c) / (1 - c)); first monomer uniform in the
+ * box, first bond uniform on the sphere, uniform azimuths.  A state whose
+ * Eq. 14 fit over N/4 <= n <= N/2 (kg_fit_lk) misses Eq. 12 by more than 2%
+ * is redrawn, up to max_attempts (KG_ERR_CAPACITY past that).  Random numbers:
+ * Philox4x32-10, key = seed, counter (monomer index in the chain, chain,
+ * attempt, 5), u = (w + 1/2) 2^-32.  x: host (3, n_chains chain_len)
+ * unwrapped, chain-major; *lk_fit and *attempts may be NULL.  Host only. */
+kg_status kg_generate_fr(int n_chains, int chain_len, double box, double kappa, double l0, unsigned long long seed,
+                         int max_attempts, double *x, double *lk_fit, int *attempts);
+
 /* Static structure factor of `melt` (App. A): S[a] = |sum_j exp(i q_a . r_j)|^2
  * / M for q_a = 2 pi (h, k, l)_a / L, hkl a host array of nq integer triples
  * (nq <= 65535), S host.  Phases reduced to whole turns in binary64 and

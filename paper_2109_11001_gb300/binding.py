@@ -28,7 +28,7 @@ EXPORTS = ["kg_create", "kg_load_config", "kg_get_config", "kg_set_potential_sch
            "kg_strerror", "kg_r2n_noalloc", "kg_mlp_set_weights", "kg_mlp_get_weights", "kg_mlp_forward",
            "kg_mlp_loss_grad", "kg_mlp_log", "kg_mlp_log_read", "kg_mlp_train", "kg_db_sweep_learned",
            "kg_db_sweep_learned_k", "kg_db_proposal", "kg_msd_reset", "kg_msd", "kg_fit_lk",
-           "kg_structure_factor", "kg_pair_distribution"]
+           "kg_structure_factor", "kg_pair_distribution", "kg_generate_fr"]
 
 KG_MLP_NPARAM = 5825
 KG_DB_CAND_MAX = 48
@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
         "kg_msd": (i, [p, i, C.POINTER(d)]),
         "kg_fit_lk": (i, [p, i, d, i, i, C.POINTER(d)]),
         "kg_structure_factor": (i, [p, i, p, i, p]),
+        "kg_generate_fr": (i, [i, i, d, d, d, C.c_ulonglong, i, p, C.POINTER(d), C.POINTER(i)]),
         "kg_pair_distribution": (i, [p, i, d, i, p]),
         "kg_mlp_set_weights": (i, [p, p]),
         "kg_mlp_get_weights": (i, [p, p]),
@@ -236,6 +237,16 @@ def kg_fit_lk(r2n, l0=0.960897, n_lo=0, n_hi=0):
     out = C.c_double()
     _check(load().kg_fit_lk(ptr(r), len(r), float(l0), int(n_lo), int(n_hi), C.byref(out)), "kg_fit_lk")
     return out.value
+
+
+def kg_generate_fr(n_chains, chain_len, box, kappa, seed, l0=0.960897, max_attempts=100):
+    """(x (3, M), fitted l_K, attempts) of the paper's FR-chain initial state."""
+    x = np.zeros((3, int(n_chains) * int(chain_len)))
+    lk = C.c_double()
+    att = C.c_int()
+    _check(load().kg_generate_fr(int(n_chains), int(chain_len), float(box), float(kappa), float(l0), int(seed),
+                                 int(max_attempts), ptr(x), C.byref(lk), C.byref(att)), "kg_generate_fr")
+    return x, lk.value, att.value
 
 
 def kg_structure_factor(ctx, melt, hkl):

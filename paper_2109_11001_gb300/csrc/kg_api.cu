@@ -910,6 +910,87 @@ kg_status kg_fit_lk(const double *r2n, int N, double l0, int n_lo, int n_hi, dou
     return KG_OK;
 }
 
+// Philox4x32-10 (Salmon et al., SC'11) on the host, for the initial-state generator
+static void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+        c[0] = n0; c[1] = (uint32_t)p1; c[2] = n2; c[3] = (uint32_t)p0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+kg_status kg_generate_fr(int n_chains, int chain_len, double box, double kappa, double l0, unsigned long long seed,
+                         int max_attempts, double *x, double *lk_fit, int *attempts)
+{
+    if (n_chains < 1 || chain_len < 8 || !(box > 0.0) || !(kappa >= 0.0) || !(l0 > 0.0) || max_attempts < 1 || !x)
+        return KG_ERR_INVALID_ARG;
+    const int N = chain_len;
+    const size_t M = (size_t)n_chains * N;
+    const double r = lk_over_l0(kappa), cos_t = (r - 1.0) / (r + 1.0), sin_t = std::sqrt(1.0 - cos_t * cos_t);
+    const double U32 = 2.3283064365386963e-10, TWO_PI = 6.283185307179586;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const int lo = std::max(N / 4, 1), hi = N / 2;
+    std::vector<double> r2n(N, 0.0);
+    for (int a = 0; a < max_attempts; ++a) {
+        for (int ch = 0; ch < n_chains; ++ch) {
+            double p[3] = {0.0, 0.0, 0.0}, b[3] = {0.0, 0.0, 1.0};
+            for (int i = 0; i < N; ++i) {
+                uint32_t w[4] = {(uint32_t)i, (uint32_t)ch, (uint32_t)a, 5u};
+                philox_host(w, k0, k1);
+                auto u = [&](int q) { return ((double)w[q] + 0.5) * U32; };
+                if (i == 0) {
+                    p[0] = box * u(0); p[1] = box * u(1); p[2] = box * u(2);
+                } else {
+                    double nb[3];
+                    if (i == 1) {                     // first bond uniform on the sphere
+                        const double ct = 2.0 * u(0) - 1.0, st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+                        const double ph = TWO_PI * u(1);
+                        nb[0] = st * std::cos(ph); nb[1] = st * std::sin(ph); nb[2] = ct;
+                    } else {                          // angle theta* to the previous bond, uniform azimuth
+                        const double ph = TWO_PI * u(0);
+                        const double ax = std::fabs(b[2]) < 0.9 ? 0.0 : 1.0, az = std::fabs(b[2]) < 0.9 ? 1.0 : 0.0;
+                        const double cx = b[1] * az - b[2] * 0.0, cy = b[2] * ax - b[0] * az, cz = b[0] * 0.0 - b[1] * ax;
+                        const double cn = std::sqrt((cx * cx + cy * cy) + cz * cz);
+                        const double e1[3] = {cx / cn, cy / cn, cz / cn};
+                        const double e2[3] = {b[1] * e1[2] - b[2] * e1[1], b[2] * e1[0] - b[0] * e1[2],
+                                              b[0] * e1[1] - b[1] * e1[0]};
+                        const double cp = std::cos(ph), sp = std::sin(ph);
+                        for (int k = 0; k < 3; ++k) nb[k] = cos_t * b[k] + sin_t * (cp * e1[k] + sp * e2[k]);
+                    }
+                    const double n = std::sqrt((nb[0] * nb[0] + nb[1] * nb[1]) + nb[2] * nb[2]);
+                    for (int k = 0; k < 3; ++k) {
+                        b[k] = nb[k] / n;
+                        p[k] = p[k] + l0 * b[k];
+                    }
+                }
+                for (int k = 0; k < 3; ++k) x[k * M + (size_t)ch * N + i] = p[k];
+            }
+        }
+        for (int n = lo; n <= hi; ++n) {              // <R^2(n)> over the fit range
+            double s = 0.0;
+            for (int ch = 0; ch < n_chains; ++ch)
+                for (int i = 0; i + n < N; ++i) {
+                    const size_t j = (size_t)ch * N + i;
+                    const double dx = x[j + n] - x[j], dy = x[M + j + n] - x[M + j], dz = x[2 * M + j + n] - x[2 * M + j];
+                    s += (dx * dx + dy * dy) + dz * dz;
+                }
+            r2n[n] = s / ((double)n_chains * (N - n));
+        }
+        double lk = 0.0;
+        const kg_status st = kg_fit_lk(r2n.data(), N, l0, lo, hi, &lk);
+        if (st != KG_OK) return st;
+        if (std::fabs(lk / (r * l0) - 1.0) <= 0.02) {
+            if (lk_fit) *lk_fit = lk;
+            if (attempts) *attempts = a + 1;
+            return KG_OK;
+        }
+    }
+    return KG_ERR_CAPACITY;
+}
+
 kg_status kg_structure_factor(kg_ctx *c, int melt, const int *hkl, int nq, double *S)
 {
     kg_status s = check_melt(c, melt);

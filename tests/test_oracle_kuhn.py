@@ -47,3 +47,32 @@ def test_library_fit_matches_the_oracle():
         assert kg.kg_fit_lk(r2n) == pytest.approx(kuhn.fit_lk(r2n), rel=1e-7)
         assert kg.kg_fit_lk(r2n, n_lo=5, n_hi=N - 1) == pytest.approx(kuhn.fit_lk(r2n, n_lo=5, n_hi=N - 1),
                                                                        rel=1e-7)
+
+
+def test_fr_generator_geometry_and_acceptance():
+    from oracle import frgen, schedule
+    kappa, N, nch = 2.0, 40, 30
+    r = schedule.lk_over_l0(kappa)
+    c = (r - 1) / (r + 1)
+    x, lk, att = frgen.generate(nch, N, 12.0, kappa, 99)
+    X = x.reshape(3, nch, N)
+    b = X[:, :, 1:] - X[:, :, :-1]
+    assert np.sqrt((b * b).sum(axis=0)) == pytest.approx(frgen.L0, rel=1e-12)   # every bond l0
+    bh = b / np.sqrt((b * b).sum(axis=0))
+    cos = (bh[:, :, 1:] * bh[:, :, :-1]).sum(axis=0)
+    assert cos == pytest.approx(c, abs=1e-12)                                     # fixed angle theta*
+    assert abs(lk / (r * frgen.L0) - 1) <= 0.02 and att >= 1
+    assert np.all((X[:, :, 0] >= 0) & (X[:, :, 0] < 12.0))                        # first monomers in the box
+    # theta* inverts the FR relation: (1 + c) / (1 - c) = l_K / l0 of Eq. 12
+    assert (1 + c) / (1 - c) == pytest.approx(r, rel=1e-14)
+
+
+@pytest.mark.parametrize("kappa,N,nch", [(0.0, 48, 40), (2.5, 80, 25)])
+def test_library_fr_generator_matches_the_oracle(kappa, N, nch):
+    kg = pytest.importorskip("paper_2109_11001_gb300")
+    from oracle import frgen
+    x, lk, att = kg.kg_generate_fr(nch, N, 15.0, kappa, 2109)
+    xo, lko, atto = frgen.generate(nch, N, 15.0, kappa, 2109)
+    assert att == atto
+    assert np.abs(x - xo).max() < 1e-9
+    assert lk == pytest.approx(lko, rel=1e-7)          # two minimisers on a flat minimum
