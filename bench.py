@@ -58,10 +58,10 @@ def bytes_per_monomer(precision, skin):
 
 # DRAM bytes per monomer of the mixed step kernel from an ncu capture, and the
 # hash of kg_md.cu they were taken on (reported as null once the source changes)
-# (ncu --set full of the 1.6M-monomer case, skin 0.5: 301.2 MB read + 79.7 MB
+# (ncu --set full of the 1.6M-monomer case, skin 0.5: 301.9 MB read + 91.2 MB
 # written per launch; profiles/md_step_and_nlist_1.6M_mixed.md)
-NCU_TRAFFIC = {"bytes_per_monomer": (301.175808e6 + 79.698688e6) / 1.6e6,
-               "kg_md_sha1": "b2ac71288081a01f38d280254db9411f7f287d8e"}
+NCU_TRAFFIC = {"bytes_per_monomer": (301.939968e6 + 91.210240e6) / 1.6e6,
+               "kg_md_sha1": "0f8edb8d39f38b544daa526bcd5cab7082af6bf1"}
 
 WORKLOADS = {
     "cfg5": dict(index=5, desc="1000 chains x N=1600 (1.6M monomers), kappa=3.5, rho=0.85"),
