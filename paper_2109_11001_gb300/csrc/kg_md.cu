@@ -540,8 +540,9 @@ __global__ void __launch_bounds__(1024) k_scan2(int *__restrict__ out, const int
     }
 }
 
-// slot list in cell order; with recb, the build records are copied into the
-// same order (recs) so that a cell's candidates are one contiguous run
+// slot list in cell order; with recb, the build offsets are copied into the
+// same order (recs, w = the compute index) so that a cell's candidates are one
+// contiguous run of single 16-byte loads
 __global__ void __launch_bounds__(256) k_scatter(const int *__restrict__ cellid, const int *__restrict__ rank,
                                                 const int *__restrict__ start, int *__restrict__ list, int M,
                                                 const unsigned *__restrict__ flags,
@@ -552,7 +553,10 @@ __global__ void __launch_bounds__(256) k_scatter(const int *__restrict__ cellid,
     if (s >= M) return;
     const int pos = start[cellid[s]] + rank[s];
     list[pos] = s;
-    if (recs) recs[pos] = recb[s];
+    if (recs) {
+        const float4 r = recb[s];
+        recs[pos] = make_float4(r.x, r.y, r.z, __int_as_float(s));
+    }
 }
 
 // within-cell order by slot (deterministic lists), then clear the counts
@@ -592,15 +596,15 @@ __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start,
 // A warp walks the 27 stencil cells in lockstep: for cell q every lane runs
 // the warp's largest count of that cell, lanes past their own count idle, and
 // the candidate test, exclusions and list append need no divergent control
-// flow except for the rare binary64 band check.  The candidate's record and
-// compute index are loaded together.
+// flow except for the rare binary64 band check.  The candidate's offsets and
+// compute index arrive in one 16-byte load.
 constexpr int NL_BLOCK = 128;
 
 // (128, 10): at most 48 registers; more resident warps hide the candidate
 // loads (tighter caps spill too much, looser ones leave the SM half idle)
 __global__ void __launch_bounds__(NL_BLOCK, 10) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
                                                    const float4 *__restrict__ recb, const float4 *__restrict__ recs,
-                                                   const int *__restrict__ start, const int *__restrict__ list,
+                                                   const int *__restrict__ start,
                                                    unsigned *__restrict__ nl, int *__restrict__ nn,
                                                    unsigned *__restrict__ flags, const int *__restrict__ slot_of,
                                                    const int4 *__restrict__ bpa)
@@ -642,12 +646,9 @@ __global__ void __launch_bounds__(NL_BLOCK, 10) k_nlist(const SimDev *__restrict
         const unsigned tag = (unsigned)q << IDX_BITS;
         for (int j = 0; j < nmax; ++j) {
             const bool valid = j < n;
-            float4 rj = make_float4(1e30f, 1e30f, 1e30f, 0.f);
-            int t = -1;
-            if (valid) {
-                rj = __ldg(recs + k0 + j);
-                t = __ldg(list + k0 + j);
-            }
+            float4 rj = make_float4(1e30f, 1e30f, 1e30f, __int_as_float(-1));
+            if (valid) rj = __ldg(recs + k0 + j);
+            const int t = __float_as_int(rj.w);
             const float ex = rj.x - ox, ey = rj.y - oy, ez = rj.z - oz;
             const float r2 = ex * ex + ey * ey + ez * ez;
             bool take = r2 < hi && t != s && t != bp.y && t != bp.z;
@@ -924,8 +925,8 @@ static void launch_rebuild(kg_ctx *c, cudaStream_t st)
                                                c->recs);
     k_cellsort<<<nblk(c->ncell_md, 256), 256, 0, st>>>(c->cstart, c->clist, c->recs, c->ccount, c->ncell_md,
                                                        c->flags);
-    k_nlist<<<nblk(c->M, NL_BLOCK), NL_BLOCK, 0, st>>>(c->d_sim, c->x, c->recb, c->recs, c->cstart, c->clist,
-                                                       c->nl, c->nn, c->flags, c->slot_of, c->bp);
+    k_nlist<<<nblk(c->M, NL_BLOCK), NL_BLOCK, 0, st>>>(c->d_sim, c->x, c->recb, c->recs, c->cstart, c->nl,
+                                                       c->nn, c->flags, c->slot_of, c->bp);
 }
 
 static void launch_step_kernel(kg_ctx *c, cudaStream_t st, int cur)
