@@ -601,7 +601,7 @@ def ncu_case(args):
     kg.kg_step(ctx, 3)          # builds the list; the 4th step first re-sorts into cell order
     kg.kg_set_counters(ctx, 3, 0)
     kg.kg_step(ctx, 4)
-    st = kg.kg_db_sweep(ctx, 1e-3)
+    st = kg.kg_db_sweep(ctx, args.ncu_db_budget)
     torch.cuda.synchronize()
     kg.kg_destroy(ctx)
     print(json.dumps({"ncu_case": args.workload, "M": m.M, "db_accepted": st.accepted}))
@@ -622,6 +622,7 @@ def main():
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the direct-launch window (same bench steps, no graphs) with cudaProfilerStart/Stop, for ncu --profile-from-start off")
     ap.add_argument("--ncu-case", action="store_true")
+    ap.add_argument("--ncu-db-budget", type=float, default=1e-3, help="DB attempts per monomer in the --ncu-case sweep")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args)

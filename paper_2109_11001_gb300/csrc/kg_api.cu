@@ -249,7 +249,7 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     SimDev &S = c->sim;
     S.n_melts = p->n_melts;
     const double rl = RC + c->p.skin;
-    long long M = 0, ncell = 0, ndbcell = 0;
+    long long M = 0, ncell = 0, ndbcell = 0, nchain = 0;
     for (int m = 0; m < p->n_melts; ++m) {
         const kg_melt &ml = c->melts[m];
         if (ml.n_chains < 1 || ml.chain_len < 3 || !(ml.box > 7.0) || ml.kappa < 0) return fail(KG_ERR_INVALID_ARG);
@@ -293,6 +293,8 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
         }
         md.cell_off = (int)ncell;
         md.dbcell_off = (int)ndbcell;
+        md.ch_off = (int)nchain;
+        nchain += ml.n_chains;
         ncell += 64LL * md.nbk * md.nbk * md.nbk;
         ndbcell += (long long)md.ndb * md.ndb * md.ndb;
         M += md.M;
@@ -354,12 +356,14 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->dblist = (int *)A(Mp * sizeof(int));
     c->dbrec = (float4 *)A(Mp * sizeof(float4));
     c->dbmark = (int *)A((size_t)c->ncell_db * sizeof(int));
+    c->n_chain_total = (int)nchain;
+    c->chain_ver = (int *)A((size_t)nchain * sizeof(int));
+    c->dbround = (int *)A(4 * kg::MAX_MELTS * sizeof(int));
     c->koff = (int *)A((kg::MAX_MELTS + 1) * sizeof(int));
     c->slot_of = (int *)A(Mp * sizeof(int));
     c->comp_of = (int *)A(Mp * sizeof(int));
     c->bp = (int4 *)A(Mp * sizeof(int4));
     c->img = (int *)A(3 * Mp * sizeof(int));
-    c->dirty = (int *)A(Mp * sizeof(int));
     c->db_stats = (long long *)A(4 * kg::MAX_MELTS * sizeof(long long));
     c->scratch = (double *)A(7 * Mp * sizeof(double));
     c->flags = (unsigned *)A(16 * sizeof(unsigned));
@@ -407,9 +411,9 @@ void kg_destroy(kg_ctx *c)
     void *bufs[] = {c->d_sim, c->d_stage, c->x, c->u, c->pid, c->recb, c->recs, c->shtab, c->dlt[0], c->dlt[1],
                     c->pg[0], c->pg[1], c->pos64[0],
                     c->pos64[1], c->xb, c->cellid, c->rank, c->ccount, c->cstart, c->clist, c->bsum, c->nl,
-                    c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->dbrec, c->dbmark, c->att,
+                    c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->dbrec, c->dbmark, c->chain_ver, c->dbround, c->att_ver, c->att,
                     c->koff, c->slot_of,
-                    c->comp_of, c->bp, c->img, c->dirty, c->db_stats, c->scratch, c->flags, c->fout, c->partials,
+                    c->comp_of, c->bp, c->img, c->db_stats, c->scratch, c->flags, c->fout, c->partials,
                     c->r2tmp, c->hist, c->mlp_master, c->mlp_adam, c->mlp_grad, c->mlp_blob, c->mlp_w2t,
                     c->logf, c->logt, c->logn, c->trainf, c->traint, c->d_train_head, c->tr_buf, c->bmax2,
                     c->d_io, c->msd_ref};
@@ -573,9 +577,18 @@ static kg_status sweep_impl(kg_ctx *c, const long long *attempts, kg_db_stats *s
     if (tot >= (1LL << 31)) return KG_ERR_INVALID_ARG;
     if (tot > c->att_cap) {
         dev_free(c, c->att);
+        dev_free(c, c->att_ver);
         c->att_cap = std::max(tot, 2 * c->att_cap);
         c->att = dev_alloc(c, (size_t)c->att_cap * sizeof(kg::Attempt));
-        if (!c->att) { c->att_cap = 0; return KG_ERR_OOM; }
+        c->att_ver = (int *)dev_alloc(c, (size_t)c->att_cap * sizeof(int));
+        if (!c->att || !c->att_ver) {
+            dev_free(c, c->att);
+            dev_free(c, c->att_ver);
+            c->att = nullptr;
+            c->att_ver = nullptr;
+            c->att_cap = 0;
+            return KG_ERR_OOM;
+        }
     }
     if (learned && !kg::mlp_ensure(c)) return KG_ERR_OOM;
     static thread_local long long *hstats = nullptr;

@@ -34,6 +34,8 @@
 //      monomer data moves (the maps are the topology).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kg_db.cuh"
 
 namespace kg {
@@ -125,18 +127,23 @@ __global__ void __launch_bounds__(32 * EVAL_WARPS_U) k_db_eval(const SimDev *__r
     }
 }
 
-// uniform proposal: any warp re-evaluates, junction cells within one cell
-struct UniformPolicy {
-    int paper;
-    WarpCand *wc;                                  // one per warp of the block
-    __device__ void init() {}
-    __device__ int radius(const MeltDev &) const { return 1; }
-    __device__ int batch() const { return 32; }
-    __device__ void reeval(const DBC &C, const ViewMap &V, const SimDev &S, long long sweep, int kk, int, int warp,
-                           Attempt &out, unsigned *flags)
+// uniform proposal: a stale record is re-evaluated by one warp; the
+// staleness radius is one cell
+struct UniformEval {
+    const SimDev *S;
+    const StageDev *st;
+    const double *x;
+    const int *pid, *cell, *start, *list;
+    const float4 *rec;
+    const int *comp_of, *slot_of;
+    long long sweep;
+    unsigned *flags;
+    WarpCand *wc;
+    __device__ void eval(int m, int k, int, Attempt &out)
     {
+        const DBC C = make_dbc(*S, *st, m, x, pid, cell, start, list, rec, st->T);
         unsigned err = 0;
-        const Attempt a = evaluate(C, V, wc[warp], S.seed, sweep, kk, paper, err);
+        const Attempt a = evaluate(C, ViewMap{comp_of, slot_of}, *wc, S->seed, sweep, k, S->paper_metropolis, err);
         if ((threadIdx.x & 31) == 0) {
             out = a;
             if (err) atomicOr(flags, err);
@@ -144,36 +151,47 @@ struct UniformPolicy {
     }
 };
 
-constexpr int COMMIT_THREADS_U = 512;
+struct UniformRadius {
+    __device__ void init() {}
+    __device__ int radius(const MeltDev &) const { return 1; }
+};
 
-__global__ void __launch_bounds__(COMMIT_THREADS_U) k_db_commit(const SimDev *__restrict__ Sp,
-                                                               const StageDev *__restrict__ stp,
-                                                               const double *__restrict__ x,
-                                                               const int *__restrict__ pid,
-                                                               const int *__restrict__ cell,
-                                                               const int *__restrict__ start,
-                                                               const int *__restrict__ list,
-                                                               const float4 *__restrict__ rec,
-                                                               const int *__restrict__ koff,
-                                                               const Attempt *__restrict__ att, int *__restrict__ occ,
-                                                               int *__restrict__ curmap, int *__restrict__ img,
-                                                               int *__restrict__ dirty, int *__restrict__ mark,
-                                                               int stamp, long long *__restrict__ stats,
-                                                               long long sweep, unsigned *flags, int maxN)
+constexpr int RESTALE_WARPS = 8;
+
+__global__ void __launch_bounds__(32 * RESTALE_WARPS) k_db_restale(
+    const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp, const double *__restrict__ x,
+    const int *__restrict__ pid, const int *__restrict__ cell, const int *__restrict__ start,
+    const int *__restrict__ list, const float4 *__restrict__ rec, const int *__restrict__ koff,
+    const int *__restrict__ comp_of, const int *__restrict__ slot_of, Attempt *__restrict__ att, int *__restrict__ ver,
+    const int *__restrict__ chain_ver, const int *__restrict__ cell_ver, int *__restrict__ round, long long sweep,
+    unsigned *flags)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    int *old_occ = reinterpret_cast<int *>(smem);            // 2N ints
-    WarpCand *wc = reinterpret_cast<WarpCand *>(smem + ((sizeof(int) * 2 * (size_t)maxN + 15) & ~(size_t)15));
-    UniformPolicy pol{Sp->paper_metropolis, wc};
-    db_commit_body(pol, *Sp, *stp, x, pid, cell, start, list, rec, koff, att, occ, curmap, img, dirty, mark, stamp,
-                   stats, sweep, flags, old_occ);
+    __shared__ WarpCand wcs[RESTALE_WARPS];
+    if (flags[0]) return;                          // a latched error stops the sweep
+    UniformEval ev{Sp, stp, x, pid, cell, start, list, rec, comp_of, slot_of, sweep, flags,
+                   wcs + (threadIdx.x >> 5)};
+    restale_body(ev, *Sp, koff, att, ver, chain_ver, cell, cell_ver, round);
+}
+
+constexpr int COMMIT_THREADS = 512;
+
+__global__ void __launch_bounds__(COMMIT_THREADS) k_db_commit_next(
+    const SimDev *__restrict__ Sp, const double *__restrict__ x, const int *__restrict__ cell,
+    const int *__restrict__ koff, const Attempt *__restrict__ att, int *__restrict__ occ, int *__restrict__ curmap,
+    int *__restrict__ img, int *__restrict__ chain_ver, int *__restrict__ cell_ver, int *__restrict__ round,
+    long long *__restrict__ stats, unsigned *flags)
+{
+    extern __shared__ int old_occ[];              // 2N ints
+    UniformRadius pol;
+    commit_next_body(pol, *Sp, x, cell, koff, att, occ, curmap, img, chain_ver, cell_ver, round, stats, flags,
+                     old_occ);
 }
 
 // end of a sweep: box shifts into the positions (x + L*img, as one rounding of
 // a product and one of a sum), counters cleared
 __global__ void __launch_bounds__(256) k_db_finish(const SimDev *__restrict__ Sp, double *__restrict__ x,
                                                   const int *__restrict__ slot_of, int *__restrict__ img,
-                                                  int *__restrict__ dirty, double *__restrict__ msd_ref)
+                                                  double *__restrict__ msd_ref)
 {
     const SimDev &S = *Sp;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -189,7 +207,6 @@ __global__ void __launch_bounds__(256) k_db_finish(const SimDev *__restrict__ Sp
         }
         img[d * Mp + j] = 0;
     }
-    dirty[j] = 0;
 }
 
 // kg_md.cu
@@ -231,18 +248,18 @@ void db_finish(kg_ctx *c, long long *host_stats)
     cudaStream_t st = c->stream;
     c->launches += 1;
     // box shifts into the positions; chain partners follow the new maps
-    k_db_finish<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->slot_of, c->img, c->dirty, c->msd_ref);
+    k_db_finish<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->slot_of, c->img, c->msd_ref);
     bonded_partners(c);
     cudaMemcpyAsync(host_stats, c->db_stats, sizeof(long long) * 4 * c->sim.n_melts, cudaMemcpyDeviceToHost, st);
 }
 
-int next_stamp(kg_ctx *c)
+void db_rounds_reset(kg_ctx *c, long long tot)
 {
-    if (++c->db_stamp >= 0x3fffffff) {          // stamps wrap: start the marks afresh
-        cudaMemsetAsync(c->dbmark, 0, sizeof(int) * c->ncell_db, c->stream);
-        c->db_stamp = 1;
-    }
-    return c->db_stamp;
+    cudaStream_t st = c->stream;
+    cudaMemsetAsync(c->chain_ver, 0xFF, sizeof(int) * (size_t)c->n_chain_total, st);    // -1: untouched
+    cudaMemsetAsync(c->dbmark, 0xFF, sizeof(int) * (size_t)c->ncell_db, st);
+    cudaMemsetAsync(c->dbround, 0, sizeof(int) * 4 * MAX_MELTS, st);
+    if (tot > 0) cudaMemsetAsync(c->att_ver, 0, sizeof(int) * (size_t)tot, st);
 }
 
 int db_max_chain_len(const kg_ctx *c)
@@ -265,16 +282,25 @@ void db_sweep(kg_ctx *c, const std::vector<long long> &K, long long *host_stats)
         k_db_eval<<<nblk(tot, EVAL_WARPS_U), 32 * EVAL_WARPS_U, 0, st>>>(
             c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart, c->dblist, c->dbrec, c->koff, c->comp_of,
             c->slot_of, att, c->sweep, c->flags);
-    // ordered commit, one block per melt
+    // ordered commit in rounds (kg_db.cuh)
+    db_rounds_reset(c, tot);
     const int maxN = db_max_chain_len(c);
-    const size_t sm = ((sizeof(int) * 2 * (size_t)maxN + 15) & ~(size_t)15) +
-                      sizeof(WarpCand) * (COMMIT_THREADS_U / 32);
-    cudaFuncSetAttribute(k_db_commit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_db_commit<<<nm, COMMIT_THREADS_U, sm, st>>>(c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart,
-                                                  c->dblist, c->dbrec, c->koff, att, c->comp_of, c->slot_of, c->img,
-                                                  c->dirty, c->dbmark, next_stamp(c), c->db_stats, c->sweep,
-                                                  c->flags, maxN);
-    c->launches += 2;
+    const size_t sm = sizeof(int) * 2 * (size_t)maxN;
+    cudaFuncSetAttribute(k_db_commit_next, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int rgrid = std::max(1, std::min(nblk(tot, 32 * RESTALE_WARPS), 152 * 8));
+    db_rounds(c, tot,
+              [&] {
+                  k_db_restale<<<rgrid, 32 * RESTALE_WARPS, 0, st>>>(
+                      c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart, c->dblist, c->dbrec, c->koff,
+                      c->comp_of, c->slot_of, att, c->att_ver, c->chain_ver, c->dbmark, c->dbround, c->sweep,
+                      c->flags);
+              },
+              [&] {
+                  k_db_commit_next<<<nm, COMMIT_THREADS, sm, st>>>(c->d_sim, c->x, c->dbcell, c->koff, att,
+                                                                   c->comp_of, c->slot_of, c->img, c->chain_ver,
+                                                                   c->dbmark, c->dbround, c->db_stats, c->flags);
+              });
+    c->launches += 1;
     db_finish(c, host_stats);
 }
 

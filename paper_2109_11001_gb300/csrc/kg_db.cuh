@@ -206,186 +206,213 @@ __device__ __forceinline__ DBC make_dbc(const SimDev &S, const StageDev &st, int
     return C;
 }
 
-// Ordered validation and commit, one block per melt (P: re-evaluation policy).
-// An attempt's speculative record is stale when an earlier accepted swap of
-// the sweep touched one of its two chains or put a junction monomer within
-// P::radius cells of one of the attempt's junction monomers (cells carry the
-// sweep's stamp in `mark`).  The walk finds the next attempts that are stale
-// or accepted with a block-wide scan, re-evaluates up to one stale attempt
-// per warp against the current topology, then takes them in order: the
-// re-evaluations before the first acceptance are final, the first accepted
-// swap is committed, and the scan resumes after it.  The result is that of
-// the strictly sequential loop over attempts.  P provides init (block-wide),
-// radius, batch (the most warps that may re-evaluate at once) and reeval (one
-// whole warp; lane 0 leaves the new record in `out`).
-template <class P>
-__device__ void db_commit_body(P &pol, const SimDev &S, const StageDev &stg, const double *__restrict__ x,
-                               const int *__restrict__ pid, const int *__restrict__ cell,
-                               const int *__restrict__ start, const int *__restrict__ list,
-                               const float4 *__restrict__ rec, const int *__restrict__ koff,
-                               const Attempt *__restrict__ att, int *__restrict__ occ, int *__restrict__ curmap,
-                               int *__restrict__ img, int *__restrict__ dirty, int *__restrict__ mark, int stamp,
-                               long long *__restrict__ stats, long long sweep, unsigned *flags, int *old_occ)
+// ---------------------------------------------------------------------------
+// Ordered commit in rounds.  Every attempt record carries the number of swaps
+// committed (in its melt) when it was evaluated, ver[k]; chains and cells of
+// the 1.3 sigma grid carry the number of the last commit that touched them
+// (chain_ver, cell_ver; -1 for none).  A record is stale when a commit at or
+// after its version touched one of its two chains, or stamped a cell within
+// P::radius cells of one of its junction monomers: only then can its
+// evaluation differ, since swaps preserve positions, the bonds inside moved
+// segments and the lengths of the pieces on either side of every bond.
+// One round: (A) every stale record at or after the melt's position is
+// re-evaluated against the current topology, across the whole GPU, one warp
+// per attempt; (B) one block per melt finds the first accepted attempt from
+// its position (every record there is now current), commits it (slot maps,
+// box shifts, chain and cell stamps) and moves the position past it, or, if
+// there is none, finishes the melt (statistics).  Rounds repeat until every
+// melt is finished: as many rounds as accepted swaps plus one, and the result
+// is that of the strictly sequential loop over attempts.
+// round[4 m + 0..3] = position, commits, finished, re-evaluations.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool stale_rec(const Attempt &a, int v, const int *__restrict__ chain_ver, int choff,
+                                          const int *__restrict__ cell, const int *__restrict__ cell_ver)
 {
-    constexpr int MAXB = 32;
-    __shared__ Attempt bres[MAXB];
-    __shared__ int bidx[MAXB], bstale[MAXB], wcnt[32];
-    __shared__ int nb_s, sh[6];
-    __shared__ unsigned long long n_acc, n_empty, n_re;
-    __shared__ long long empty_adj;
-    __shared__ int stop_s;
-    const int m = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nw = blockDim.x >> 5;
-    if (tid == 0) stop_s = flags[0] != 0;          // one reading for the whole block
-    __syncthreads();
-    if (stop_s) {                                  // a latched error stops the sweep
-        if (tid == 0) for (int k = 0; k < 4; ++k) stats[4 * m + k] = 0;
-        return;
+    if (chain_ver[choff + a.c] >= v) return true;
+    if ((a.flags & 1) && chain_ver[choff + a.d] >= v) return true;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (a.jp[q] >= 0 && cell_ver[cell[a.jp[q]]] >= v) return true;
+    return false;
+}
+
+// (A) E provides eval(m, k_in_melt, k_global, Attempt &out) for one whole warp
+// (lane 0 leaves the record in out).
+template <class E>
+__device__ void restale_body(E &ev, const SimDev &S, const int *__restrict__ koff, Attempt *__restrict__ att,
+                             int *__restrict__ ver, const int *__restrict__ chain_ver, const int *__restrict__ cell,
+                             const int *__restrict__ cell_ver, int *__restrict__ round)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarp = (int)((gridDim.x * blockDim.x) >> 5);
+    const int Ktot = koff[S.n_melts];
+    for (int base = gw * 32; base < Ktot; base += nwarp * 32) {
+        const int k = base + lane;
+        bool st = false;
+        int m = 0;
+        if (k < Ktot) {
+            while (k >= koff[m + 1]) ++m;
+            const int *R = round + 4 * m;
+            if (!R[2] && k - koff[m] >= R[0])
+                st = stale_rec(att[k], ver[k], chain_ver, S.melt[m].ch_off, cell, cell_ver);
+        }
+        unsigned bal = __ballot_sync(FULL_MASK, st);
+        while (bal) {
+            const int src = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const int kk = __shfl_sync(FULL_MASK, k, src), mm = __shfl_sync(FULL_MASK, m, src);
+            Attempt a;
+            ev.eval(mm, kk - koff[mm], kk, a);
+            if (lane == 0) {
+                att[kk] = a;
+                ver[kk] = round[4 * mm + 1];
+                atomicAdd(round + 4 * mm + 3, 1);
+            }
+            __syncwarp();
+        }
     }
+}
+
+// (B) one block per melt; P provides init (block-wide) and radius.
+template <class P>
+__device__ void commit_next_body(P &pol, const SimDev &S, const double *__restrict__ x, const int *__restrict__ cell,
+                                 const int *__restrict__ koff, const Attempt *__restrict__ att,
+                                 int *__restrict__ occ, int *__restrict__ curmap, int *__restrict__ img,
+                                 int *__restrict__ chain_ver, int *__restrict__ cell_ver, int *__restrict__ round,
+                                 long long *__restrict__ stats, unsigned *flags, int *old_occ)
+{
+    __shared__ int found_s, sh[6], done_s;
+    __shared__ unsigned long long n_empty;
+    const int m = blockIdx.x, tid = threadIdx.x;
+    int *R = round + 4 * m;
+    if (tid == 0) done_s = R[2] || flags[0] != 0;
+    __syncthreads();
+    if (done_s) return;
     const MeltDev &md = S.melt[m];
     const int N = md.N, off = md.off, Mp = S.Mp;
-    const DBC C = make_dbc(S, stg, m, x, pid, cell, start, list, rec, stg.T);
-    const ViewMap V{occ, curmap};
-    pol.init();
-    const int R = pol.radius(md);
-    const int B = min(min(nw, pol.batch()), MAXB);
-    if (tid == 0) { n_acc = n_empty = n_re = 0; empty_adj = 0; }
+    const int k0 = koff[m], K = koff[m + 1] - k0, pos = R[0];
+    // the first accepted attempt at or after pos
+    if (tid == 0) found_s = K;
     __syncthreads();
-    const int k0 = koff[m], K = koff[m + 1] - k0;
-    {   // empty proposals among the speculative records (corrected as re-evaluations are adopted)
+    for (int base = pos; base < K; base += blockDim.x) {
+        const int k = base + tid;
+        if (k < K && (att[k0 + k].flags & 2)) atomicMin(&found_s, k);
+        __syncthreads();
+        const bool stop = found_s < K;
+        __syncthreads();
+        if (stop) break;
+    }
+    const int found = found_s;
+    if (found == K) {                              // the melt is finished
+        if (tid == 0) n_empty = 0;
+        __syncthreads();
         unsigned long long e = 0;
         for (int k = tid; k < K; k += blockDim.x) e += !(att[k0 + k].flags & 1);
         atomicAdd(&n_empty, e);
+        __syncthreads();
+        if (tid == 0) {
+            stats[4 * m + 0] = K;
+            stats[4 * m + 1] = (long long)n_empty;
+            stats[4 * m + 2] = R[1];
+            stats[4 * m + 3] = R[3];
+            if (R[1]) atomicOr(flags + 1, 1u);
+            R[2] = 1;
+        }
+        return;
     }
-    int pos = 0;
-    while (pos < K) {
-        // 1. the next (up to B) stale or accepted attempts at or after pos, in order
-        if (tid == 0) nb_s = 0;
-        __syncthreads();
-        for (int base = pos;; base += blockDim.x) {
-            const int k = base + tid;
-            bool inter = false, stale = false;
-            if (k < K) {
-                const Attempt &a = att[k0 + k];
-                stale = dirty[off + a.c * N] || ((a.flags & 1) && dirty[off + a.d * N]);
+    pol.init();
+    const int Rr = pol.radius(md);
+    const Attempt a = att[k0 + found];
+    const int kind = a.kind, A = a.A, Bc = a.B, pA = a.pA, pB = a.pB, nc = R[1];
+    const int baseA = off + A * N, baseB = off + Bc * N;
+    for (int j = tid; j < N; j += blockDim.x) {
+        old_occ[j] = occ[baseA + j];
+        old_occ[N + j] = occ[baseB + j];
+    }
+    __syncthreads();
+    for (int j = tid; j < 2 * N; j += blockDim.x) {
+        const int s = j < N ? baseA + j : baseB + (j - N);
+        const int src = swap_slot(s, kind, A, Bc, pA, pB, N, off);
+        const int val = src - baseA < N && src >= baseA ? old_occ[src - baseA] : old_occ[N + src - baseB];
+        occ[s] = val;
+        curmap[val] = s;
+    }
+    __syncthreads();
+    if (tid < 2) {
+        // segment 0: A' slots pA+1..N-1 anchored at A' slot pA;
+        // segment 1: kind 0 -> B' slots pA+1..N-1 at pA; kind 1 -> B' slots 0..pB at pB+1
+        int f, an;
+        if (tid == 0) { f = occ[baseA + pA + 1]; an = occ[baseA + pA]; }
+        else if (kind == 0) { f = occ[baseB + pA + 1]; an = occ[baseB + pA]; }
+        else { f = occ[baseB + pB]; an = occ[baseB + pB + 1]; }
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (a.jp[q] >= 0 && mark[cell[a.jp[q]]] == stamp) stale = true;
-                inter = stale || (a.flags & 2);
-            }
-            const unsigned bal = __ballot_sync(FULL_MASK, inter);
-            if (lane == 0) wcnt[warp] = __popc(bal);
-            __syncthreads();
-            int before = nb_s;
-            for (int w = 0; w < warp; ++w) before += wcnt[w];
-            const int o = before + __popc(bal & ((1u << lane) - 1u));
-            if (inter && o < B) {
-                bidx[o] = k;
-                bstale[o] = stale;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                int tot = nb_s;
-                for (int w = 0; w < nw; ++w) tot += wcnt[w];
-                nb_s = min(tot, B);
-            }
-            __syncthreads();
-            if (nb_s >= B || base + (int)blockDim.x >= K) break;
+        for (int d = 0; d < 3; ++d)
+            sh[3 * tid + d] = -((int)rint(__ddiv_rn(__dsub_rn(x[d * Mp + f], x[d * Mp + an]), md.L))
+                                + img[d * Mp + f] - img[d * Mp + an]);
+    }
+    __syncthreads();
+    for (int j = tid; j < 2 * N; j += blockDim.x) {
+        int seg = -1, s;
+        if (j < N) {
+            s = baseA + j;
+            if (j > pA) seg = 0;
+        } else {
+            const int jj = j - N;
+            s = baseB + jj;
+            if ((kind == 0 && jj > pA) || (kind == 1 && jj <= pB)) seg = 1;
         }
-        const int nb = nb_s;
-        if (nb == 0) break;                        // everything after pos is final as evaluated
-        // 2. stale ones re-evaluated against the current topology, one warp each
-        if (warp < nb) {
-            const int k = bidx[warp];
-            if (bstale[warp]) pol.reeval(C, V, S, sweep, k, k0 + k, warp, bres[warp], flags);
-            else if (lane == 0) bres[warp] = att[k0 + k];
-        }
-        __syncthreads();
-        // 3. in order: adopt the re-evaluations up to the first acceptance and commit it
-        int next = bidx[nb - 1] + 1;
-        for (int i = 0; i < nb; ++i) {
-            const Attempt a = bres[i];
-            if (bstale[i] && tid == 0) {
-                ++n_re;
-                empty_adj += (long long)!(a.flags & 1) - (long long)!(att[k0 + bidx[i]].flags & 1);
-            }
-            if (!(a.flags & 2)) continue;
-            const int kind = a.kind, A = a.A, Bc = a.B, pA = a.pA, pB = a.pB;
-            const int baseA = off + A * N, baseB = off + Bc * N;
-            for (int j = tid; j < N; j += blockDim.x) {
-                old_occ[j] = occ[baseA + j];
-                old_occ[N + j] = occ[baseB + j];
-            }
-            __syncthreads();
-            for (int j = tid; j < 2 * N; j += blockDim.x) {
-                const int s = j < N ? baseA + j : baseB + (j - N);
-                const int src = swap_slot(s, kind, A, Bc, pA, pB, N, off);
-                const int val = src - baseA < N && src >= baseA ? old_occ[src - baseA] : old_occ[N + src - baseB];
-                occ[s] = val;
-                curmap[val] = s;
-            }
-            __syncthreads();
-            if (tid < 2) {
-                // segment 0: A' slots pA+1..N-1 anchored at A' slot pA;
-                // segment 1: kind 0 -> B' slots pA+1..N-1 at pA; kind 1 -> B' slots 0..pB at pB+1
-                int f, an;
-                if (tid == 0) { f = occ[baseA + pA + 1]; an = occ[baseA + pA]; }
-                else if (kind == 0) { f = occ[baseB + pA + 1]; an = occ[baseB + pA]; }
-                else { f = occ[baseB + pB]; an = occ[baseB + pB + 1]; }
+        if (seg >= 0) {
+            const int p = occ[s];
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    sh[3 * tid + d] = -((int)rint(__ddiv_rn(__dsub_rn(x[d * Mp + f], x[d * Mp + an]), md.L))
-                                        + img[d * Mp + f] - img[d * Mp + an]);
-            }
-            __syncthreads();
-            for (int j = tid; j < 2 * N; j += blockDim.x) {
-                int seg = -1, s;
-                if (j < N) {
-                    s = baseA + j;
-                    if (j > pA) seg = 0;
-                } else {
-                    const int jj = j - N;
-                    s = baseB + jj;
-                    if ((kind == 0 && jj > pA) || (kind == 1 && jj <= pB)) seg = 1;
-                }
-                if (seg >= 0) {
-                    const int p = occ[s];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) img[d * Mp + p] += sh[3 * seg + d];
-                }
-            }
-            // stamp the cells within R of the four junction monomers
-            const int n = md.ndb, W = 2 * R + 1;
-            for (int q = 0; q < 4; ++q) {
-                const int p = a.jp[q];
-                if (p < 0) continue;
-                const int c0 = cell[p] - md.dbcell_off;
-                const int cx = c0 % n, cy = (c0 / n) % n, cz = c0 / (n * n);
-                for (int t = tid; t < W * W * W; t += blockDim.x) {
-                    const int dx = t % W - R, dy = (t / W) % W - R, dz = t / (W * W) - R;
-                    const int xx = ((cx + dx) % n + n) % n, yy = ((cy + dy) % n + n) % n;
-                    const int zz = ((cz + dz) % n + n) % n;
-                    mark[md.dbcell_off + (zz * n + yy) * n + xx] = stamp;
-                }
-            }
-            if (tid == 0) {
-                dirty[baseA] = 1;
-                dirty[baseB] = 1;
-                ++n_acc;
-            }
-            next = bidx[i] + 1;
-            break;
+            for (int d = 0; d < 3; ++d) img[d * Mp + p] += sh[3 * seg + d];
         }
-        pos = next;
-        __syncthreads();
+    }
+    // stamp the two chains and the cells within Rr of the four junction monomers
+    const int n = md.ndb, W = 2 * Rr + 1;
+    for (int q = 0; q < 4; ++q) {
+        const int p = a.jp[q];
+        if (p < 0) continue;
+        const int c0 = cell[p] - md.dbcell_off;
+        const int cx = c0 % n, cy = (c0 / n) % n, cz = c0 / (n * n);
+        for (int t = tid; t < W * W * W; t += blockDim.x) {
+            const int dx = t % W - Rr, dy = (t / W) % W - Rr, dz = t / (W * W) - Rr;
+            const int xx = ((cx + dx) % n + n) % n, yy = ((cy + dy) % n + n) % n;
+            const int zz = ((cz + dz) % n + n) % n;
+            cell_ver[md.dbcell_off + (zz * n + yy) * n + xx] = nc;
+        }
     }
     __syncthreads();
     if (tid == 0) {
-        stats[4 * m + 0] = K;
-        stats[4 * m + 1] = (long long)n_empty + empty_adj;
-        stats[4 * m + 2] = (long long)n_acc;
-        stats[4 * m + 3] = (long long)n_re;
-        if (n_acc) atomicOr(flags + 1, 1u);
+        chain_ver[md.ch_off + A] = nc;
+        chain_ver[md.ch_off + Bc] = nc;
+        R[1] = nc + 1;
+        R[0] = found + 1;
+    }
+}
+
+// Commit rounds until every melt is finished (host).  restale() and
+// commit_next() enqueue one pass each; the host reads the per-melt finished
+// flags after rounds 1, 2, 4, 8 and then every 8 (the passes of a finished melt
+// return at once), and stops on a latched device error.
+template <class FA, class FB>
+void db_rounds(kg_ctx *c, long long tot, FA restale, FB commit_next)
+{
+    static thread_local int *hround = nullptr;
+    if (!hround && cudaMallocHost(&hround, sizeof(int) * (4 * MAX_MELTS + 1)) != cudaSuccess) return;
+    const int nm = c->sim.n_melts;
+    long long r = 0, next_check = 1;
+    while (r <= tot) {                              // at most one round per accepted swap, plus one
+        restale();
+        commit_next();
+        c->launches += 2;
+        if (++r < next_check) continue;
+        cudaMemcpyAsync(hround, c->dbround, sizeof(int) * 4 * nm, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(hround + 4 * MAX_MELTS, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return;
+        bool all = true;
+        for (int m = 0; m < nm; ++m) all = all && hround[4 * m + 2] != 0;
+        if (all || hround[4 * MAX_MELTS] != 0) return;
+        next_check = r < 8 ? 2 * r : r + 8;
     }
 }
 

@@ -72,12 +72,15 @@ struct kg_ctx {
     int ncell_db = 0;
     int *dbcell = nullptr, *dbrank = nullptr, *dbcount = nullptr, *dbstart = nullptr, *dblist = nullptr;
     float4 *dbrec = nullptr;     // binary32 records on the DB grid (swap-bond prefilter)
-    int *dbmark = nullptr;       // per DB cell: stamp of the last sweep that changed bonds near it
-    int db_stamp = 0;
+    int *dbmark = nullptr;       // per DB cell: number of the last commit of the sweep near it (-1: none)
+    int *chain_ver = nullptr;    // per chain: number of the last commit of the sweep that touched it
+    int n_chain_total = 0;
+    int *dbround = nullptr;      // per melt: position, commits, finished, re-evaluations
+    int *att_ver = nullptr;      // per attempt: commits seen by its record
     void *att = nullptr;         // kg::Attempt[att_cap]
     long long att_cap = 0;
     int *koff = nullptr;         // [n_melts+1] attempt offsets
-    int *img = nullptr, *dirty = nullptr;
+    int *img = nullptr;
     long long *db_stats = nullptr;   // [n_melts][4]
 
     // learned proposal (kg_mlp.cu, kg_learned.cu)
@@ -156,7 +159,9 @@ void db_sweep(kg_ctx *c, const std::vector<long long> &K, long long *host_stats 
 void db_bin(kg_ctx *c, const std::vector<long long> &K);     // attempt offsets + the >= 1.3 sigma grid
 void db_finish(kg_ctx *c, long long *host_stats);             // box shifts, chain partners, stats to host
 int db_max_chain_len(const kg_ctx *c);
-int next_stamp(kg_ctx *c);                                    // stamp of a new sweep's cell marks
+// reset the commit bookkeeping of a sweep (versions, stamps, rounds)
+void db_rounds_reset(kg_ctx *c, long long tot);
+
 
 // kg_learned.cu
 void db_sweep_learned(kg_ctx *c, const std::vector<long long> &K, double lambda, long long *host_stats);

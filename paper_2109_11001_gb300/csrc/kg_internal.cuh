@@ -41,6 +41,7 @@ enum : unsigned {
 
 struct MeltDev {
     int off, M, N, n_ch;          // slots [off, off+M): chain c, position i -> off + c*N + i
+    int ch_off;                   // chains of earlier melts (global chain index = ch_off + c)
     double L, invL, kappa;
     float Lf, invLf, kappaf;
     // Verlet-list cell grid (cells >= r_c + skin), numbered brick-major

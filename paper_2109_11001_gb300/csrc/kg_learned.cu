@@ -34,6 +34,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kg_db.cuh"
 #include "kg_mlp.cuh"
 
@@ -311,34 +313,24 @@ __global__ void __launch_bounds__(32 * EVAL_WARPS) k_dbl_eval(const SimDev *__re
     }
 }
 
-// learned proposal: up to LEARN_BATCH warps re-evaluate at once; the reach of
-// an evaluation sets the radius
-constexpr int LEARN_BATCH = 4;
-
-struct LearnedPolicy {
+// learned proposal: a stale record is re-evaluated by one warp with the
+// network in shared memory; the reach of an evaluation sets the radius
+struct LearnedEval {
+    const SimDev *S;
+    const StageDev *st;
+    const double *x;
+    const int *pid, *cell, *start, *list;
+    const int *comp_of, *slot_of;
+    long long sweep;
+    unsigned *flags;
     LearnedArgs la;
-    MlpSmem *W;
-    WarpProp *wp;                                  // LEARN_BATCH of them
-    double lim;                                    // swap bond limit (1.3)
-    __device__ void init()
+    const MlpSmem *W;
+    WarpProp *wp;
+    __device__ void eval(int m, int k, int g, Attempt &out)
     {
-        mlp_load(*W, la.w);
-        __syncthreads();
-    }
-    // cells within 2 lim + 3 max(b_max, lim) of a junction monomer, one extra
-    // cell against rounding at cell faces
-    __device__ int radius(const MeltDev &md) const
-    {
-        const double bmax = sqrt(__longlong_as_double((long long)*la.bmax2));
-        const double reach = 2.0 * lim + 3.0 * fmax(bmax, lim);
-        return (int)ceil(reach * md.invhdb) + 1;
-    }
-    __device__ int batch() const { return LEARN_BATCH; }
-    __device__ void reeval(const DBC &C, const ViewMap &V, const SimDev &S, long long sweep, int kk, int g, int warp,
-                           Attempt &out, unsigned *flags)
-    {
+        const DBC C = make_dbc(*S, *st, m, x, pid, cell, start, list, la.rec, st->T);
         unsigned err = 0;
-        const Attempt a = learned_eval(C, V, *W, wp[warp], la, S.seed, sweep, kk, g, err);
+        const Attempt a = learned_eval(C, ViewMap{comp_of, slot_of}, *W, *wp, la, S->seed, sweep, k, g, err);
         if ((threadIdx.x & 31) == 0) {
             out = a;
             if (err) atomicOr(flags, err);
@@ -346,25 +338,53 @@ struct LearnedPolicy {
     }
 };
 
+struct LearnedRadius {
+    const unsigned long long *bmax2;
+    double lim;                                    // swap bond limit (1.3)
+    __device__ void init() {}
+    // cells within 2 lim + 3 max(b_max, lim) of a junction monomer, one extra
+    // cell against rounding at cell faces
+    __device__ int radius(const MeltDev &md) const
+    {
+        const double bmax = sqrt(__longlong_as_double((long long)*bmax2));
+        const double reach = 2.0 * lim + 3.0 * fmax(bmax, lim);
+        return (int)ceil(reach * md.invhdb) + 1;
+    }
+};
+
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-__global__ void __launch_bounds__(256) k_dbl_commit(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
-                                                   const double *__restrict__ x, const int *__restrict__ pid,
-                                                   const int *__restrict__ cell, const int *__restrict__ start,
-                                                   const int *__restrict__ list, const int *__restrict__ koff,
-                                                   const Attempt *__restrict__ att, int *__restrict__ occ,
-                                                   int *__restrict__ curmap, int *__restrict__ img,
-                                                   int *__restrict__ dirty, int *__restrict__ mark, int stamp,
-                                                   long long *__restrict__ stats, long long sweep, unsigned *flags,
-                                                   LearnedArgs la, int maxN)
+__host__ __device__ constexpr size_t restale_smem() { return sizeof(MlpSmem) + EVAL_WARPS * sizeof(WarpProp); }
+
+__global__ void __launch_bounds__(32 * EVAL_WARPS) k_dbl_restale(
+    const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp, const double *__restrict__ x,
+    const int *__restrict__ pid, const int *__restrict__ cell, const int *__restrict__ start,
+    const int *__restrict__ list, const int *__restrict__ koff, const int *__restrict__ comp_of,
+    const int *__restrict__ slot_of, Attempt *__restrict__ att, int *__restrict__ ver,
+    const int *__restrict__ chain_ver, const int *__restrict__ cell_ver, int *__restrict__ round, long long sweep,
+    unsigned *flags, LearnedArgs la)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    int *old_occ = reinterpret_cast<int *>(smem);
-    const size_t o1 = align16(sizeof(int) * 2 * (size_t)maxN);
-    LearnedPolicy pol{la, reinterpret_cast<MlpSmem *>(smem + o1),
-                      reinterpret_cast<WarpProp *>(smem + o1 + sizeof(MlpSmem)), sqrt(Sp->db_lim2)};
-    db_commit_body(pol, *Sp, *stp, x, pid, cell, start, list, la.rec, koff, att, occ, curmap, img, dirty, mark,
-                   stamp, stats, sweep, flags, old_occ);
+    MlpSmem &W = *reinterpret_cast<MlpSmem *>(smem);
+    WarpProp *wps = reinterpret_cast<WarpProp *>(smem + sizeof(MlpSmem));
+    mlp_load(W, la.w);
+    __syncthreads();
+    if (flags[0]) return;                          // a latched error stops the sweep (no block barrier follows)
+    LearnedEval ev{Sp, stp, x, pid, cell, start, list, comp_of, slot_of, sweep, flags, la, &W,
+                   wps + (threadIdx.x >> 5)};
+    restale_body(ev, *Sp, koff, att, ver, chain_ver, cell, cell_ver, round);
+}
+
+__global__ void __launch_bounds__(256) k_dbl_commit_next(
+    const SimDev *__restrict__ Sp, const double *__restrict__ x, const int *__restrict__ cell,
+    const int *__restrict__ koff, const Attempt *__restrict__ att, int *__restrict__ occ, int *__restrict__ curmap,
+    int *__restrict__ img, int *__restrict__ chain_ver, int *__restrict__ cell_ver, int *__restrict__ round,
+    long long *__restrict__ stats, unsigned *flags, const unsigned long long *bmax2)
+{
+    extern __shared__ int old_occ[];              // 2N ints
+    LearnedRadius pol{bmax2, sqrt(Sp->db_lim2)};
+    commit_next_body(pol, *Sp, x, cell, koff, att, occ, curmap, img, chain_ver, cell_ver, round, stats, flags,
+                     old_occ);
 }
 
 // longest bond of all melts, squared, as ordered binary64 bits
@@ -512,13 +532,25 @@ void db_sweep_learned(kg_ctx *c, const std::vector<long long> &K, double lambda,
             c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart, c->dblist, c->koff, c->comp_of, c->slot_of,
             att, c->sweep, c->flags, la);
     }
+    // ordered commit in rounds (kg_db.cuh)
+    db_rounds_reset(c, tot);
     const int maxN = db_max_chain_len(c);
-    const size_t sm = align16(sizeof(int) * 2 * (size_t)maxN) + sizeof(MlpSmem) + LEARN_BATCH * sizeof(WarpProp);
-    cudaFuncSetAttribute(k_dbl_commit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_dbl_commit<<<nm, 256, sm, st>>>(c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart, c->dblist, c->koff,
-                                      att, c->comp_of, c->slot_of, c->img, c->dirty, c->dbmark, next_stamp(c),
-                                      c->db_stats, c->sweep, c->flags, la, maxN);
-    c->launches += 3;
+    const size_t sm = sizeof(int) * 2 * (size_t)maxN;
+    cudaFuncSetAttribute(k_dbl_commit_next, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_dbl_restale, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)restale_smem());
+    const int rgrid = std::max(1, std::min(nblk(tot, 32 * EVAL_WARPS), 152 * 4));
+    db_rounds(c, tot,
+              [&] {
+                  k_dbl_restale<<<rgrid, 32 * EVAL_WARPS, restale_smem(), st>>>(
+                      c->d_sim, c->d_stage, c->x, c->pid, c->dbcell, c->dbstart, c->dblist, c->koff, c->comp_of,
+                      c->slot_of, att, c->att_ver, c->chain_ver, c->dbmark, c->dbround, c->sweep, c->flags, la);
+              },
+              [&] {
+                  k_dbl_commit_next<<<nm, 256, sm, st>>>(c->d_sim, c->x, c->dbcell, c->koff, att, c->comp_of,
+                                                         c->slot_of, c->img, c->chain_ver, c->dbmark, c->dbround,
+                                                         c->db_stats, c->flags, c->bmax2);
+              });
+    c->launches += 2;
     if (log && tot > 0) {
         k_log_append<<<1, 1024, 0, st>>>(c->logn, (int)tot, c->logf, c->logt, c->trainf, c->traint, c->train_cap,
                                          c->d_train_head, c->flags);
