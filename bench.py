@@ -365,10 +365,10 @@ def run_ours(args, world, rank, local):
         db_re += st.reevaluated
     d1.record(stream)
     torch.cuda.synchronize()
-    t_db = allmax(world, d0.elapsed_time(d1) / 1e3)
+    t_sweeps = allmax(world, d0.elapsed_time(d1) / 1e3)
     db_acc_all = allsum(world, float(db_acc))
     db_att_all = allsum(world, float(db_att))
-    log(f"db budget: {DB_SWEEPS} sweeps, {db_att} attempts, {db_acc} accepted, {db_re} re-evaluated, {t_db * 1e3:.1f} ms")
+    log(f"db budget: {DB_SWEEPS} sweeps, {db_att} attempts, {db_acc} accepted, {db_re} re-evaluated, {t_sweeps * 1e3:.1f} ms")
 
     # secondary: the same step in plain binary64 on this GPU (single rank), and
     # the learned double-bridging proposal against the uniform one
@@ -405,11 +405,11 @@ def run_ours(args, world, rank, local):
                    "precision": args.precision, "replicas": world, "autotuned": tuning,
                    "skin": tuning["skin"] if tuning else args.skin,
                    "l2": "inputs larger than L2 (working set > 129 MB), no flush"},
-        "accepted_db_moves_per_s": db_acc_all / t_db,
+        "accepted_db_moves_per_s": db_acc_all / t_sweeps,
         "db": {"attempts_per_sweep": int(round(DB_BUDGET * m.M)), "sweeps": DB_SWEEPS * world,
                "attempted": int(db_att_all), "accepted": int(db_acc_all), "reevaluated": int(db_re),
-               "accepted_per_s": db_acc_all / t_db, "attempts_per_s": db_att_all / t_db,
-               "ms_per_sweep": t_db * 1e3 / DB_SWEEPS, "proposal": "uniform",
+               "accepted_per_s": db_acc_all / t_sweeps, "attempts_per_s": db_att_all / t_sweeps,
+               "ms_per_sweep": t_sweeps * 1e3 / DB_SWEEPS, "proposal": "uniform",
                "timing": "CUDA events around back-to-back sweeps, stats read after each"},
         "accepted_db_moves_per_s_in_step": acc_all / t_max,
         "db_attempts_per_step": att / args.steps,
