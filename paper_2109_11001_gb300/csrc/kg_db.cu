@@ -19,17 +19,16 @@
 //      topology, one warp each (the 27 cells of a partner scan on its lanes).
 //      A "monomer" here is its compute index; the topology is the pair of
 //      maps slot -> monomer (comp_of) and monomer -> slot (slot_of);
-//   3. k_db_commit: one block per melt takes the attempts in order.  An
-//      attempt is re-evaluated against the current topology when an earlier
-//      accepted swap in the sweep touched one of its two chains, or put a
-//      junction monomer (whose bonds changed) within one cell of a monomer
-//      whose neighbourhood it scanned.  Nothing else an evaluation reads can
-//      change: swaps preserve positions, the bonds inside moved segments, and
-//      the lengths of the two pieces on either side of every bond.  The block
-//      skips runs of unaffected rejected attempts with a block-wide scan and
-//      re-evaluates up to one affected attempt per warp at a time (the shared
-//      walk in kg_db.cuh).  Accepted swaps rewrite the two maps for the slots
-//      of their two chains and add box shifts to a per-monomer counter;
+//   3. commit rounds (kg_db.cuh): an attempt's record is stale when an
+//      earlier accepted swap in the sweep touched one of its two chains, or
+//      put a junction monomer (whose bonds changed) within one cell of a
+//      monomer whose neighbourhood it scanned.  Nothing else an evaluation
+//      reads can change: swaps preserve positions, the bonds inside moved
+//      segments, and the lengths of the two pieces on either side of every
+//      bond.  Each round, k_db_restale re-evaluates the stale records across
+//      the GPU, then k_db_commit_next (one block per melt) commits the first
+//      accepted attempt: the two maps are rewritten for the slots of its two
+//      chains and box shifts are added to a per-monomer counter;
 //   4. k_db_finish: the box shifts are added to the positions in place; no
 //      monomer data moves (the maps are the topology).
 #include <cuda_runtime.h>
