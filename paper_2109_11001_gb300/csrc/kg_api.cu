@@ -358,7 +358,7 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->dbmark = (int *)A((size_t)c->ncell_db * sizeof(int));
     c->n_chain_total = (int)nchain;
     c->chain_ver = (int *)A((size_t)nchain * sizeof(int));
-    c->dbround = (int *)A(4 * kg::MAX_MELTS * sizeof(int));
+    c->dbround = (int *)A(kg::RS * kg::MAX_MELTS * sizeof(int));
     c->koff = (int *)A((kg::MAX_MELTS + 1) * sizeof(int));
     c->slot_of = (int *)A(Mp * sizeof(int));
     c->comp_of = (int *)A(Mp * sizeof(int));

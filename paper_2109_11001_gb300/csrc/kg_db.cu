@@ -259,7 +259,9 @@ void db_rounds_reset(kg_ctx *c, long long tot)
     cudaStream_t st = c->stream;
     cudaMemsetAsync(c->chain_ver, 0xFF, sizeof(int) * (size_t)c->n_chain_total, st);    // -1: untouched
     cudaMemsetAsync(c->dbmark, 0xFF, sizeof(int) * (size_t)c->ncell_db, st);
-    cudaMemsetAsync(c->dbround, 0, sizeof(int) * 4 * MAX_MELTS, st);
+    std::vector<int> r0((size_t)RS * MAX_MELTS, 0);
+    for (int m = 0; m < MAX_MELTS; ++m) r0[(size_t)RS * m + 4] = INT_MAX;   // no accepted attempt known
+    cudaMemcpyAsync(c->dbround, r0.data(), sizeof(int) * r0.size(), cudaMemcpyHostToDevice, st);
     if (tot > 0) cudaMemsetAsync(c->att_ver, 0, sizeof(int) * (size_t)tot, st);
 }
 

@@ -4,6 +4,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include "kg_host.h"
 
 namespace kg {
@@ -223,7 +225,9 @@ __device__ __forceinline__ DBC make_dbc(const SimDev &S, const StageDev &st, int
 // there is none, finishes the melt (statistics).  Rounds repeat until every
 // melt is finished: as many rounds as accepted swaps plus one, and the result
 // is that of the strictly sequential loop over attempts.
-// round[4 m + 0..3] = position, commits, finished, re-evaluations.
+// round[RS m + 0..4] = position, commits, finished, re-evaluations, and the
+// first accepted attempt at or after the position (INT_MAX: none), which pass
+// (A) records while it reads every current record, so (B) needs no search.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool stale_rec(const Attempt &a, int v, const int *__restrict__ chain_ver, int choff,
                                           const int *__restrict__ cell, const int *__restrict__ cell_ver)
@@ -248,13 +252,24 @@ __device__ void restale_body(E &ev, const SimDev &S, const int *__restrict__ kof
     const int Ktot = koff[S.n_melts];
     for (int base = gw * 32; base < Ktot; base += nwarp * 32) {
         const int k = base + lane;
-        bool st = false;
+        bool st = false, live = false;
         int m = 0;
         if (k < Ktot) {
             while (k >= koff[m + 1]) ++m;
-            const int *R = round + 4 * m;
-            if (!R[2] && k - koff[m] >= R[0])
+            const int *R = round + RS * m;
+            if (!R[2] && k - koff[m] >= R[0]) {
                 st = stale_rec(att[k], ver[k], chain_ver, S.melt[m].ch_off, cell, cell_ver);
+                live = true;
+            }
+        }
+        // fresh records are current: note the first accepted one of each melt
+        const int m0 = __shfl_sync(FULL_MASK, m, 0);
+        const bool acc = live && !st && (att[k].flags & 2);
+        if (__all_sync(FULL_MASK, !live || m == m0)) {  // one melt in the warp: one atomic
+            const int first = __reduce_min_sync(FULL_MASK, acc ? k - koff[m] : INT_MAX);
+            if (lane == 0 && first != INT_MAX) atomicMin(round + RS * m0 + 4, first);
+        } else if (acc) {
+            atomicMin(round + RS * m + 4, k - koff[m]);
         }
         unsigned bal = __ballot_sync(FULL_MASK, st);
         while (bal) {
@@ -265,8 +280,9 @@ __device__ void restale_body(E &ev, const SimDev &S, const int *__restrict__ kof
             ev.eval(mm, kk - koff[mm], kk, a);
             if (lane == 0) {
                 att[kk] = a;
-                ver[kk] = round[4 * mm + 1];
-                atomicAdd(round + 4 * mm + 3, 1);
+                ver[kk] = round[RS * mm + 1];
+                atomicAdd(round + RS * mm + 3, 1);
+                if (a.flags & 2) atomicMin(round + RS * mm + 4, kk - koff[mm]);
             }
             __syncwarp();
         }
@@ -284,24 +300,16 @@ __device__ void commit_next_body(P &pol, const SimDev &S, const double *__restri
     __shared__ int found_s, sh[6], done_s;
     __shared__ unsigned long long n_empty;
     const int m = blockIdx.x, tid = threadIdx.x;
-    int *R = round + 4 * m;
+    int *R = round + RS * m;
     if (tid == 0) done_s = R[2] || flags[0] != 0;
     __syncthreads();
     if (done_s) return;
     const MeltDev &md = S.melt[m];
     const int N = md.N, off = md.off, Mp = S.Mp;
-    const int k0 = koff[m], K = koff[m + 1] - k0, pos = R[0];
-    // the first accepted attempt at or after pos
-    if (tid == 0) found_s = K;
+    const int k0 = koff[m], K = koff[m + 1] - k0;
+    // the first accepted attempt at or after the position, as pass (A) found it
+    if (tid == 0) found_s = R[4] < K ? R[4] : K;
     __syncthreads();
-    for (int base = pos; base < K; base += blockDim.x) {
-        const int k = base + tid;
-        if (k < K && (att[k0 + k].flags & 2)) atomicMin(&found_s, k);
-        __syncthreads();
-        const bool stop = found_s < K;
-        __syncthreads();
-        if (stop) break;
-    }
     const int found = found_s;
     if (found == K) {                              // the melt is finished
         if (tid == 0) n_empty = 0;
@@ -387,6 +395,7 @@ __device__ void commit_next_body(P &pol, const SimDev &S, const double *__restri
         chain_ver[md.ch_off + Bc] = nc;
         R[1] = nc + 1;
         R[0] = found + 1;
+        R[4] = INT_MAX;                            // to be found again by the next pass (A)
     }
 }
 
@@ -398,7 +407,7 @@ template <class FA, class FB>
 void db_rounds(kg_ctx *c, long long tot, FA restale, FB commit_next)
 {
     static thread_local int *hround = nullptr;
-    if (!hround && cudaMallocHost(&hround, sizeof(int) * (4 * MAX_MELTS + 1)) != cudaSuccess) return;
+    if (!hround && cudaMallocHost(&hround, sizeof(int) * (RS * MAX_MELTS + 1)) != cudaSuccess) return;
     const int nm = c->sim.n_melts;
     long long r = 0, next_check = 1;
     while (r <= tot) {                              // at most one round per accepted swap, plus one
@@ -406,12 +415,12 @@ void db_rounds(kg_ctx *c, long long tot, FA restale, FB commit_next)
         commit_next();
         c->launches += 2;
         if (++r < next_check) continue;
-        cudaMemcpyAsync(hround, c->dbround, sizeof(int) * 4 * nm, cudaMemcpyDeviceToHost, c->stream);
-        cudaMemcpyAsync(hround + 4 * MAX_MELTS, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(hround, c->dbround, sizeof(int) * RS * nm, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(hround + RS * MAX_MELTS, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return;
         bool all = true;
-        for (int m = 0; m < nm; ++m) all = all && hround[4 * m + 2] != 0;
-        if (all || hround[4 * MAX_MELTS] != 0) return;
+        for (int m = 0; m < nm; ++m) all = all && hround[RS * m + 2] != 0;
+        if (all || hround[RS * MAX_MELTS] != 0) return;
         next_check = r < 8 ? 2 * r : r + 8;
     }
 }

@@ -132,6 +132,7 @@ void *dev_alloc(kg_ctx *c, size_t bytes);
 void dev_free(kg_ctx *c, void *p);
 
 constexpr int GRAPH_STEPS = 10;          // MD steps per captured graph (even)
+constexpr int RS = 8;                    // ints per melt in the DB commit-round array
 
 struct Attempt {
     int flags;                   // 1: non-empty partner set, 2: accepted
