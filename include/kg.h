@@ -124,7 +124,7 @@ typedef struct {
     long long attempted;    /* attempts drawn                                          */
     long long empty;        /* attempts whose drawn bond had no admissible partner     */
     long long accepted;     /* swaps applied                                           */
-    long long reevaluated;  /* attempts re-evaluated after an earlier swap in the sweep */
+    long long reevaluated;  /* re-evaluations of attempts made stale by earlier swaps   */
     long long sweep;        /* index of the sweep just run                             */
 } kg_db_stats;
 
