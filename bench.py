@@ -58,10 +58,10 @@ def bytes_per_monomer(precision, skin):
 
 # DRAM bytes per monomer of the mixed step kernel from an ncu capture, and the
 # hash of kg_md.cu they were taken on (reported as null once the source changes)
-# (ncu --set full of the 1.6M-monomer case, skin 0.5: 301.9 MB read + 91.2 MB
+# (ncu --set full of the 1.6M-monomer case, skin 0.5: 302.0 MB read + 91.0 MB
 # written per launch; profiles/md_step_and_nlist_1.6M_mixed.md)
-NCU_TRAFFIC = {"bytes_per_monomer": (301.939968e6 + 91.210240e6) / 1.6e6,
-               "kg_md_sha1": "0f8edb8d39f38b544daa526bcd5cab7082af6bf1"}
+NCU_TRAFFIC = {"bytes_per_monomer": (301.975040e6 + 91.038976e6) / 1.6e6,
+               "kg_md_sha1": "19781cb9468660a8fa6aa0dc8b66e8cdb0ee1e0c"}
 
 WORKLOADS = {
     "cfg5": dict(index=5, desc="1000 chains x N=1600 (1.6M monomers), kappa=3.5, rho=0.85"),
