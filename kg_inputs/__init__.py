@@ -110,3 +110,15 @@ def make(index: int, melt: int = 0, **over) -> Melt:
     d = config(index, melt)
     d.update(over)
     return random_walk_melt(d["n_chains"], d["chain_len"], d["rho"], d["kappa"], d["seed"])
+
+
+def hooked_pair(D: float = 1.2, lift: float = 0.6, box: float = 10.0) -> Melt:
+    """Two three-monomer chains hooked around each other, for primitive-path
+    tests: chain A has its ends at c -+ (D, 0, 0) and its middle monomer at
+    c + (0, lift, 0); chain B has its ends at c -+ (0, 0, D) and its middle at
+    c - (0, lift, 0); c is the box centre.  Velocities zero."""
+    c = 0.5 * box
+    pts = [(c - D, c, c), (c, c + lift, c), (c + D, c, c),
+           (c, c, c - D), (c, c - lift, c), (c, c, c + D)]
+    x = np.array(pts, dtype=np.float64).T.copy()
+    return Melt(2, 3, float(box), 0.0, x, np.zeros_like(x))
