@@ -372,8 +372,9 @@ def run_ours(args, world, rank, local):
 
     # secondary: the same step in plain binary64 on this GPU (single rank), and
     # the learned double-bridging proposal against the uniform one
-    sec = lsec = bsec = None
+    sec = lsec = bsec = psec = None
     if world == 1 and args.secondary:
+        psec = ppa_secondary(kg, torch, ctx, m)
         sec = secondary(kg, torch, args, local)
         bsec = batched_secondary(kg, torch, args, local)
         lsec = learned_secondary(kg, torch, args, local)
@@ -432,7 +433,40 @@ def run_ours(args, world, rank, local):
         line["batched"] = bsec
     if lsec:
         line["learned_db"] = lsec
+    if psec:
+        line["ppa"] = psec
     print(json.dumps(line))
+
+
+PPA_ITERS = 2000
+
+
+def ppa_secondary(kg, torch, ctx, m):
+    """Primitive-path analysis of the equilibrated benchmark melt: calls of 0
+    and PPA_ITERS minimisation steps, each timed with CUDA events on the
+    library's stream; the per-step time is their difference over PPA_ITERS,
+    so the copy of the state, the work-space allocation and the first list
+    cancel.  A throughput figure over the contraction phase, where most list
+    builds fall."""
+    stream = torch.cuda.current_stream()
+    kw = dict(dt=0.005, gamma=1.0, skin=0.3)
+    kg.kg_primitive_path(ctx, 0, m.n_chains, 2, **kw)            # warm-up
+    ms = {}
+    for n in (0, PPA_ITERS):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lpp, res = kg.kg_primitive_path(ctx, 0, m.n_chains, n, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[n] = e0.elapsed_time(e1)
+    per = (ms[PPA_ITERS] - ms[0]) / PPA_ITERS
+    log(f"ppa: {per * 1e3:.1f} us per step, L_pp {res['lpp_mean']:.2f} after {PPA_ITERS} steps, "
+        f"{res['builds']} list builds")
+    return {"workload": f"{m.n_chains} chains x N={m.chain_len}, the equilibrated benchmark melt",
+            "steps": PPA_ITERS, "ms_per_step": per, "monomer_steps_per_s": m.M / (per * 1e-3),
+            "setup_ms": ms[0], "lpp_mean": res["lpp_mean"], "fmax": res["fmax"], "list_builds": res["builds"],
+            "precision": "mixed",
+            "timing": f"CUDA events: (call with {PPA_ITERS} steps - call with 0 steps) / {PPA_ITERS}"}
 
 
 # kappa scan of eight melts of uneven size (kappa, N, chains): 485k monomers

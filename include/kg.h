@@ -354,6 +354,63 @@ kg_status kg_pair_distribution(kg_ctx *c, int melt, double r_max, int nbins, dou
  * l0 <= 0 or a non-finite value in the range. */
 kg_status kg_fit_lk(const double *r2n, int N, double l0, int n_lo, int n_hi, double *lk);
 
+/* Primitive-path analysis (PPA), the N_e measurement of Sec. III: the method of
+ * Everaers et al. (Science 303, 823 (2004)), which the paper cites without
+ * restating, in this form -- both end monomers of every chain fixed; the n = 12
+ * member of Eq. 5 (LJ 12-6 truncated and shifted at 2^(1/6)) only between
+ * monomers of different chains (any periodic image), none inside a chain, so
+ * bonds keep their FENE part alone (Eq. 10 without U_MLJ, k = k_fene, R0 of
+ * kg_params); no bending; the energy minimised by n_iter steps of the
+ * integrator at T = 0 (velocity Verlet with friction gamma and no noise) from
+ * rest:  v += dt/2 F;  x += dt v;  F = F_c(x) - gamma v;  v += dt/2 F.
+ * Runs on a copy of `melt`'s current state; the simulation state is not
+ * changed.  Neighbours within 2^(1/6) + skin are listed on a cell grid of side
+ * >= 2^(1/6) + skin, rebuilt when a monomer has moved more than skin / 2 (the
+ * grid must have 3 to 1024 cells a side, else KG_ERR_INVALID_ARG).
+ * precision KG_FP64: everything in binary64.  KG_MIXED: pair vectors from
+ * binary32 cell offsets plus binary32 displacements (~1e-7 sigma), bond vectors
+ * as binary64 differences rounded to binary32, forces, velocities and the kick
+ * in binary32, positions in binary64.
+ *
+ *   lpp       host, n_chains doubles or NULL: every chain's minimised contour
+ *             length sum_i |r_{i+1} - r_i|
+ *   x_out     host or device, 3 M doubles (3, M) slot order, or NULL: the
+ *             minimised positions
+ *   res       host or NULL: lpp_mean, the mean over chains (L_pp of Eq. 22);
+ *             fmax, the largest net force on a mobile monomer after the last
+ *             step (a convergence measure); builds, the neighbour-list builds
+ * Device work space per monomer: 24 + 72 (KG_FP64) or 24 + 24 (KG_MIXED)
+ * bytes of state, 64 bytes of records and 133 ints; plus the cell grid.
+ * Synchronises.  A bond reaching R0 returns KG_ERR_BOND_OVERSTRETCH, a
+ * non-finite position KG_ERR_NONFINITE, more than 128 listed neighbours or
+ * 1024 monomers in one cell KG_ERR_CAPACITY; none of them latches the context. */
+typedef struct {
+    long long n_iter;         /* minimisation steps (>= 0)                                */
+    double dt;                /* step (> 0)                                               */
+    double gamma;             /* friction (>= 0)                                          */
+    double skin;              /* Verlet skin (> 0)                                        */
+    double k_fene;            /* FENE spring; <= 0: k_n of Eq. 9 at n = 12                */
+    int precision;            /* KG_FP64 or KG_MIXED                                      */
+} kg_ppa_params;
+
+typedef struct {
+    double lpp_mean;          /* mean primitive-path length over chains                   */
+    double fmax;              /* largest net force on a mobile monomer after the last step */
+    long long builds;         /* neighbour-list builds, the first included                */
+} kg_ppa_result;
+
+kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *p, double *lpp, double *x_out,
+                            kg_ppa_result *res);
+
+/* Entanglement length from the primitive paths (Eq. 22, Sec. III): the N_eK
+ * solving (2 N_eK + exp(-2 N_eK) - 1) / (2 N_eK^2) = (L_pp / L)^2 with
+ * L = (chain_len - 1) l0, found by bisection in log N_eK (the left-hand side
+ * falls monotonically from 1 to 0), and N_e = N_eK l_K / l0 (n_e may be NULL;
+ * l_k is then ignored).  KG_ERR_INVALID_ARG unless 0 < L_pp / L < 1.  Host
+ * only. */
+kg_status kg_entanglement_length(double lpp_mean, int chain_len, double l0, double l_k, double *n_ek,
+                                 double *n_e);
+
 /* Largest n_chains * chain_len that kg_r2n_noalloc accepts. */
 #define KG_NOALLOC_MAX_MONOMERS 2097152
 

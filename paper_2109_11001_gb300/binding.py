@@ -28,7 +28,8 @@ EXPORTS = ["kg_create", "kg_load_config", "kg_get_config", "kg_set_potential_sch
            "kg_strerror", "kg_r2n_noalloc", "kg_mlp_set_weights", "kg_mlp_get_weights", "kg_mlp_forward",
            "kg_mlp_loss_grad", "kg_mlp_log", "kg_mlp_log_read", "kg_mlp_train", "kg_db_sweep_learned",
            "kg_db_sweep_learned_k", "kg_db_proposal", "kg_msd_reset", "kg_msd", "kg_fit_lk",
-           "kg_structure_factor", "kg_pair_distribution", "kg_generate_fr"]
+           "kg_structure_factor", "kg_pair_distribution", "kg_generate_fr", "kg_primitive_path",
+           "kg_entanglement_length"]
 
 KG_MLP_NPARAM = 5825
 KG_DB_CAND_MAX = 48
@@ -63,6 +64,18 @@ class kg_obs(C.Structure):
 class kg_tuning(C.Structure):
     _fields_ = [("skin", C.c_double), ("block_size", C.c_int), ("ms_per_step", C.c_double), ("trials", C.c_int),
                 ("threads_per_monomer", C.c_int)]
+
+
+class kg_ppa_params(C.Structure):
+    _fields_ = [("n_iter", C.c_longlong), ("dt", C.c_double), ("gamma", C.c_double), ("skin", C.c_double),
+                ("k_fene", C.c_double), ("precision", C.c_int)]
+
+
+class kg_ppa_result(C.Structure):
+    _fields_ = [("lpp_mean", C.c_double), ("fmax", C.c_double), ("builds", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class kg_db_stats(C.Structure):
@@ -122,6 +135,8 @@ def load(path: str = LIB_PATH):
         "kg_structure_factor": (i, [p, i, p, i, p]),
         "kg_generate_fr": (i, [i, i, d, d, d, C.c_ulonglong, i, p, C.POINTER(d), C.POINTER(i)]),
         "kg_pair_distribution": (i, [p, i, d, i, p]),
+        "kg_primitive_path": (i, [p, i, C.POINTER(kg_ppa_params), p, p, C.POINTER(kg_ppa_result)]),
+        "kg_entanglement_length": (i, [d, i, d, d, C.POINTER(d), C.POINTER(d)]),
         "kg_mlp_set_weights": (i, [p, p]),
         "kg_mlp_get_weights": (i, [p, p]),
         "kg_mlp_forward": (i, [p, p, ll, p]),
@@ -261,6 +276,27 @@ def kg_pair_distribution(ctx, melt, r_max, nbins):
     g = np.zeros(int(nbins))
     _check(load().kg_pair_distribution(ctx, int(melt), float(r_max), int(nbins), ptr(g)), "kg_pair_distribution")
     return g
+
+
+def kg_primitive_path(ctx, melt, n_chains, n_iter, dt=0.005, gamma=1.0, skin=0.3, k_fene=0.0, x_out=None,
+                      precision=KG_MIXED):
+    """Primitive-path analysis of a melt: returns (per-chain L_pp, result dict
+    with lpp_mean, fmax, builds); x_out (3, M) float64 receives the minimised
+    positions when given."""
+    pp = kg_ppa_params(int(n_iter), float(dt), float(gamma), float(skin), float(k_fene), int(precision))
+    lpp = np.zeros(int(n_chains))
+    res = kg_ppa_result()
+    _check(load().kg_primitive_path(ctx, int(melt), C.byref(pp), ptr(lpp), ptr(x_out), C.byref(res)),
+           "kg_primitive_path")
+    return lpp, res.as_dict()
+
+
+def kg_entanglement_length(lpp_mean, chain_len, l_k, l0=0.960897):
+    """(N_eK, N_e) from the mean primitive-path length (Eq. 22)."""
+    n_ek, n_e = C.c_double(), C.c_double()
+    _check(load().kg_entanglement_length(float(lpp_mean), int(chain_len), float(l0), float(l_k), C.byref(n_ek),
+                                         C.byref(n_e)), "kg_entanglement_length")
+    return n_ek.value, n_e.value
 
 
 def kg_msd(ctx, melt):

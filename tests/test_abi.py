@@ -65,3 +65,19 @@ def test_create_rejects_bad_arguments(lib):
     with pytest.raises(kg.KGError) as e:
         kg.kg_create(kg.make_params([(10, 10, 20.0, 1.0)], precision=7), 0)
     assert e.value.status == kg.KG_ERR_INVALID_ARG
+
+
+def test_entanglement_length_host_matches_oracle(lib):
+    """Eq. 22 solved by the library's host bisection and by the oracle's root finder."""
+    import paper_2109_11001_gb300 as kg
+    from oracle import ppa as P
+    N, lk = 400, 2.4
+    for ratio in (0.05, 0.2, 0.45, 0.8, 0.999):
+        n_ek, n_e = kg.kg_entanglement_length(ratio * (N - 1) * P.L0, N, lk)
+        ref = P.n_ek_from_ratio(ratio)
+        assert n_ek == pytest.approx(ref, rel=1e-12)
+        assert n_e == pytest.approx(ref * lk / P.L0, rel=1e-12)
+    for bad in (0.0, 1.0, 1.3):
+        with pytest.raises(kg.KGError) as e:
+            kg.kg_entanglement_length(bad * (N - 1) * P.L0, N, lk)
+        assert e.value.status == kg.KG_ERR_INVALID_ARG
