@@ -9,34 +9,45 @@
 //   * no bending energy (Eq. 4 off);
 //   * the energy is minimised by the path's integrator at T = 0, Langevin
 //     velocity Verlet with zero noise (damped dynamics), from rest.
-// It runs on a binary64 copy of the melt in slot order (chain-major, s = c N +
-// i), (3, M) SoA x, v, F, and leaves the simulation state untouched.
+// It runs on a copy of the melt and leaves the simulation state untouched.
+//
+// Storage.  The copy lives in cell order: every list build bins the monomers
+// on a grid of n_c^3 cells of side h >= r_c + skin (n_c >= 3), sorts them by
+// cell (a counting sort, each cell's run ordered by the previous storage index,
+// so the order is deterministic) and moves every per-monomer array into that
+// order, double-buffered with the buffer in use named by flag word 3.  A
+// cell's monomers are then one contiguous run of storage indices, the 32
+// monomers of a warp sit in a few neighbouring cells, and the candidate
+// loads of the build and the neighbour gathers of the force kernel stay in
+// L1 and L2.  Bonds reach their partners through a partner-index array
+// refreshed at each build; results return to slot order (chain-major, s = c N
+// + i) at the end.
 //
 // Neighbours: a Verlet list of interchain pairs within r_c + skin, entries
-// j | q << IDX_BITS (q the stencil cell, which fixes the periodic image), stored
-// column-major (entry k of monomer s at k M + s, so the loads of entry k by a
-// warp are one coalesced row), rebuilt on the device whenever a monomer has
-// moved more than skin / 2 since the last build (flag word 1).  Steps run as
-// a captured CUDA graph of 25 steps, each step drift, a one-thread kernel that
-// arms a conditional graph node with the build request, the node holding the
-// build kernels, and the force kernel, the scheme of the MD graphs; steps
-// outside whole graphs launch the build kernels directly, which return at once
-// without a request.  The build bins monomers on a grid of
-// n_c^3 cells of side h >= r_c + skin (n_c >= 3), keeps each monomer's binary32
-// offset from its cell's corner, sorts every cell by slot (deterministic
-// lists and sums) and tests candidates in binary32 on those offsets, with a
-// margin that keeps every pair within r_c + skin: the list only has to
-// contain the pairs, so its edge need not be exact.
+// j | q << IDX_BITS (j a storage index, q the stencil cell, which fixes the
+// periodic image), column-major (entry k of monomer p at k M + p, so the loads
+// of entry k by a warp are one coalesced row), rebuilt whenever a monomer has
+// moved more than skin / 2 since the last build (flag word 1).  Candidates are
+// tested in binary32 on the monomers' offsets from their cells' corners, with
+// a margin that keeps every pair within r_c + skin: the list only has to
+// contain the pairs, so its edge need not be exact.  Steps run as a captured
+// CUDA graph of 25 steps, each step drift, a one-thread kernel that arms a
+// conditional graph node with the build request, the node holding the build
+// kernels, and the force kernel, the scheme of the MD graphs; steps outside
+// whole graphs launch the build kernels directly, which return at once without
+// a request.
 //
 // Two force kernels.  Binary64 (KG_FP64): minimum-image distances and forces
 // in binary64, the same update order as the definition.  Mixed (KG_MIXED), the
 // GB300 path, whose binary64 rate is a small fraction of its binary32 rate:
-// the pair vector is (o_j + d_j) - (o_s + d_s) + q h in binary32, o the build
-// offset and d the binary64 displacement since the build rounded to binary32,
-// so every term is small and the vector is good to ~1e-7 sigma; bond vectors
-// are binary64 differences rounded to binary32; forces, velocities and the
-// kick are binary32 and the positions binary64, which they step by the
-// binary32 increment dt v.
+// the pair vector is (o_j + d_j) - (o_p + d_p) + q h in binary32, o the build
+// offset and d the displacement since the build, so every term is small and
+// the vector is good to ~1e-7 sigma.  The binary64 position is touched only
+// at a build: between builds a monomer's position is its binary64 build
+// position plus d, and every step runs in binary32 (a bond vector is its
+// build value, a binary64 difference rounded to binary32, plus the
+// difference of the two displacements); the build folds d into the binary64
+// position.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -47,27 +58,20 @@
 
 namespace kg {
 
-// kg_md.cu: exclusive scan of the cell counts, the scatter into cell order
-// (with the records, w = slot) and the per-cell sort by slot
+// kg_md.cu: exclusive scan of the cell counts
 __global__ void k_scan1(const int *__restrict__ in, int *__restrict__ out, int *__restrict__ bsum, int n,
                         const unsigned *__restrict__ flags);
 __global__ void k_scan2(int *__restrict__ out, const int *__restrict__ bsum, int n, int nblk,
                         const unsigned *__restrict__ flags);
-__global__ void k_scatter(const int *__restrict__ cellid, const int *__restrict__ rank,
-                          const int *__restrict__ start, int *__restrict__ list, int M,
-                          const unsigned *__restrict__ flags, const float4 *__restrict__ recb,
-                          float4 *__restrict__ recs);
-__global__ void k_cellsort(const int *__restrict__ start, int *__restrict__ list, float4 *__restrict__ recs,
-                           int *__restrict__ count, int ncell, unsigned *__restrict__ flags);
 
 namespace {
 
 constexpr double PPA_RC = 1.122462048309373;   // 2^(1/6)
 constexpr int PPA_MAXNB = 128;                  // list entries per monomer (overflow: capacity error)
+constexpr int PPA_CELL_CAP = 1024;              // monomers per cell the build accepts
 constexpr int PPA_GRAPH_ITERS = 25;             // steps per captured graph
 constexpr int PPA_BLOCK = 128;
-constexpr int PPA_LAUNCHES_PER_ITER = 8;     // direct launches of one step
-constexpr int PPA_BUILD_LAUNCHES = 6;        // kernels of one list build
+constexpr unsigned FIXED_BIT = 0x80000000u;     // record word w: chain index | FIXED_BIT at a chain end
 
 struct PpaArgs {
     int M, N, nc, ncell;
@@ -76,20 +80,26 @@ struct PpaArgs {
     double half_skin2;           // (skin / 2)^2
     double dt, gamma, k, R0sq;
     float dtf, gammaf, kf, invR0sqf, half_skin2f;
-    double *x, *v, *F, *xb;      // (3, M) each; xb = positions at the last build (binary64 mode)
-    float *v32, *F32;            // (3, M) velocities and forces of the mixed mode
-    float4 *rec, *recs, *pg;     // build offsets + cell code; the same in cell order (w = slot); offsets + d
-    float4 *dl;                  // mixed: displacement d since the build
-    int *cellid, *rank, *count, *start, *list, *nn;
+    // double-buffered per-monomer state (storage order), buffer flags[3] in use
+    double *x0, *x1;             // (3, M) positions (mixed: positions at the last build)
+    double *v0, *v1, *F0, *F1;   // (3, M) velocities and forces, binary64 mode
+    float *u0, *u1, *G0, *G1;    // (3, M) velocities and forces, mixed mode
+    int *slot0, *slot1;          // storage index -> slot
+    // single-buffered, rewritten at each build (storage order of the new buffer)
+    double *xb;                  // positions at the build (binary64 mode)
+    float4 *rec, *pg, *dl;       // build offset + (chain | FIXED_BIT); offset + d; d
+    float4 *off;                 // bin output in the old order: offset + cell index
+    float4 *bvec;                // mixed: bond vector to the next monomer at the build
+    int2 *bp;                    // storage indices of the bonded partners (-1 past an end)
+    int *pos_of;                 // slot -> storage index
+    int *cellof;                 // packed cell coordinates of each storage index
+    int *rank, *count, *start, *list, *nn;
     unsigned *nl;                // entries j | q << IDX_BITS, column-major
-    unsigned *flags;             // [0] error bits, [1] rebuild request, [2] builds
+    unsigned *flags;             // [0] error bits, [1] rebuild request, [2] builds, [3] buffer in use
 };
 
-__device__ __forceinline__ bool fixed_end(const PpaArgs &a, int s)
-{
-    const int i = s % a.N;
-    return i == 0 || i == a.N - 1;
-}
+__device__ __forceinline__ int cur_buf(const PpaArgs &a) { return (int)(a.flags[3] & 1u); }
+__device__ __forceinline__ bool build_requested(const PpaArgs &a) { return a.flags[1] && !a.flags[0]; }
 
 __device__ __forceinline__ double min_image(double d, const PpaArgs &a)
 {
@@ -103,21 +113,28 @@ __device__ __forceinline__ float3 stencil_shift(unsigned q, float h)
     return make_float3((float)dx * h, (float)dy * h, (float)dz * h);
 }
 
+__device__ __forceinline__ bool is_fixed(const float4 &r) { return (__float_as_uint(r.w) & FIXED_BIT) != 0u; }
+
+// ---- one step: drift, (conditional) build, force ----
+
 // first half kick and drift of the mobile monomers:
 // v <- v + (dt/2) F; x <- x + dt v; request a rebuild past skin / 2
 __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_drift_f64(PpaArgs a)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.M || fixed_end(a, s)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.M || is_fixed(a.rec[p])) return;
+    const int cb = cur_buf(a);
+    double *x = cb ? a.x1 : a.x0, *v = cb ? a.v1 : a.v0;
+    const double *F = cb ? a.F1 : a.F0;
     const double hdt = 0.5 * a.dt;
     double dr2 = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const size_t o = (size_t)d * a.M + s;
-        const double vh = __dadd_rn(a.v[o], __dmul_rn(hdt, a.F[o]));
-        const double xn = __dadd_rn(a.x[o], __dmul_rn(a.dt, vh));
-        a.v[o] = vh;
-        a.x[o] = xn;
+        const size_t o = (size_t)d * a.M + p;
+        const double vh = __dadd_rn(v[o], __dmul_rn(hdt, F[o]));
+        const double xn = __dadd_rn(x[o], __dmul_rn(a.dt, vh));
+        v[o] = vh;
+        x[o] = xn;
         const double e = xn - a.xb[o];
         dr2 += e * e;
     }
@@ -127,28 +144,29 @@ __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_drift_f64(PpaArgs a)
     }
 }
 
-// mixed: the same step with binary32 v and F; the increment dt v (binary32)
-// goes into the binary64 position and into the binary32 displacement d, and
-// the gather record becomes o + d
+// mixed: the same step with binary32 v and F; the drift goes into the
+// binary32 displacement d since the build, and the gather record becomes o + d
 __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_drift_mixed(PpaArgs a)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.M || fixed_end(a, s)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.M) return;
+    const float4 r = a.rec[p];
+    if (is_fixed(r)) return;
+    const int cb = cur_buf(a);
+    float *u = cb ? a.u1 : a.u0;
+    const float *G = cb ? a.G1 : a.G0;
     const float hdt = 0.5f * a.dtf;
-    const float4 d0 = a.dl[s];
+    const float4 d0 = a.dl[p];
     float dd[3] = {d0.x, d0.y, d0.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const size_t o = (size_t)d * a.M + s;
-        const float vh = a.v32[o] + hdt * a.F32[o];
-        const float inc = a.dtf * vh;
-        a.v32[o] = vh;
-        a.x[o] += (double)inc;
-        dd[d] += inc;
+        const size_t o = (size_t)d * a.M + p;
+        const float vh = u[o] + hdt * G[o];
+        u[o] = vh;
+        dd[d] += a.dtf * vh;
     }
-    a.dl[s] = make_float4(dd[0], dd[1], dd[2], 0.f);
-    const float4 r = a.rec[s];
-    a.pg[s] = make_float4(r.x + dd[0], r.y + dd[1], r.z + dd[2], r.w);
+    a.dl[p] = make_float4(dd[0], dd[1], dd[2], 0.f);
+    a.pg[p] = make_float4(r.x + dd[0], r.y + dd[1], r.z + dd[2], r.w);
     const float dr2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
     if (!(dr2 <= a.half_skin2f)) {
         if (!isfinite(dr2)) atomicOr(a.flags, ERR_NONFINITE);
@@ -156,64 +174,178 @@ __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_drift_mixed(PpaArgs a)
     }
 }
 
-// cell of each monomer from its wrapped position; the build record (offset
-// from the cell's corner, cell code), the gather record and the build position
+// build 1: cell of each monomer (current order) from its wrapped position,
+// its offset from the cell's corner and its rank in the cell; mixed: the
+// displacement d is folded into the binary64 position here, each thread on
+// its own monomer (the permutation then reads positions only)
 __global__ void __launch_bounds__(256) k_ppa_bin(PpaArgs a)
 {
-    if (!a.flags[1] || a.flags[0]) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.M) return;
+    if (!build_requested(a)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.M) return;
+    double *x = cur_buf(a) ? a.x1 : a.x0;
+    const float4 dp = a.u0 ? a.dl[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float dd[3] = {dp.x, dp.y, dp.z};
     int cc[3];
-    float off[3];
+    float o[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const double xd = a.x[(size_t)d * a.M + s];
+        double xd = x[(size_t)d * a.M + p];
+        if (a.u0) {                                    // mixed: fold d into the binary64 position
+            xd += (double)dd[d];
+            x[(size_t)d * a.M + p] = xd;
+        }
         const double w = xd - a.L * floor(xd * a.invL);
         int q = (int)(w * a.invh);
         q = q < 0 ? 0 : (q >= a.nc ? a.nc - 1 : q);
         cc[d] = q;
-        off[d] = (float)(w - (double)q * a.h);
-        if (a.xb) a.xb[(size_t)d * a.M + s] = xd;
+        o[d] = (float)(w - (double)q * a.h);
     }
-    const float4 r = make_float4(off[0], off[1], off[2], __uint_as_float(pack_code(cc[0], cc[1], cc[2])));
-    a.rec[s] = r;
-    a.pg[s] = r;
-    a.dl[s] = make_float4(0.f, 0.f, 0.f, 0.f);
     const int c = (cc[2] * a.nc + cc[1]) * a.nc + cc[0];
-    a.cellid[s] = c;
-    a.rank[s] = atomicAdd(a.count + c, 1);
+    a.off[p] = make_float4(o[0], o[1], o[2], __int_as_float(c));
+    a.rank[p] = atomicAdd(a.count + c, 1);
 }
 
-// interchain Verlet list of monomer s from the binary32 build offsets: every t
-// of another chain in the 27 cells around s whose vector o_t - o_s + q h is
-// shorter than r_c + skin (plus a margin above the offsets' rounding)
+// build 2: the current storage indices in cell order
+__global__ void __launch_bounds__(256) k_ppa_scatter(PpaArgs a)
+{
+    if (!build_requested(a)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.M) return;
+    a.list[a.start[__float_as_int(a.off[p].w)] + a.rank[p]] = p;
+}
+
+// build 3: each cell's run ordered by current storage index (deterministic);
+// clear the counts for the next build
+__global__ void __launch_bounds__(256) k_ppa_cellsort(PpaArgs a)
+{
+    if (!build_requested(a)) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.ncell) return;
+    const int b0 = a.start[c], b1 = a.start[c + 1];
+    a.count[c] = 0;
+    if (b1 - b0 > PPA_CELL_CAP) {
+        atomicOr(a.flags, ERR_NL_CAPACITY);
+        return;
+    }
+    for (int k = b0 + 1; k < b1; ++k) {
+        const int v = a.list[k];
+        int j = k - 1;
+        while (j >= b0 && a.list[j] > v) {
+            a.list[j + 1] = a.list[j];
+            --j;
+        }
+        a.list[j + 1] = v;
+    }
+}
+
+// build 4: move every per-monomer array into cell order (the other buffer);
+// the records, displacement, build positions and slot -> storage map
+__global__ void __launch_bounds__(256) k_ppa_permute(PpaArgs a)
+{
+    if (!build_requested(a)) return;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.M) return;
+    const int cb = cur_buf(a);
+    const int p = a.list[q];
+    const size_t M = a.M;
+    const double *xs = cb ? a.x1 : a.x0;
+    double *xd = cb ? a.x0 : a.x1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double xv = xs[d * M + p];
+        xd[d * M + q] = xv;
+        if (a.xb) a.xb[d * M + q] = xv;
+    }
+    if (a.u0) {
+        const float *us = cb ? a.u1 : a.u0, *Gs = cb ? a.G1 : a.G0;
+        float *ud = cb ? a.u0 : a.u1, *Gd = cb ? a.G0 : a.G1;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ud[d * M + q] = us[d * M + p];
+            Gd[d * M + q] = Gs[d * M + p];
+        }
+    } else {
+        const double *vs = cb ? a.v1 : a.v0, *Fs = cb ? a.F1 : a.F0;
+        double *vd = cb ? a.v0 : a.v1, *Fd = cb ? a.F0 : a.F1;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            vd[d * M + q] = vs[d * M + p];
+            Fd[d * M + q] = Fs[d * M + p];
+        }
+    }
+    const int s = (cb ? a.slot1 : a.slot0)[p];
+    (cb ? a.slot0 : a.slot1)[q] = s;
+    a.pos_of[s] = q;
+    const int i = s % a.N;
+    const unsigned w = (unsigned)(s / a.N) | ((i == 0 || i == a.N - 1) ? FIXED_BIT : 0u);
+    const float4 o = a.off[p];
+    const float4 r = make_float4(o.x, o.y, o.z, __uint_as_float(w));
+    a.rec[q] = r;
+    a.pg[q] = r;
+    a.dl[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int c = __float_as_int(o.w);
+    a.cellof[q] = (int)pack_code(c % a.nc, (c / a.nc) % a.nc, c / (a.nc * a.nc));
+}
+
+// build 5 (one thread): the new buffer becomes the one in use
+__global__ void k_ppa_flip(PpaArgs a)
+{
+    if (build_requested(a)) a.flags[3] ^= 1u;
+}
+
+// build 6: storage indices of each monomer's bonded partners; mixed: the
+// bond vector to the next monomer (binary64 difference rounded to binary32)
+__global__ void __launch_bounds__(256) k_ppa_partners(PpaArgs a)
+{
+    if (!build_requested(a)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.M) return;
+    const int cb = cur_buf(a);
+    const int s = (cb ? a.slot1 : a.slot0)[p];
+    const int i = s % a.N;
+    const int2 b = make_int2(i > 0 ? a.pos_of[s - 1] : -1, i < a.N - 1 ? a.pos_of[s + 1] : -1);
+    a.bp[p] = b;
+    if (a.bvec && b.y >= 0) {
+        const double *x = cb ? a.x1 : a.x0;
+        const size_t M = a.M;
+        a.bvec[p] = make_float4((float)(x[b.y] - x[p]), (float)(x[M + b.y] - x[M + p]),
+                                (float)(x[2 * M + b.y] - x[2 * M + p]), 0.f);
+    }
+}
+
+// build 7: interchain Verlet list of monomer p from the binary32 build
+// offsets: every t of another chain in the 27 cells around p whose vector
+// o_t - o_p + q h is shorter than r_c + skin (plus a margin above the offsets'
+// rounding)
 __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_nlist(PpaArgs a)
 {
-    if (!a.flags[1] || a.flags[0]) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.M) return;
-    const float4 rs = a.rec[s];
-    const unsigned code = __float_as_uint(rs.w);
+    if (!build_requested(a)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.M) return;
+    const float4 rp = a.rec[p];
+    const unsigned chain = __float_as_uint(rp.w) & ~FIXED_BIT;
+    const unsigned code = (unsigned)a.cellof[p];
     const int cx = (int)(code & CODE_MASK), cy = (int)((code >> CODE_BITS) & CODE_MASK),
               cz = (int)(code >> (2 * CODE_BITS));
-    const unsigned c0 = (unsigned)(s - s % a.N);     // first slot of the chain of s
+    const int nc = a.nc;
+    auto wrap = [nc](int v) { return v < 0 ? v + nc : (v >= nc ? v - nc : v); };
     int n = 0;
     unsigned q = 0;
     for (int dz = -1; dz <= 1; ++dz) {
-        const int z = (cz + dz + a.nc) % a.nc;
+        const int z = wrap(cz + dz);
         for (int dy = -1; dy <= 1; ++dy) {
-            const int y = (cy + dy + a.nc) % a.nc;
+            const int zy = (z * nc + wrap(cy + dy)) * nc;
             for (int dx = -1; dx <= 1; ++dx, ++q) {
-                const int c = (z * a.nc + y) * a.nc + (cx + dx + a.nc) % a.nc;
-                const float sx = (float)dx * a.hf - rs.x, sy = (float)dy * a.hf - rs.y, sz = (float)dz * a.hf - rs.z;
-                const int p1 = a.start[c + 1];
-                for (int p = a.start[c]; p < p1; ++p) {
-                    const float4 rj = a.recs[p];
-                    const int j = __float_as_int(rj.w);
-                    if ((unsigned)j - c0 < (unsigned)a.N) continue;   // same chain
+                const int cn = zy + wrap(cx + dx);
+                const float sx = (float)dx * a.hf - rp.x, sy = (float)dy * a.hf - rp.y, sz = (float)dz * a.hf - rp.z;
+                const int j1 = __ldg(a.start + cn + 1);
+                for (int j = __ldg(a.start + cn); j < j1; ++j) {
+                    const float4 rj = __ldg(a.rec + j);
+                    if ((__float_as_uint(rj.w) & ~FIXED_BIT) == chain) continue;
                     const float ex = rj.x + sx, ey = rj.y + sy, ez = rj.z + sz;
                     if (ex * ex + ey * ey + ez * ez < a.rl2f) {
-                        if (n < PPA_MAXNB) a.nl[(size_t)n * a.M + s] = (unsigned)j | (q << IDX_BITS);
+                        if (n < PPA_MAXNB) a.nl[(size_t)n * a.M + p] = (unsigned)j | (q << IDX_BITS);
                         ++n;
                     }
                 }
@@ -224,71 +356,39 @@ __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_nlist(PpaArgs a)
         atomicOr(a.flags, ERR_NL_CAPACITY);
         n = PPA_MAXNB;
     }
-    a.nn[s] = n;
-}
-
-// FENE force of the two bonds of mobile monomer s (binary64, unwrapped)
-__device__ __forceinline__ void bond_forces(const PpaArgs &a, int s, double xs, double ys, double zs, double &fx,
-                                            double &fy, double &fz)
-{
-    const size_t M = a.M;
-#pragma unroll
-    for (int side = -1; side <= 1; side += 2) {
-        const int t = s + side;
-        const double bx = __dsub_rn(a.x[t], xs), by = __dsub_rn(a.x[M + t], ys), bz = __dsub_rn(a.x[2 * M + t], zs);
-        const double q = __dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), __dmul_rn(bz, bz)) / a.R0sq;
-        if (!(q < 1.0)) {
-            atomicOr(a.flags, ERR_OVERSTRETCH);
-            continue;
-        }
-        const double gb = a.k / (1.0 - q);
-        fx += gb * bx;
-        fy += gb * by;
-        fz += gb * bz;
-    }
-}
-
-// F <- F_c(x) - gamma v; v <- v + half dt F (half = 0 for the first force)
-__device__ __forceinline__ void kick(const PpaArgs &a, int s, double fx, double fy, double fz, double half)
-{
-    const double hdt = half * a.dt;
-    const double f[3] = {fx, fy, fz};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const size_t o = (size_t)d * a.M + s;
-        const double vh = a.v[o];
-        const double Ft = __dsub_rn(f[d], __dmul_rn(a.gamma, vh));
-        a.F[o] = Ft;
-        a.v[o] = __dadd_rn(vh, __dmul_rn(hdt, Ft));
-    }
+    a.nn[p] = n;
 }
 
 // the thread of monomer 0 retires the build request of this step (every build
 // kernel has run) and counts the build
-__device__ __forceinline__ void retire_build(const PpaArgs &a, int s)
+__device__ __forceinline__ void retire_build(const PpaArgs &a, int p)
 {
-    if (s == 0 && a.flags[1]) {
+    if (p == 0 && a.flags[1]) {
         if (!a.flags[0]) a.flags[2] += 1u;
         a.flags[1] = 0u;
     }
 }
 
-// binary64 force: minimum-image pair vectors, LJ 12-6 between chains
+// binary64 force: minimum-image pair vectors, LJ 12-6 between chains, FENE
+// bonds; F <- F_c(x) - gamma v; v <- v + half dt F (half = 0 for the first force)
 __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_force_f64(PpaArgs a, double half)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    retire_build(a, s);
-    if (s >= a.M || fixed_end(a, s)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    retire_build(a, p);
+    if (p >= a.M || is_fixed(a.rec[p])) return;
+    const int cb = cur_buf(a);
+    const double *x = cb ? a.x1 : a.x0;
+    double *v = cb ? a.v1 : a.v0, *F = cb ? a.F1 : a.F0;
     const size_t M = a.M;
-    const double xs = a.x[s], ys = a.x[M + s], zs = a.x[2 * M + s];
+    const double xs = x[p], ys = x[M + p], zs = x[2 * M + p];
     double fx = 0.0, fy = 0.0, fz = 0.0;
-    const int n = a.nn[s];
+    const int n = a.nn[p];
     const double rc2 = PPA_RC * PPA_RC;
     for (int k = 0; k < n; ++k) {
-        const int j = (int)(a.nl[(size_t)k * M + s] & IDX_MASK);
-        const double ex = min_image(__dsub_rn(a.x[j], xs), a);
-        const double ey = min_image(__dsub_rn(a.x[M + j], ys), a);
-        const double ez = min_image(__dsub_rn(a.x[2 * M + j], zs), a);
+        const int j = (int)(a.nl[(size_t)k * M + p] & IDX_MASK);
+        const double ex = min_image(__dsub_rn(x[j], xs), a);
+        const double ey = min_image(__dsub_rn(x[M + j], ys), a);
+        const double ez = min_image(__dsub_rn(x[2 * M + j], zs), a);
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
         if (r2 < rc2) {
             const double ir2 = 1.0 / r2;
@@ -299,23 +399,51 @@ __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_force_f64(PpaArgs a, double h
             fz -= g * ez;
         }
     }
-    bond_forces(a, s, xs, ys, zs, fx, fy, fz);
-    kick(a, s, fx, fy, fz, half);
+    const int2 b = a.bp[p];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int t = side ? b.y : b.x;
+        const double bx = __dsub_rn(x[t], xs), by = __dsub_rn(x[M + t], ys), bz = __dsub_rn(x[2 * M + t], zs);
+        const double q = __dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), __dmul_rn(bz, bz)) / a.R0sq;
+        if (!(q < 1.0)) {
+            atomicOr(a.flags, ERR_OVERSTRETCH);
+            continue;
+        }
+        const double gb = a.k / (1.0 - q);
+        fx += gb * bx;
+        fy += gb * by;
+        fz += gb * bz;
+    }
+    const double hdt = half * a.dt;
+    const double f[3] = {fx, fy, fz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const size_t o = (size_t)d * M + p;
+        const double vh = v[o];
+        const double Ft = __dsub_rn(f[d], __dmul_rn(a.gamma, vh));
+        F[o] = Ft;
+        v[o] = __dadd_rn(vh, __dmul_rn(hdt, Ft));
+    }
 }
 
-// mixed force: binary32 pair vectors from the gather records and binary32
-// LJ 12-6; bond vectors are binary64 differences rounded to binary32, the
-// FENE force, friction and kick binary32
+// mixed force, all binary32: pair vectors from the gather records, LJ 12-6;
+// bond vectors from the build's bond vectors and the displacements; FENE,
+// friction and kick
 __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_force_mixed(PpaArgs a, float half)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    retire_build(a, s);
-    if (s >= a.M || fixed_end(a, s)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    retire_build(a, p);
+    if (p >= a.M) return;
+    const float4 ps = a.pg[p];
+    if (is_fixed(ps)) return;
+    const int cb = cur_buf(a);
+    float *u = cb ? a.u1 : a.u0, *G = cb ? a.G1 : a.G0;
     const size_t M = a.M;
-    const float4 ps = a.pg[s];
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    const int n = a.nn[s];
-    auto pair = [&](unsigned e, float4 pj) {
+    const int n = a.nn[p];
+    for (int k = 0; k < n; ++k) {
+        const unsigned e = __ldg(a.nl + (size_t)k * M + p);
+        const float4 pj = __ldg(a.pg + (e & IDX_MASK));
         const float3 sh = stencil_shift(e >> IDX_BITS, a.hf);
         const float ex = (pj.x - ps.x) + sh.x, ey = (pj.y - ps.y) + sh.y, ez = (pj.z - ps.z) + sh.z;
         const float r2 = ex * ex + ey * ey + ez * ez;
@@ -327,28 +455,17 @@ __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_force_mixed(PpaArgs a, float 
             fy -= g * ey;
             fz -= g * ez;
         }
-    };
-    // four entries in flight: their list words, then their gathers, then the arithmetic
-    int k = 0;
-    for (; k + 4 <= n; k += 4) {
-        unsigned e[4];
-        float4 pj[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = __ldg(a.nl + (size_t)(k + u) * M + s);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) pj[u] = __ldg(a.pg + (e[u] & IDX_MASK));
-#pragma unroll
-        for (int u = 0; u < 4; ++u) pair(e[u], pj[u]);
     }
-    for (; k < n; ++k) {
-        const unsigned e = __ldg(a.nl + (size_t)k * M + s);
-        pair(e, __ldg(a.pg + (e & IDX_MASK)));
-    }
-    const double xs = a.x[s], ys = a.x[M + s], zs = a.x[2 * M + s];
+    const int2 b = a.bp[p];
+    const float4 dp = a.dl[p];
 #pragma unroll
-    for (int side = -1; side <= 1; side += 2) {
-        const int t = s + side;
-        const float bx = (float)(a.x[t] - xs), by = (float)(a.x[M + t] - ys), bz = (float)(a.x[2 * M + t] - zs);
+    for (int side = 0; side < 2; ++side) {
+        const int t = side ? b.y : b.x;
+        const float4 dt_ = __ldg(a.dl + t);
+        const float4 bv = __ldg(a.bvec + (side ? p : t));
+        const float sg = side ? 1.f : -1.f;             // the previous bond is -(its bond to p)
+        const float bx = sg * bv.x + (dt_.x - dp.x), by = sg * bv.y + (dt_.y - dp.y),
+                    bz = sg * bv.z + (dt_.z - dp.z);
         const float q = (bx * bx + by * by + bz * bz) * a.invR0sqf;
         if (!(q < 1.f)) {
             atomicOr(a.flags, ERR_OVERSTRETCH);
@@ -363,51 +480,91 @@ __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_force_mixed(PpaArgs a, float 
     const float f[3] = {fx, fy, fz};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const size_t o = (size_t)d * M + s;
-        const float vh = a.v32[o];
+        const size_t o = (size_t)d * M + p;
+        const float vh = u[o];
         const float Ft = f[d] - a.gammaf * vh;
-        a.F32[o] = Ft;
-        a.v32[o] = vh + hdt * Ft;
+        G[o] = Ft;
+        u[o] = vh + hdt * Ft;
     }
 }
 
-// contour length of every chain (bond order) and the largest net force on a mobile monomer
-__global__ void __launch_bounds__(256) k_ppa_lengths(PpaArgs a, double *__restrict__ lpp,
-                                                    unsigned long long *__restrict__ fmax_bits)
+// ---- results in slot order ----
+
+// positions back to slot order; the largest net force on a mobile monomer
+__global__ void __launch_bounds__(256) k_ppa_unpermute(PpaArgs a, double *__restrict__ xs,
+                                                      unsigned long long *__restrict__ fmax_bits)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.M / a.N) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.M) return;
+    const int cb = cur_buf(a);
+    const double *x = cb ? a.x1 : a.x0;
     const size_t M = a.M;
-    double sum = 0.0, f2max = 0.0;
-    for (int i = 0; i + 1 < a.N; ++i) {
-        const size_t s = (size_t)c * a.N + i;
-        const double bx = __dsub_rn(a.x[s + 1], a.x[s]);
-        const double by = __dsub_rn(a.x[M + s + 1], a.x[M + s]);
-        const double bz = __dsub_rn(a.x[2 * M + s + 1], a.x[2 * M + s]);
-        sum += sqrt(__dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), __dmul_rn(bz, bz)));
-        if (i > 0) {
-            double f[3];
-            for (int d = 0; d < 3; ++d) f[d] = a.F32 ? (double)a.F32[d * M + s] : a.F[d * M + s];
-            const double f2 = f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
-            f2max = f2 > f2max ? f2 : f2max;
-        }
+    const int p = a.pos_of[s];
+    const float4 dp = a.u0 ? a.dl[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float dd[3] = {dp.x, dp.y, dp.z};
+    double f2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        xs[d * M + s] = x[d * M + p] + (double)dd[d];
+        const double f = a.u0 ? (double)(cb ? a.G1 : a.G0)[d * M + p] : (cb ? a.F1 : a.F0)[d * M + p];
+        f2 += f * f;
     }
-    lpp[c] = sum;
-    atomicMax(fmax_bits, (unsigned long long)__double_as_longlong(sqrt(f2max)));
+    const int i = s % a.N;
+    if (i > 0 && i < a.N - 1) atomicMax(fmax_bits, (unsigned long long)__double_as_longlong(sqrt(f2)));
+}
+
+// contour length of every chain from slot-order positions: one warp per
+// chain, lane l sums bonds l, l + 32, ..., then a fixed-order shuffle tree
+__global__ void __launch_bounds__(256) k_ppa_lengths(const double *__restrict__ x, int M, int N,
+                                                    double *__restrict__ lpp)
+{
+    const int c = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= M / N) return;
+    double sum = 0.0;
+    for (int i = lane; i + 1 < N; i += 32) {
+        const size_t s = (size_t)c * N + i;
+        const double bx = __dsub_rn(x[s + 1], x[s]);
+        const double by = __dsub_rn(x[M + s + 1], x[M + s]);
+        const double bz = __dsub_rn(x[2 * (size_t)M + s + 1], x[2 * (size_t)M + s]);
+        sum += sqrt(__dadd_rn(__dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by)), __dmul_rn(bz, bz)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if (lane == 0) lpp[c] = sum;
+}
+
+__global__ void k_ppa_iota(int *__restrict__ a, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = i;
 }
 
 inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
-// the conditional list build (each kernel returns at once unless flag word 1 is set)
+constexpr int PPA_BUILD_LAUNCHES = 9;        // kernels of one list build
+constexpr int PPA_LAUNCHES_PER_ITER = 2 + PPA_BUILD_LAUNCHES;   // direct launches of one step
+
+// the list build (each kernel returns at once unless a build is requested)
 void enqueue_build(const PpaArgs &a, cudaStream_t st, int *bsum)
 {
     const int nbs = nblk(a.ncell, 1024);
     k_ppa_bin<<<nblk(a.M, 256), 256, 0, st>>>(a);
     k_scan1<<<nbs, 1024, 0, st>>>(a.count, a.start, bsum, a.ncell, a.flags);
     k_scan2<<<nbs, 1024, 0, st>>>(a.start, bsum, a.ncell, nbs, a.flags);
-    k_scatter<<<nblk(a.M, 256), 256, 0, st>>>(a.cellid, a.rank, a.start, a.list, a.M, a.flags, a.rec, a.recs);
-    k_cellsort<<<nblk(a.ncell, 256), 256, 0, st>>>(a.start, a.list, a.recs, a.count, a.ncell, a.flags);
+    k_ppa_scatter<<<nblk(a.M, 256), 256, 0, st>>>(a);
+    k_ppa_cellsort<<<nblk(a.ncell, 256), 256, 0, st>>>(a);
+    k_ppa_permute<<<nblk(a.M, 256), 256, 0, st>>>(a);
+    k_ppa_flip<<<1, 1, 0, st>>>(a);
+    k_ppa_partners<<<nblk(a.M, 256), 256, 0, st>>>(a);
     k_ppa_nlist<<<nblk(a.M, PPA_BLOCK), PPA_BLOCK, 0, st>>>(a);
+}
+
+void enqueue_drift(const PpaArgs &a, cudaStream_t st, bool mixed)
+{
+    const int nbm = nblk(a.M, PPA_BLOCK);
+    if (mixed) k_ppa_drift_mixed<<<nbm, PPA_BLOCK, 0, st>>>(a);
+    else k_ppa_drift_f64<<<nbm, PPA_BLOCK, 0, st>>>(a);
 }
 
 void enqueue_force(const PpaArgs &a, cudaStream_t st, bool mixed, double half)
@@ -419,9 +576,7 @@ void enqueue_force(const PpaArgs &a, cudaStream_t st, bool mixed, double half)
 
 void enqueue_step(const PpaArgs &a, cudaStream_t st, int *bsum, bool mixed)
 {
-    const int nbm = nblk(a.M, PPA_BLOCK);
-    if (mixed) k_ppa_drift_mixed<<<nbm, PPA_BLOCK, 0, st>>>(a);
-    else k_ppa_drift_f64<<<nbm, PPA_BLOCK, 0, st>>>(a);
+    enqueue_drift(a, st, mixed);
     enqueue_build(a, st, bsum);
     enqueue_force(a, st, mixed, 0.5);
 }
@@ -441,10 +596,8 @@ bool capture_steps(const PpaArgs &a, cudaStream_t s1, cudaStream_t s2, int *bsum
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
     bool ok = cudaStreamBeginCaptureToGraph(s1, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
               cudaSuccess;
-    const int nbm = nblk(a.M, PPA_BLOCK);
     for (int i = 0; ok && i < PPA_GRAPH_ITERS; ++i) {
-        if (mixed) k_ppa_drift_mixed<<<nbm, PPA_BLOCK, 0, s1>>>(a);
-        else k_ppa_drift_f64<<<nbm, PPA_BLOCK, 0, s1>>>(a);
+        enqueue_drift(a, s1, mixed);
         cudaGraphConditionalHandle h;
         ok = cudaGraphConditionalHandleCreate(&h, g, 0, 0) == cudaSuccess;
         if (!ok) break;
@@ -511,7 +664,7 @@ kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *pp, double
     const MeltDev &md = c->sim.melt[melt];
     const double rl = PPA_RC + pp->skin;
     const int nc = (int)std::floor(md.L / rl);
-    if (nc < 3 || nc > CODE_MASK + 1) return KG_ERR_INVALID_ARG;   // 27 distinct stencil cells; packed codes
+    if (nc < 3 || nc > 1024) return KG_ERR_INVALID_ARG;     // 27 distinct stencil cells; bounded grid
     const bool mixed = pp->precision == KG_MIXED;
     const double k = pp->k_fene > 0.0 ? pp->k_fene : kg_kn(12.0, c->p.R0, c->p.l0);
     const int M = md.M, N = md.N, n_ch = md.n_ch;
@@ -547,20 +700,30 @@ kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *pp, double
         bufs.push_back(p);
         return p;
     };
-    a.x = (double *)get(sizeof(double) * m3);
+    a.x0 = (double *)get(sizeof(double) * m3);
+    a.x1 = (double *)get(sizeof(double) * m3);
     if (mixed) {
-        a.v32 = (float *)get(sizeof(float) * m3);
-        a.F32 = (float *)get(sizeof(float) * m3);
+        a.u0 = (float *)get(sizeof(float) * m3);
+        a.u1 = (float *)get(sizeof(float) * m3);
+        a.G0 = (float *)get(sizeof(float) * m3);
+        a.G1 = (float *)get(sizeof(float) * m3);
     } else {
-        a.v = (double *)get(sizeof(double) * m3);
-        a.F = (double *)get(sizeof(double) * m3);
+        a.v0 = (double *)get(sizeof(double) * m3);
+        a.v1 = (double *)get(sizeof(double) * m3);
+        a.F0 = (double *)get(sizeof(double) * m3);
+        a.F1 = (double *)get(sizeof(double) * m3);
         a.xb = (double *)get(sizeof(double) * m3);
     }
-    a.dl = (float4 *)get(sizeof(float4) * M);
+    a.slot0 = (int *)get(sizeof(int) * M);
+    a.slot1 = (int *)get(sizeof(int) * M);
     a.rec = (float4 *)get(sizeof(float4) * M);
-    a.recs = (float4 *)get(sizeof(float4) * M);
     a.pg = (float4 *)get(sizeof(float4) * M);
-    a.cellid = (int *)get(sizeof(int) * M);
+    a.dl = (float4 *)get(sizeof(float4) * M);
+    a.off = (float4 *)get(sizeof(float4) * M);
+    if (mixed) a.bvec = (float4 *)get(sizeof(float4) * M);
+    a.bp = (int2 *)get(sizeof(int2) * M);
+    a.pos_of = (int *)get(sizeof(int) * M);
+    a.cellof = (int *)get(sizeof(int) * M);
     a.rank = (int *)get(sizeof(int) * M);
     a.count = (int *)get(sizeof(int) * ((size_t)a.ncell + 1));
     a.start = (int *)get(sizeof(int) * ((size_t)a.ncell + 1));
@@ -569,6 +732,7 @@ kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *pp, double
     a.nn = (int *)get(sizeof(int) * M);
     a.flags = (unsigned *)get(sizeof(unsigned) * 4);
     int *bsum = (int *)get(sizeof(int) * (size_t)nbs);
+    double *d_xs = (double *)get(sizeof(double) * m3);
     double *d_lpp = (double *)get(sizeof(double) * n_ch);
     unsigned long long *d_fmax = (unsigned long long *)get(sizeof(unsigned long long));
     cudaStream_t gs = nullptr, gs2 = nullptr;
@@ -585,14 +749,15 @@ kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *pp, double
         if (!p) return done(KG_ERR_OOM);
 
     cudaStream_t st = c->stream;
-    kg::to_slots(c, melt, c->x, a.x, 3);               // (3, M) slot order, unwrapped
+    kg::to_slots(c, melt, c->x, a.x0, 3);              // (3, M) slot order, unwrapped; buffer 0
+    k_ppa_iota<<<nblk(M, 256), 256, 0, st>>>(a.slot0, M);
     static const unsigned one = 1u;
     if (cudaMemcpyAsync(a.flags + 1, &one, sizeof(unsigned), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return done(KG_ERR_CUDA);
-    // the first list and force, from rest (v = 0, no kick)
+    // the first build (into cell order) and force, from rest (v = 0, no kick)
     enqueue_build(a, st, bsum);
     enqueue_force(a, st, mixed, 0.0);
-    c->launches += 7;
+    c->launches += 2 + PPA_BUILD_LAUNCHES;
     long long left = pp->n_iter, graph_steps = 0;
     if (left >= 2 * PPA_GRAPH_ITERS && cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) == cudaSuccess &&
         cudaStreamCreateWithFlags(&gs2, cudaStreamNonBlocking) == cudaSuccess &&
@@ -602,8 +767,9 @@ kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *pp, double
     }
     c->launches += 3 * graph_steps + PPA_LAUNCHES_PER_ITER * left;   // + the graphs' builds, below
     for (; left > 0; --left) enqueue_step(a, st, bsum, mixed);
-    k_ppa_lengths<<<nblk(n_ch, 256), 256, 0, st>>>(a, d_lpp, d_fmax);
-    ++c->launches;
+    k_ppa_unpermute<<<nblk(M, 256), 256, 0, st>>>(a, d_xs, d_fmax);
+    k_ppa_lengths<<<nblk(32LL * n_ch, 256), 256, 0, st>>>(d_xs, M, N, d_lpp);
+    c->launches += 2;
     if (cudaGetLastError() != cudaSuccess) return done(KG_ERR_CUDA);
 
     std::vector<double> h_lpp((size_t)n_ch);
@@ -613,7 +779,7 @@ kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *pp, double
         cudaMemcpyAsync(h_flags, a.flags, sizeof(h_flags), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(&h_fmax, d_fmax, sizeof(h_fmax), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return done(KG_ERR_CUDA);
-    if (x_out && cudaMemcpyAsync(x_out, a.x, sizeof(double) * m3, cudaMemcpyDefault, st) != cudaSuccess)
+    if (x_out && cudaMemcpyAsync(x_out, d_xs, sizeof(double) * m3, cudaMemcpyDefault, st) != cudaSuccess)
         return done(KG_ERR_CUDA);
     if (cudaStreamSynchronize(st) != cudaSuccess) return done(KG_ERR_CUDA);
     if (graph_steps) c->launches += PPA_BUILD_LAUNCHES * (long long)h_flags[2];   // upper bound: all builds
