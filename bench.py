@@ -465,6 +465,7 @@ def ppa_secondary(kg, torch, ctx, m):
     return {"workload": f"{m.n_chains} chains x N={m.chain_len}, the equilibrated benchmark melt",
             "steps": PPA_ITERS, "ms_per_step": per, "monomer_steps_per_s": m.M / (per * 1e-3),
             "setup_ms": ms[0], "lpp_mean": res["lpp_mean"], "fmax": res["fmax"], "list_builds": res["builds"],
+            "mean_list_length": res["mean_neighbours"],
             "precision": "mixed",
             "timing": f"CUDA events: (call with {PPA_ITERS} steps - call with 0 steps) / {PPA_ITERS}"}
 

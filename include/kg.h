@@ -378,7 +378,8 @@ kg_status kg_fit_lk(const double *r2n, int N, double l0, int n_lo, int n_hi, dou
  *             minimised positions
  *   res       host or NULL: lpp_mean, the mean over chains (L_pp of Eq. 22);
  *             fmax, the largest net force on a mobile monomer after the last
- *             step (a convergence measure); builds, the neighbour-list builds
+ *             step (a convergence measure); builds, the neighbour-list builds;
+ *             mean_neighbours, the mean length of the last list
  * Device work space per monomer: 24 + 72 (KG_FP64) or 24 + 24 (KG_MIXED)
  * bytes of state, 64 bytes of records and 133 ints; plus the cell grid.
  * Synchronises.  A bond reaching R0 returns KG_ERR_BOND_OVERSTRETCH, a
@@ -397,6 +398,7 @@ typedef struct {
     double lpp_mean;          /* mean primitive-path length over chains                   */
     double fmax;              /* largest net force on a mobile monomer after the last step */
     long long builds;         /* neighbour-list builds, the first included                */
+    double mean_neighbours;   /* mean length of the last interchain list                  */
 } kg_ppa_result;
 
 kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *p, double *lpp, double *x_out,

@@ -72,7 +72,8 @@ class kg_ppa_params(C.Structure):
 
 
 class kg_ppa_result(C.Structure):
-    _fields_ = [("lpp_mean", C.c_double), ("fmax", C.c_double), ("builds", C.c_longlong)]
+    _fields_ = [("lpp_mean", C.c_double), ("fmax", C.c_double), ("builds", C.c_longlong),
+                ("mean_neighbours", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

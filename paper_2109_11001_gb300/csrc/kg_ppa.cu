@@ -490,12 +490,9 @@ __global__ void __launch_bounds__(PPA_BLOCK) k_ppa_force_mixed(PpaArgs a, float 
 
 // ---- results in slot order ----
 
-// positions back to slot order; the largest net force on a mobile monomer
-__global__ void __launch_bounds__(256) k_ppa_unpermute(PpaArgs a, double *__restrict__ xs,
-                                                      unsigned long long *__restrict__ fmax_bits)
+// one monomer back to slot order; the bits of its net force (0 at a chain end)
+__device__ __forceinline__ unsigned long long unpermute_one(const PpaArgs &a, int s, double *__restrict__ xs)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.M) return;
     const int cb = cur_buf(a);
     const double *x = cb ? a.x1 : a.x0;
     const size_t M = a.M;
@@ -510,7 +507,32 @@ __global__ void __launch_bounds__(256) k_ppa_unpermute(PpaArgs a, double *__rest
         f2 += f * f;
     }
     const int i = s % a.N;
-    if (i > 0 && i < a.N - 1) atomicMax(fmax_bits, (unsigned long long)__double_as_longlong(sqrt(f2)));
+    return (i > 0 && i < a.N - 1) ? (unsigned long long)__double_as_longlong(sqrt(f2)) : 0ull;
+}
+
+// positions back to slot order; the largest net force on a mobile monomer
+// (a warp maximum, then one atomic per warp) and the sum of the list lengths
+__global__ void __launch_bounds__(256) k_ppa_unpermute(PpaArgs a, double *__restrict__ xs,
+                                                      unsigned long long *__restrict__ fmax_bits,
+                                                      unsigned long long *__restrict__ nn_sum)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long fb = 0ull;                      // bits of a non-negative double order like it
+    unsigned long long nb = 0ull;
+    if (s < a.M) {
+        fb = unpermute_one(a, s, xs);
+        nb = (unsigned long long)a.nn[s];              // list lengths, storage order (any order sums)
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_down_sync(0xffffffffu, fb, o);
+        fb = t > fb ? t : fb;
+        nb += __shfl_down_sync(0xffffffffu, nb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (fb) atomicMax(fmax_bits, fb);
+        atomicAdd(nn_sum, nb);
+    }
 }
 
 // contour length of every chain from slot-order positions: one warp per
@@ -734,7 +756,7 @@ kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *pp, double
     int *bsum = (int *)get(sizeof(int) * (size_t)nbs);
     double *d_xs = (double *)get(sizeof(double) * m3);
     double *d_lpp = (double *)get(sizeof(double) * n_ch);
-    unsigned long long *d_fmax = (unsigned long long *)get(sizeof(unsigned long long));
+    unsigned long long *d_fmax = (unsigned long long *)get(2 * sizeof(unsigned long long));   // max |F|, sum nn
     cudaStream_t gs = nullptr, gs2 = nullptr;
     cudaGraphExec_t gexec = nullptr;
     auto done = [&](kg_status r) {
@@ -767,17 +789,17 @@ kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *pp, double
     }
     c->launches += 3 * graph_steps + PPA_LAUNCHES_PER_ITER * left;   // + the graphs' builds, below
     for (; left > 0; --left) enqueue_step(a, st, bsum, mixed);
-    k_ppa_unpermute<<<nblk(M, 256), 256, 0, st>>>(a, d_xs, d_fmax);
+    k_ppa_unpermute<<<nblk(M, 256), 256, 0, st>>>(a, d_xs, d_fmax, d_fmax + 1);
     k_ppa_lengths<<<nblk(32LL * n_ch, 256), 256, 0, st>>>(d_xs, M, N, d_lpp);
     c->launches += 2;
     if (cudaGetLastError() != cudaSuccess) return done(KG_ERR_CUDA);
 
     std::vector<double> h_lpp((size_t)n_ch);
     unsigned h_flags[4] = {0, 0, 0, 0};
-    unsigned long long h_fmax = 0;
+    unsigned long long h_fmax[2] = {0, 0};
     if (cudaMemcpyAsync(h_lpp.data(), d_lpp, sizeof(double) * n_ch, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(h_flags, a.flags, sizeof(h_flags), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(&h_fmax, d_fmax, sizeof(h_fmax), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        cudaMemcpyAsync(h_fmax, d_fmax, sizeof(h_fmax), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return done(KG_ERR_CUDA);
     if (x_out && cudaMemcpyAsync(x_out, d_xs, sizeof(double) * m3, cudaMemcpyDefault, st) != cudaSuccess)
         return done(KG_ERR_CUDA);
@@ -793,8 +815,9 @@ kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *pp, double
         double sum = 0.0;
         for (double v : h_lpp) sum += v;               // chain order
         res->lpp_mean = sum / (double)n_ch;
-        std::memcpy(&res->fmax, &h_fmax, sizeof(double));
+        std::memcpy(&res->fmax, &h_fmax[0], sizeof(double));
         res->builds = (long long)h_flags[2];
+        res->mean_neighbours = (double)h_fmax[1] / (double)M;
     }
     return done(KG_OK);
 }

@@ -181,6 +181,8 @@ def test_full_size_properties(kg):
         x = np.zeros_like(m.x)
         lpp, res = kg.kg_primitive_path(ctx, 0, m.n_chains, 200, 0.005, 1.0, 0.3, K12, x)
         mean, fmax = res["lpp_mean"], res["fmax"]
+        # interchain neighbours within 2^(1/6) + 0.3 at rho = 0.85: a few to a few tens
+        assert 2.0 < res["mean_neighbours"] < 64.0 and res["builds"] >= 1
     finally:
         kg.kg_destroy(ctx)
     N = m.chain_len
