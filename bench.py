@@ -642,6 +642,32 @@ def ncu_case(args):
     print(json.dumps({"ncu_case": args.workload, "M": m.M, "db_accepted": st.accepted}))
 
 
+def ppa_case(args):
+    """A run for primitive-path captures: the 1.6M-monomer melt relaxed
+    through the prelude walk, then kg_primitive_path (mixed) of 0 and
+    --ppa-case steps, the second between cudaProfilerStart/Stop (for ncu
+    --profile-from-start off); below 50 steps every launch is direct."""
+    import torch
+
+    import paper_2109_11001_gb300 as kg
+    m = make_melt(args.workload, 0)
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=kg.KG_MIXED, seed=11,
+                       fene_qmin=FENE_QMIN, skin=0.5)
+    ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+    stages, n_prelude = prelude_stages(kg)
+    kg.kg_set_potential_schedule(ctx, stages)
+    kg.kg_load_config(ctx, 0, m.x, m.v)
+    kg.kg_step(ctx, n_prelude)
+    kg.kg_primitive_path(ctx, 0, m.n_chains, 0, dt=0.005, gamma=1.0, skin=0.3)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    lpp, res = kg.kg_primitive_path(ctx, 0, m.n_chains, args.ppa_case, dt=0.005, gamma=1.0, skin=0.3)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    kg.kg_destroy(ctx)
+    print(json.dumps({"ppa_case": args.workload, "M": m.M, "steps": args.ppa_case, **res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -658,9 +684,13 @@ def main():
                     help="bracket the direct-launch window (same bench steps, no graphs) with cudaProfilerStart/Stop, for ncu --profile-from-start off")
     ap.add_argument("--ncu-case", action="store_true")
     ap.add_argument("--ncu-db-budget", type=float, default=1e-3, help="DB attempts per monomer in the --ncu-case sweep")
+    ap.add_argument("--ppa-case", type=int, default=0, help="primitive-path steps of a capture run (0: off)")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args)
+        return
+    if args.ppa_case:
+        ppa_case(args)
         return
     if args.warmup < 3:
         args.warmup = 3
