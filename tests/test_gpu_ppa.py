@@ -195,3 +195,24 @@ def test_full_size_properties(kg):
     assert np.allclose(lpp, P.path_lengths(x, N), rtol=1e-12)
     assert mean == pytest.approx(lpp.mean(), rel=1e-12)
     assert np.isfinite(fmax)
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED])
+def test_second_melt_of_a_batch(kg, melt, precision):
+    """The analysis of melt 1 in a two-melt context reads that melt's slots
+    only: bit-identical to the same melt in a context of its own."""
+    import torch
+    other = KI.hooked_pair()
+    p = kg.make_params([(other.n_chains, other.chain_len, other.box, other.kappa),
+                        (melt.n_chains, melt.chain_len, melt.box, melt.kappa)], precision=0, seed=3)
+    ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+    try:
+        kg.kg_load_config(ctx, 0, other.x, other.v)
+        kg.kg_load_config(ctx, 1, melt.x, melt.v)
+        x = np.zeros_like(melt.x)
+        lpp, _ = kg.kg_primitive_path(ctx, 1, melt.n_chains, 60, 0.005, 1.0, 0.3, K12, x, precision)
+    finally:
+        kg.kg_destroy(ctx)
+    x1, lpp1, _, _ = _ppa(kg, melt, 60, 0.005, 1.0, precision=precision)
+    assert np.array_equal(x, x1)
+    assert np.array_equal(lpp, lpp1)
