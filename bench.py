@@ -60,8 +60,8 @@ def bytes_per_monomer(precision, skin):
 # hash of kg_md.cu they were taken on (reported as null once the source changes)
 # (ncu --set full of the 1.6M-monomer case, skin 0.5: 302.0 MB read + 91.0 MB
 # written per launch; profiles/md_step_and_nlist_1.6M_mixed.md)
-NCU_TRAFFIC = {"bytes_per_monomer": (301.975040e6 + 91.038976e6) / 1.6e6,
-               "kg_md_sha1": "19781cb9468660a8fa6aa0dc8b66e8cdb0ee1e0c"}
+NCU_TRAFFIC = {"bytes_per_monomer": (263.346944e6 + 58.959104e6) / 1.6e6,
+               "kg_md_sha1": "006f7e8f5bcc2671741c554b534fdd9e05e53dac"}
 
 WORKLOADS = {
     "cfg5": dict(index=5, desc="1000 chains x N=1600 (1.6M monomers), kappa=3.5, rho=0.85"),

@@ -325,6 +325,7 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->d_sim = (SimDev *)A(sizeof(SimDev));
     c->d_stage = (StageDev *)A(sizeof(StageDev));
     c->x = (double *)A(3 * Mp * sizeof(double));
+    if (c->precision == KG_MIXED) c->xb64 = (double *)A(3 * Mp * sizeof(double));
     c->u = A(3 * Mp * ureal);
     c->pid = (int *)A(Mp * sizeof(int));
     c->recb = (float4 *)A(Mp * sizeof(float4));
@@ -408,7 +409,7 @@ void kg_destroy(kg_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    void *bufs[] = {c->d_sim, c->d_stage, c->x, c->u, c->pid, c->recb, c->recs, c->shtab, c->dlt[0], c->dlt[1],
+    void *bufs[] = {c->d_sim, c->d_stage, c->x, c->xb64, c->u, c->pid, c->recb, c->recs, c->shtab, c->dlt[0], c->dlt[1],
                     c->pg[0], c->pg[1], c->pos64[0],
                     c->pos64[1], c->xb, c->cellid, c->rank, c->ccount, c->cstart, c->clist, c->bsum, c->nl,
                     c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->dbrec, c->dbmark, c->chain_ver, c->dbround, c->att_ver, c->att,
@@ -443,6 +444,12 @@ kg_status kg_load_config(kg_ctx *c, int melt, const double *x, const double *v, 
     const size_t Mm = md.M, Mp = c->Mp;
     for (int d = 0; d < 3; ++d)
         KG_TRY(cudaMemcpyAsync(c->x + d * Mp + md.off, x + d * Mm, Mm * sizeof(double), cudaMemcpyDefault, c->stream));
+    if (c->precision == KG_MIXED) {   // build position = the loaded one, no displacement since
+        for (int d = 0; d < 3; ++d)
+            KG_TRY(cudaMemcpyAsync(c->xb64 + d * Mp + md.off, c->x + d * Mp + md.off, Mm * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, c->stream));
+        KG_TRY(cudaMemsetAsync(c->dlt[c->cur] + md.off, 0, Mm * sizeof(float4), c->stream));
+    }
     for (int d = 0; d < 3; ++d) {
         if (c->precision == KG_MIXED) {
             float *u = (float *)c->u + d * Mp + md.off;
@@ -556,6 +563,7 @@ kg_status kg_step(kg_ctx *c, long long n_steps)
         if (c->stage_left > 0) c->stage_left -= chunk;
         n_steps -= chunk;
     }
+    kg::md_materialize(c);                      // current binary64 positions for every other call
     KG_TRY(cudaGetLastError());
     unsigned *h = pinned_flags();
     return read_flags(c, h);

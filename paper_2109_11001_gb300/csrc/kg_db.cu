@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(COMMIT_THREADS) k_db_commit_next(
 // a product and one of a sum), counters cleared
 __global__ void __launch_bounds__(256) k_db_finish(const SimDev *__restrict__ Sp, double *__restrict__ x,
                                                   const int *__restrict__ slot_of, int *__restrict__ img,
-                                                  double *__restrict__ msd_ref)
+                                                  double *__restrict__ msd_ref, double *__restrict__ xb64)
 {
     const SimDev &S = *Sp;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(256) k_db_finish(const SimDev *__restrict__ Sp
         if (k) {
             x[d * Mp + j] = __dadd_rn(x[d * Mp + j], __dmul_rn(L, (double)k));
             if (msd_ref) msd_ref[d * Mp + j] = __dadd_rn(msd_ref[d * Mp + j], __dmul_rn(L, (double)k));
+            if (xb64) xb64[d * Mp + j] = __dadd_rn(xb64[d * Mp + j], __dmul_rn(L, (double)k));
         }
         img[d * Mp + j] = 0;
     }
@@ -249,7 +250,7 @@ void db_finish(kg_ctx *c, long long *host_stats)
     cudaStream_t st = c->stream;
     c->launches += 1;
     // box shifts into the positions; chain partners follow the new maps
-    k_db_finish<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->slot_of, c->img, c->msd_ref);
+    k_db_finish<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->slot_of, c->img, c->msd_ref, c->xb64);
     bonded_partners(c);
     cudaMemcpyAsync(host_stats, c->db_stats, sizeof(long long) * 4 * c->sim.n_melts, cudaMemcpyDeviceToHost, st);
 }

@@ -33,7 +33,10 @@ struct kg_ctx {
     kg_status latched = KG_ERR_STATE;
 
     // state
-    double *x = nullptr;         // [3][Mp]
+    double *x = nullptr;         // [3][Mp]; mixed: current only outside kg_step (see xb64)
+    double *xb64 = nullptr;      // mixed: binary64 positions at the last Verlet build [3][Mp];
+                                 // the current position is xb64 + dlt[cur] (folded at every
+                                 // build and at the end of every kg_step call)
     void *u = nullptr;           // [3][Mp] float or double
     int *pid = nullptr;          // particle id of the monomer at each compute index
     int *slot_of = nullptr;      // compute index -> chain-major slot
@@ -150,6 +153,7 @@ void forces_eval(kg_ctx *c, int melt, long long step, double *F_dev, double *par
 void prof_collect(kg_ctx *c);                // fold recorded event pairs into the totals
 void bonded_partners(kg_ctx *c);             // bp from slot_of / comp_of
 void md_sort(kg_ctx *c);                     // re-sort the state into the last cell order
+void md_materialize(kg_ctx *c);              // mixed: x <- xb64 + dlt[cur]
 void to_slots(kg_ctx *c, int melt, const double *in_comp, double *out_dev, int dims);
 void u_to_slots(kg_ctx *c, int melt, double *out_dev);
 void pid_to_slots(kg_ctx *c, int melt, int *out_dev);

@@ -282,19 +282,20 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
 }
 
 // ---------------------------------------------------------------------------
-// fused MD step: forces at x_n, then u <- u + dt F_n, x <- x + dt u
+// fused MD step: forces at x_n, then u <- u + dt F_n, x <- x + dt u, the
+// position step taken in binary32 into the displacement since the build
+// (the binary64 position is folded from it at builds and between calls)
 // F_n = F_c - gamma u + sqrt(2 gamma T / dt) g_n,  g_n = Philox normals.
 // ---------------------------------------------------------------------------
 // TPM threads per monomer (1 or 2, adjacent lanes): the lanes split the
 // Verlet list (entries k = sub, sub + TPM, ...); with two, lane 0 adds the
 // bonded terms and lane 1 draws the noise while the other works, the forces
-// are combined with a shuffle, and lane 0 writes the binary32 state while
-// lane 1 writes the binary64 positions.
+// are combined with a shuffle, and lane 0 writes the state.
 // (256, 6): at most 40 registers, 75% occupancy; the few spills cost less than
 // the latency the extra warps hide (143 against 153 us at 1.6M monomers)
 template <int TPM>
 __global__ void __launch_bounds__(256, 6) k_step_mixed(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
-                                                   const float4 *__restrict__ shtab, double *__restrict__ x,
+                                                   const float4 *__restrict__ shtab,
                                                    float *__restrict__ u, const float4 *__restrict__ recb,
                                                    const float4 *__restrict__ dcur, float4 *__restrict__ dnext,
                                                    const float4 *__restrict__ pcur, float4 *__restrict__ pnext,
@@ -343,11 +344,6 @@ __global__ void __launch_bounds__(256, 6) k_step_mixed(const SimDev *__restrict_
         v.x += st.dtf * (F.x - st.gammaf * v.x + st.ampf * gn.x);
         v.y += st.dtf * (F.y - st.gammaf * v.y + st.ampf * gn.y);
         v.z += st.dtf * (F.z - st.gammaf * v.z + st.ampf * gn.z);
-        if (sub == TPM - 1) {
-            x[s] += st.dt * (double)v.x;
-            x[Mp + s] += st.dt * (double)v.y;
-            x[2 * Mp + s] += st.dt * (double)v.z;
-        }
         if (sub == 0) {
             u[s] = v.x; u[Mp + s] = v.y; u[2 * Mp + s] = v.z;
             float4 d = dc;
@@ -410,7 +406,8 @@ __global__ void __launch_bounds__(256) k_step_f64(const SimDev *__restrict__ Sp,
 // ---------------------------------------------------------------------------
 // build records (offset from the Verlet-cell corner + cell coordinates),
 // gather buffers reset, Verlet-grid cell + rank within it
-__global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, const double *__restrict__ x,
+__global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, double *__restrict__ x,
+                                               double *__restrict__ xb64,
                                                float4 *__restrict__ recb, float4 *__restrict__ dcur,
                                                float4 *__restrict__ pgcur, double4_32a *__restrict__ pcur,
                                                double4_32a *__restrict__ xb, int *__restrict__ cellid,
@@ -423,17 +420,33 @@ __global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, c
     if (s >= S.M) return;
     const MeltDev &md = S.melt[melt_of(S, slot_of[s])];
     const int Mp = S.Mp;
-    if (!isfinite(x[s] + x[Mp + s] + x[2 * Mp + s])) {   // never bin a non-finite position
+    double xs[3];
+    if (xb64) {                        // mixed: the build position plus the displacement since
+        const float4 e = dcur[s];
+        xs[0] = xb64[s] + (double)e.x;
+        xs[1] = xb64[Mp + s] + (double)e.y;
+        xs[2] = xb64[2 * Mp + s] + (double)e.z;
+    } else {
+        xs[0] = x[s];
+        xs[1] = x[Mp + s];
+        xs[2] = x[2 * Mp + s];
+    }
+    if (!isfinite(xs[0] + xs[1] + xs[2])) {              // never bin a non-finite position
         atomicOr((unsigned *)flags, ERR_NONFINITE);
         return;
     }
+    if (xb64) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xb64[d * Mp + s] = xs[d];
+            x[d * Mp + s] = xs[d];     // the band check of the list build reads x
+        }
+    }
     float off[3];
     int cell[3];
-    double xs[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const double xd = x[d * Mp + s];
-        xs[d] = xd;
+        const double xd = xs[d];
         const double w = xd - md.L * floor(xd * md.invL);
         int c = (int)(w * md.invh);
         c = c < 0 ? 0 : (c >= md.nc ? md.nc - 1 : c);
@@ -836,6 +849,7 @@ void bonded_partners(kg_ctx *c)
 // The list then refers to the old order, so a rebuild is requested.
 void md_sort(kg_ctx *c)
 {
+    md_materialize(c);
     const int Mp = c->Mp;
     double *sx = c->scratch;
     int *spid = (int *)(c->scratch + 6 * (size_t)Mp);
@@ -855,10 +869,34 @@ void md_sort(kg_ctx *c)
         k_sort_finish<double><<<nblk(c->M, 256), 256, 0, c->stream>>>(c->M, Mp, c->x, (double *)c->u, c->pid,
                                                                      c->slot_of, c->comp_of, sx, su, spid, sslot);
     }
+    if (c->precision == KG_MIXED) {    // sorted current positions become the build positions
+        cudaMemcpyAsync(c->xb64, c->x, 3 * (size_t)Mp * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemsetAsync(c->dlt[c->cur], 0, (size_t)Mp * sizeof(float4), c->stream);
+    }
     msd_permute(c, c->clist);
     bonded_partners(c);
     static const unsigned one = 1u;
     cudaMemcpyAsync(c->flags + 1, &one, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream);
+}
+
+// mixed: current binary64 positions x = xb64 + dlt[cur] (the same sum as the
+// build's fold, so a later build finds the same values)
+__global__ void __launch_bounds__(256) k_materialize(double *__restrict__ x, const double *__restrict__ xb64,
+                                                    const float4 *__restrict__ d, int M, int Mp)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    const float4 e = d[s];
+    x[s] = xb64[s] + (double)e.x;
+    x[Mp + s] = xb64[Mp + s] + (double)e.y;
+    x[2 * Mp + s] = xb64[2 * Mp + s] + (double)e.z;
+}
+
+void md_materialize(kg_ctx *c)
+{
+    if (c->precision != KG_MIXED) return;
+    ++c->launches;
+    k_materialize<<<nblk(c->M, 256), 256, 0, c->stream>>>(c->x, c->xb64, c->dlt[c->cur], c->M, c->Mp);
 }
 
 void to_slots(kg_ctx *c, int melt, const double *in_comp, double *out_dev, int dims)
@@ -915,7 +953,8 @@ void rebuild_md(kg_ctx *c)
 static void launch_rebuild(kg_ctx *c, cudaStream_t st)
 {
     const bool mixed = c->precision == KG_MIXED;
-    k_bin_md<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, c->recb, mixed ? c->dlt[c->cur] : nullptr,
+    k_bin_md<<<nblk(c->M, 256), 256, 0, st>>>(c->d_sim, c->x, mixed ? c->xb64 : nullptr, c->recb,
+                                              mixed ? c->dlt[c->cur] : nullptr,
                                               mixed ? c->pg[c->cur] : nullptr, mixed ? nullptr : c->pos64[c->cur],
                                               c->xb, c->cellid, c->rank, c->ccount, c->slot_of, c->flags);
     const int nb = nblk(c->ncell_md, 1024);
@@ -934,10 +973,10 @@ static void launch_step_kernel(kg_ctx *c, cudaStream_t st, int cur)
     const int nb = nblk(c->M, c->block);
     if (c->precision == KG_MIXED && c->tpm == 2)
         k_step_mixed<2><<<nblk(2LL * c->M, c->block), c->block, 0, st>>>(
-            c->d_sim, c->d_stage, c->shtab, c->x, (float *)c->u, c->recb, c->dlt[cur], c->dlt[cur ^ 1], c->pg[cur],
+            c->d_sim, c->d_stage, c->shtab, (float *)c->u, c->recb, c->dlt[cur], c->dlt[cur ^ 1], c->pg[cur],
             c->pg[cur ^ 1], c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
     else if (c->precision == KG_MIXED)
-        k_step_mixed<1><<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->shtab, c->x, (float *)c->u, c->recb,
+        k_step_mixed<1><<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->shtab, (float *)c->u, c->recb,
                                                  c->dlt[cur], c->dlt[cur ^ 1], c->pg[cur], c->pg[cur ^ 1], c->nl,
                                                  c->nn, c->slot_of, c->bp, c->flags, c->d_step);
     else
