@@ -59,7 +59,9 @@ typedef enum {
 enum {
     KG_FP64 = 0,   /* every force term in binary64                                     */
     KG_MIXED = 1   /* pair/bond/angle forces in binary32 from binary64 positions;
-                      positions, DB energy changes and energy sums stay binary64      */
+                      between Verlet builds a step advances a binary32 displacement,
+                      folded into the binary64 positions at each build and at the end
+                      of each kg_step; DB energy changes and energy sums binary64      */
 };
 
 /* kg_params.flags */
