@@ -97,7 +97,11 @@ typedef struct {
                                  r >= 2 R0 is still an error)                          */
     unsigned long long seed;  /* key of every counter-based random draw                */
     int sort_interval;        /* MD steps between re-sorts of the per-monomer arrays into
-                                 cell order (<= 0: 200); results do not depend on it    */
+                                 cell order (<= 0: 200), tested at the start of each
+                                 kg_step call and each 10-step graph; KG_FP64 results do
+                                 not depend on it; in KG_MIXED a re-sort forces a Verlet
+                                 build, whose timing moves positions at the binary32
+                                 rounding level (~1e-7 sigma)                           */
     int block_size;           /* threads per block of the fused step kernel: 64, 128
                                  or 256 (<= 0: 128); results do not depend on it        */
     int precision;            /* KG_FP64 or KG_MIXED                                    */

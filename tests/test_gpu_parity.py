@@ -416,6 +416,40 @@ def test_long_run_across_resorts_and_sweeps(kg):
     assert np.array_equal(offs, oo) and np.array_equal(nbr, on)
 
 
+@pytest.mark.parametrize("sort_interval,tol", [(10 ** 6, 0.0), (50, 1e-6)])
+def test_mixed_positions_do_not_depend_on_call_splitting(kg, sort_interval, tol):
+    """Mixed mode folds its binary32 displacement into the binary64 positions
+    at every Verlet build and at the end of every kg_step call: splitting the
+    same steps into more calls, with the positions read in between, gives the
+    same trajectory bit for bit, DB sweeps included.  With re-sorts the host
+    tests the sort interval at call and graph boundaries, so a split run
+    re-sorts a few steps later (step 257 instead of 250 here); the re-sort
+    forces a Verlet build, which restarts the binary32 displacement, so the
+    two runs differ at the binary32 rounding level of the positions."""
+    m = KI.random_walk_melt(30, 40, 0.85, 1.0, 91)
+    plan = [(120, 200), (120, 200), (60, 0)]          # (MD steps, DB attempts after them)
+
+    def run(split):
+        with context(kg, [m], 1, schedule=[kg.stage(2.0, 10 ** 9, 0.002)], sort_interval=sort_interval) as ctx:
+            x = np.zeros_like(m.x)
+            for n, k in plan:
+                parts = [7, 13, n - 20] if split else [n]
+                for q in parts:
+                    kg.kg_step(ctx, q)
+                    if split:
+                        kg.kg_get_config(ctx, 0, x)
+                if k:
+                    kg.kg_db_sweep_k(ctx, [k])
+            pid = np.zeros(m.M, dtype=np.int32)
+            kg.kg_get_config(ctx, 0, x, None, pid)
+            return x, pid
+
+    xa, pa = run(False)
+    xb, pb = run(True)
+    assert np.array_equal(pa, pb)
+    assert np.abs(xa - xb).max() <= tol
+
+
 RELAX = [(2.0, 300, 0.0005), (2.0, 300, 0.001), (4.0, 300, 0.0015), (6.5, 300, 0.0025), (9.0, 300, 0.004),
          (12.0, 300, 0.005)]
 
