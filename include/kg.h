@@ -386,8 +386,9 @@ kg_status kg_fit_lk(const double *r2n, int N, double l0, int n_lo, int n_hi, dou
  *             fmax, the largest net force on a mobile monomer after the last
  *             step (a convergence measure); builds, the neighbour-list builds;
  *             mean_neighbours, the mean length of the last list
- * Device work space per monomer: 24 + 72 (KG_FP64) or 24 + 24 (KG_MIXED)
- * bytes of state, 64 bytes of records and 133 ints; plus the cell grid.
+ * Device work space per monomer: 192 (KG_FP64) or 120 (KG_MIXED) bytes of
+ * double-buffered state and output, 64 (KG_FP64) or 80 (KG_MIXED) bytes of
+ * binary32 records and 137 ints (128 of them the list); plus the cell grid.
  * Synchronises.  A bond reaching R0 returns KG_ERR_BOND_OVERSTRETCH, a
  * non-finite position KG_ERR_NONFINITE, more than 128 listed neighbours or
  * 1024 monomers in one cell KG_ERR_CAPACITY; none of them latches the context. */
