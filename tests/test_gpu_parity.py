@@ -236,6 +236,32 @@ def test_errors_and_recovery(kg):
     assert ei.value.status == kg.KG_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_degenerate_calls(kg, precision):
+    """Zero steps and zero attempts change nothing; a lone chain has no
+    partner chain, so every double-bridging draw is empty (as in the oracle),
+    and MD on it still runs."""
+    m = KI.make(1)
+    with context(kg, [m], precision, schedule=[kg.stage(2.0, 100, 0.002)]) as ctx:
+        kg.kg_step(ctx, 0)
+        st = kg.kg_db_sweep_k(ctx, [0])
+        x = np.zeros_like(m.x)
+        pid = np.zeros(m.M, dtype=np.int32)
+        kg.kg_get_config(ctx, 0, x, None, pid)
+    assert (st.attempted, st.accepted) == (0, 0)
+    assert np.array_equal(x, m.x) and np.array_equal(pid, np.arange(m.M))
+    one = KI.random_walk_melt(1, 40, 0.01, 1.0, 5)
+    with context(kg, [one], precision, schedule=[kg.stage(2.0, 100, 0.002)]) as ctx:
+        st = kg.kg_db_sweep_k(ctx, [500])
+        kg.kg_step(ctx, 20)
+        x = np.zeros_like(one.x)
+        kg.kg_get_config(ctx, 0, x)
+    a, e, acc = O.db_sweep(oparams(one, 2.0, dt=0.002), one.x.copy(), one.v.copy(),
+                           np.arange(one.M, dtype=np.int32), 0, 500)
+    assert (st.attempted, st.empty, st.accepted) == (a, e, acc) == (500, 500, 0)
+    assert np.all(np.isfinite(x)) and not np.array_equal(x, one.x)
+
+
 def test_runs_are_deterministic(kg):
     m = KI.make(1)
     outs = []
