@@ -216,3 +216,33 @@ def test_second_melt_of_a_batch(kg, melt, precision):
     x1, lpp1, _, _ = _ppa(kg, melt, 60, 0.005, 1.0, precision=precision)
     assert np.array_equal(x, x1)
     assert np.array_equal(lpp, lpp1)
+
+
+def test_entanglement_length_of_a_relaxed_melt(kg):
+    """End to end: generated melt (250 x 200, kappa = 3.5), the soft-to-WCA
+    walk and 1000 WCA steps on the GPU, primitive paths (10,000 steps), Eq. 22
+    with Eq. 12's Kuhn length.  The paper's fit for equilibrated melts,
+    N_e = 71.2 - 61.3 tanh(kappa / 1.631) = 11.55 at kappa = 3.5, bounds the
+    result loosely: this melt is not DBH-equilibrated and its chains are
+    short (about 17 N_e).  The 1.6M-monomer benchmark melt gives 11.3."""
+    import math
+
+    import torch
+    from oracle import schedule as SC
+    kappa = 3.5
+    m = KI.random_walk_melt(250, 200, 0.85, kappa, 77)
+    sched = [kg.stage(n, k, dt) for n, k, dt in RELAX] + [kg.stage(12.0, 10 ** 9, 0.01)]
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=1, seed=7, fene_qmin=0.01)
+    ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+    try:
+        kg.kg_set_potential_schedule(ctx, sched)
+        kg.kg_load_config(ctx, 0, m.x, m.v)
+        kg.kg_step(ctx, sum(k for _, k, _ in RELAX) + 1000)
+        lpp, res = kg.kg_primitive_path(ctx, 0, m.n_chains, 10000, 0.005, 1.0, 0.3)
+    finally:
+        kg.kg_destroy(ctx)
+    lk = SC.lk_over_l0(kappa) * P.L0
+    n_ek, n_e = kg.kg_entanglement_length(res["lpp_mean"], m.chain_len, lk)
+    paper = 71.2 - 61.3 * math.tanh(kappa / 1.631)
+    print("L_pp/L", res["lpp_mean"] / ((m.chain_len - 1) * P.L0), "N_eK", n_ek, "N_e", n_e, "paper", paper)
+    assert 0.6 * paper < n_e < 1.4 * paper
