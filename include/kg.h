@@ -178,11 +178,16 @@ kg_status kg_db_sweep(kg_ctx *c, double attempts_per_monomer, kg_db_stats *stats
 /* As kg_db_sweep with an explicit attempt count per melt (n_melts entries). */
 kg_status kg_db_sweep_k(kg_ctx *c, const long long *attempts, kg_db_stats *stats);
 
+/* Longest chain whose <R^2(n)> can be computed (kg_observables, kg_r2n_noalloc):
+ * one chain's 3N binary64 positions must fit one block's shared memory. */
+#define KG_R2N_MAX_CHAIN_LEN 9685
+
 /* Observables of melt `melt` at the current integer time step (synchronises):
  * energies and virial from the conservative forces, kinetic energy from
  * v_n = u + dt/2 F_n, <R^2(n)> for n = 0..N-1 into r2n (N doubles; NULL to
- * skip), and bond-length (on [0, R0)) / cos(theta) (on [-1, 1]) histograms of
- * n_bins bins (NULL to skip). */
+ * skip; KG_ERR_INVALID_ARG when N > KG_R2N_MAX_CHAIN_LEN), and bond-length
+ * (on [0, R0)) / cos(theta) (on [-1, 1]) histograms of n_bins bins (NULL to
+ * skip). */
 kg_status kg_observables(kg_ctx *c, int melt, kg_obs *out, double *r2n,
                          double *bond_hist, double *cos_hist, int n_bins);
 
@@ -420,7 +425,8 @@ kg_status kg_primitive_path(kg_ctx *c, int melt, const kg_ppa_params *p, double 
 kg_status kg_entanglement_length(double lpp_mean, int chain_len, double l0, double l_k, double *n_ek,
                                  double *n_e);
 
-/* Largest n_chains * chain_len that kg_r2n_noalloc accepts. */
+/* Largest n_chains * chain_len that kg_r2n_noalloc accepts (its chains may be
+ * at most KG_R2N_MAX_CHAIN_LEN long). */
 #define KG_NOALLOC_MAX_MONOMERS 2097152
 
 /* <R^2(n)> for n = 0..N-1 of chains whose positions already sit in device
@@ -432,16 +438,18 @@ kg_status kg_entanglement_length(double lpp_mean, int chain_len, double l0, doub
  *
  *   x        device pointer, (3, stride) binary64 SoA, chain-major slots
  *            c*N + i in [0, n_chains*chain_len); unwrapped positions
- *   stride   distance in doubles between the x, y and z rows (>= M)
+ *   stride   distance in doubles between the x, y and z rows (>= M; any
+ *            64-bit value, indices are formed in 64-bit arithmetic)
  *   out      device pointer to chain_len doubles; out[0] = 0
  *   stream   cudaStream_t to enqueue on (NULL: the default stream)
  *
  * Its per-chain partial sums go to one file-scope device array of
  * KG_NOALLOC_MAX_MONOMERS doubles (16 MiB), which every GPU that loads the
  * library holds until the process exits.  Sizes beyond that maximum (or
- * chains longer than fit one block's shared memory, N > 9685) return
- * KG_ERR_INVALID_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first call
+ * chains longer than KG_R2N_MAX_CHAIN_LEN) return KG_ERR_INVALID_ARG.  Every
+ * call looks up the array's device address (cudaGetSymbolAddress) on the
+ * current device, so call it with the device that holds x current; the first
+ * call on a device loads the library's kernels there, so make that first call
  * before any stream capture.  Calls share the array and overwrite it
  * completely, so calls that overlap on the GPU (different streams, or devices
  * sharing nothing but this host code) race: serialise them.  No cudaMalloc,

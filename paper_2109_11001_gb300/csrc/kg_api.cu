@@ -1113,7 +1113,8 @@ kg_status kg_observables(kg_ctx *c, int melt, kg_obs *out, double *r2n, double *
         out->step = c->step;
     }
     if (r2n) {
-        kg::r2n_eval(c, melt, c->scratch);
+        if (md.N > KG_R2N_MAX_CHAIN_LEN) return KG_ERR_INVALID_ARG;
+        if (!kg::r2n_eval(c, melt, c->scratch)) return KG_ERR_CUDA;
         KG_TRY(cudaMemcpyAsync(r2n, c->scratch, sizeof(double) * md.N, cudaMemcpyDefault, c->stream));
     }
     if (bond_hist || cos_hist) {

@@ -182,7 +182,9 @@ bool mlp_grad(kg_ctx *c, const double *f_dev, const double *t_dev, long long n, 
 bool mlp_train(kg_ctx *c, int iters, int batch, double lr, double *loss_dev);
 
 // kg_obs.cu
-void r2n_eval(kg_ctx *c, int melt, double *out_dev);
+constexpr int R2N_SMEM_MAX = 24 * KG_R2N_MAX_CHAIN_LEN;     // bytes of k_r2n_chain's positions
+bool r2n_smem_ready(int N);                                   // opt-in shared memory; false if N is too long
+bool r2n_eval(kg_ctx *c, int melt, double *out_dev);          // false: launch failed or N too long
 void hist_eval(kg_ctx *c, int melt, int nbins, int *out_dev);
 bool msd_reset(kg_ctx *c, int melt);                          // allocates the reference on first use
 int msd_blocks(const kg_ctx *c, int melt);

@@ -3,23 +3,23 @@
 // repeated calls give identical results.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "kg_host.h"
 
 namespace kg {
 
 // One block per chain: the chain's unwrapped positions in shared memory;
 // thread t accumulates sum_i |x_{i+n} - x_i|^2 for n = t+1, t+1+blockDim, ...
-__global__ void __launch_bounds__(256) k_r2n_chain(const double *__restrict__ x, int Mp, int off, int N,
+// The row stride Mp is 64-bit: a caller's rows may sit 2^30 or more doubles
+// apart, and every index into x is formed in 64-bit arithmetic.
+__global__ void __launch_bounds__(256) k_r2n_chain(const double *__restrict__ x, long long Mp, int off, int N,
                                                   double *__restrict__ out /* [n_ch][N] */,
                                                   const int *__restrict__ comp_of /* NULL: slot order */)
 {
     extern __shared__ double pos[];          // 3N
     const int c = blockIdx.x;
-    const int base = off + c * N;
+    const long long base = (long long)off + (long long)c * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const int j = comp_of ? comp_of[base + i] : base + i;
+        const long long j = comp_of ? (long long)comp_of[base + i] : base + i;
         pos[i] = x[j];
         pos[N + i] = x[Mp + j];
         pos[2 * N + i] = x[2 * Mp + j];
@@ -76,13 +76,26 @@ __global__ void __launch_bounds__(256) k_hist(const double *__restrict__ x, int 
     }
 }
 
-void r2n_eval(kg_ctx *c, int melt, double *out_dev)
+// Dynamic shared memory of k_r2n_chain for chains of N monomers (3N doubles);
+// above 48 KiB the kernel's opt-in limit is raised first.
+bool r2n_smem_ready(int N)
+{
+    const size_t smem = sizeof(double) * 3 * (size_t)N;
+    if (N < 1 || smem > (size_t)R2N_SMEM_MAX) return false;
+    if (smem <= 48 * 1024) return true;
+    return cudaFuncSetAttribute(k_r2n_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+}
+
+bool r2n_eval(kg_ctx *c, int melt, double *out_dev)
 {
     const MeltDev &md = c->sim.melt[melt];
+    if (!r2n_smem_ready(md.N)) return false;
     c->launches += 2;
-    k_r2n_chain<<<md.n_ch, 256, sizeof(double) * 3 * md.N, c->stream>>>(c->x, c->Mp, md.off, md.N, c->r2tmp,
-                                                                          c->comp_of);
+    k_r2n_chain<<<md.n_ch, 256, sizeof(double) * 3 * md.N, c->stream>>>(c->x, (long long)c->Mp, md.off, md.N,
+                                                                          c->r2tmp, c->comp_of);
+    if (cudaGetLastError() != cudaSuccess) return false;
     k_r2n_reduce<<<(md.N + 255) / 256, 256, 0, c->stream>>>(c->r2tmp, md.n_ch, md.N, out_dev);
+    return cudaGetLastError() == cudaSuccess;
 }
 
 void hist_eval(kg_ctx *c, int melt, int nbins, int *out_dev)
@@ -306,25 +319,20 @@ static __device__ __align__(256) double g_r2n_scratch[KG_NOALLOC_MAX_MONOMERS];
 
 namespace {
 
-// Device address of g_r2n_scratch, looked up once per device (with that device
-// current): in host code the symbol names a host-side stand-in, not device
-// memory, so it must never be handed to a kernel directly.
-double *scratch_address(int device, kg_status *st)
+// Device address of g_r2n_scratch on the current device.  In host code the
+// symbol names a host-side stand-in, not device memory, so it must never be
+// handed to a kernel directly.  The address is looked up on every call (the
+// lookup allocates nothing), so it stays right after the device's primary
+// context has been reset and the module reloaded.
+double *scratch_address(kg_status *st)
 {
-    static std::mutex mu;
-    static double *addr[256] = {};
-    static bool done[256] = {};
-    if (device < 0 || device >= 256) { *st = KG_ERR_INVALID_ARG; return nullptr; }
-    std::lock_guard<std::mutex> lock(mu);
-    if (!done[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, kg::g_r2n_scratch);
-        if (e != cudaSuccess) { *st = KG_ERR_CUDA; return nullptr; }
-        addr[device] = (double *)p;
-        done[device] = true;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, kg::g_r2n_scratch) != cudaSuccess) {
+        *st = KG_ERR_CUDA;
+        return nullptr;
     }
     *st = KG_OK;
-    return addr[device];
+    return (double *)p;
 }
 
 }  // namespace
@@ -335,19 +343,14 @@ extern "C" kg_status kg_r2n_noalloc(const double *x, long long stride, int n_cha
     if (!x || !out || n_chains < 1 || chain_len < 2 || stride < (long long)n_chains * chain_len)
         return KG_ERR_INVALID_ARG;
     if ((long long)n_chains * chain_len > KG_NOALLOC_MAX_MONOMERS) return KG_ERR_INVALID_ARG;
-    if ((size_t)3 * chain_len * sizeof(double) > 227 * 1024) return KG_ERR_INVALID_ARG;
-    if (stride >= (1LL << 31)) return KG_ERR_INVALID_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return KG_ERR_CUDA;
+    if (chain_len > KG_R2N_MAX_CHAIN_LEN) return KG_ERR_INVALID_ARG;
     kg_status st;
-    double *scratch = scratch_address(dev, &st);
+    double *scratch = scratch_address(&st);
     if (!scratch) return st;
     const cudaStream_t s = (cudaStream_t)stream;
     const size_t smem = sizeof(double) * 3 * chain_len;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kg::k_r2n_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return KG_ERR_CUDA;
-    kg::k_r2n_chain<<<n_chains, 256, smem, s>>>(x, (int)stride, 0, chain_len, scratch, nullptr);
+    if (!kg::r2n_smem_ready(chain_len)) return KG_ERR_CUDA;
+    kg::k_r2n_chain<<<n_chains, 256, smem, s>>>(x, stride, 0, chain_len, scratch, nullptr);
     kg::k_r2n_reduce<<<(chain_len + 255) / 256, 256, 0, s>>>(scratch, n_chains, chain_len, out);
     return cudaGetLastError() == cudaSuccess ? KG_OK : KG_ERR_CUDA;
 }
