@@ -43,23 +43,30 @@ _T0 = time.time()
 def log(msg):
     """Timestamped progress on stderr (the JSON line alone goes to stdout)."""
     print(f"[bench {time.time() - _T0:8.2f}s] {msg}", file=sys.stderr, flush=True)
-# algorithmic HBM bytes per monomer per launch of the fused step kernel (the
-# per-monomer model of the hot-path scope table): x r+w 48, v r+w 24 (f32) /
-# 48 (f64), the binary32 gather mirror written and read once 32 (f64: a
-# binary64 mirror, 64), and the Verlet list, 4 bytes per neighbour with
-# rho (4 pi / 3)(r_c + skin)^3 neighbours at the skin in use.
+# Algorithmic HBM bytes per monomer per step of the fused step kernel at the
+# reference skin 0.3 (10.3 Verlet-list neighbours of 4 bytes):
+#   positions read + written in binary64   48
+#   velocities read + written              24 (binary32) / 48 (binary64)
+#   binary32 float4 gather mirror w + r    32
+#   Verlet list                            41
+# = 145 B (mixed) and 170 B (binary64).  Gathers of neighbour positions are
+# L1/L2 hits in cell order and count 0.  The roofline fraction is taken on
+# this fixed model; the same model with the list at the skin in use is
+# reported beside it.
+ALGO_BYTES = {"mixed": 145.0, "fp64": 170.0}
+
+
 def nb_mean(skin):
     return 0.85 * 4.0 / 3.0 * np.pi * (2 ** (1 / 6) + skin) ** 3
 
 
-def bytes_per_monomer(precision, skin):
-    return (48 + 24 + 32 if precision == "mixed" else 48 + 48 + 64) + 4 * nb_mean(skin)
+def bytes_per_monomer_at_skin(precision, skin):
+    return (48 + 24 + 32 if precision == "mixed" else 48 + 48 + 32) + 4 * nb_mean(skin)
 
 
-# DRAM bytes per monomer of the mixed step kernel from an ncu capture, and the
-# hash of kg_md.cu they were taken on (reported as null once the source changes)
-# (ncu --set full of the 1.6M-monomer case, skin 0.5: 302.0 MB read + 91.0 MB
-# written per launch; profiles/md_step_and_nlist_1.6M_mixed.md)
+# DRAM bytes per monomer of the mixed step kernel from one ncu capture of the
+# 1.6M-monomer case at skin 0.5, and the hash of kg_md.cu it was taken on
+# (reported as null once the source changes)
 NCU_TRAFFIC = {"bytes_per_monomer": (263.346944e6 + 58.959104e6) / 1.6e6,
                "kg_md_sha1": "006f7e8f5bcc2671741c554b534fdd9e05e53dac"}
 
@@ -194,26 +201,97 @@ def allsum(world, v):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(m, md_steps=1, db_attempts=16):
-    """Time the oracle on the full melt: md_steps MD steps and db_attempts DB
-    attempts; returns (seconds per MD step, seconds per DB attempt, sample)."""
+def cpu_model():
+    """The host CPU's model name and its core count."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        import platform
+        name = platform.processor() or platform.machine()
+    return name, os.cpu_count() or 1
+
+
+def _oracle_job(job):
+    """One oracle sample in a worker process: md_steps MD steps and db_attempts
+    DB attempts from the state stored at job["path"]; returns the seconds of
+    each part (the processes run concurrently, one per host core)."""
     import oracle as O
-    O.build()
-    p = O.params(m.n_chains, m.chain_len, m.box, m.kappa, n_exp=2.0, dt=0.001, seed=3)
-    x, u = m.x.copy(), m.v.copy()
+    d = np.load(job["path"])
+    x, u = np.ascontiguousarray(d["x"]), np.ascontiguousarray(d["u"])
+    p = O.params(job["n_chains"], job["chain_len"], job["box"], job["kappa"], n_exp=job["n_exp"], dt=job["dt"],
+                 seed=3 + job["worker"], fene_qmin=job["fene_qmin"])
     t0 = time.perf_counter()
-    O.run(p, x, u, 0, md_steps)
-    t_md = (time.perf_counter() - t0) / md_steps
-    pid = np.arange(m.M, dtype=np.int32)
-    t0 = time.perf_counter()
-    O.db_sweep(p, x, u, pid, 0, db_attempts)
-    t_db = (time.perf_counter() - t0) / max(db_attempts, 1)
-    return t_md, t_db
+    O.run(p, x, u, 0, job["md_steps"])
+    t1 = time.perf_counter()
+    pid = np.arange(x.shape[1], dtype=np.int32)
+    O.db_sweep(p, x, u, pid, job["worker"], job["db_attempts"])
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / max(job["db_attempts"], 1)
+
+
+class OraclePool:
+    """The oracle timed as it stands on the host's cores: one process per core,
+    each advancing its own replica of the same state (independent melts are
+    the method's natural parallel unit), started with the spawn method."""
+
+    def __init__(self, m, x, u, n_exp, dt, fene_qmin, workers=None):
+        import multiprocessing as mp
+        import tempfile
+        self.m = m
+        self.workers = workers or (os.cpu_count() or 1)
+        fd, self.path = tempfile.mkstemp(suffix=".npz", prefix="kg_oracle_state_")
+        os.close(fd)
+        np.savez(self.path, x=x, u=u)
+        self.base = dict(path=self.path, n_chains=m.n_chains, chain_len=m.chain_len, box=m.box, kappa=m.kappa,
+                         n_exp=n_exp, dt=dt, fene_qmin=fene_qmin)
+        self.pool = mp.get_context("spawn").Pool(self.workers) if self.workers > 1 else None
+
+    def sample(self, md_steps, db_attempts, concurrent=True):
+        """(seconds per MD step, seconds per DB attempt, processes) averaged over
+        the processes that ran at the same time."""
+        n = self.workers if concurrent else 1
+        jobs = [dict(self.base, md_steps=md_steps, db_attempts=db_attempts, worker=w) for w in range(n)]
+        res = self.pool.map(_oracle_job, jobs, chunksize=1) if (self.pool and n > 1) else [_oracle_job(jobs[0])]
+        t_md = sum(r[0] for r in res) / len(res) / md_steps
+        t_db = sum(r[1] for r in res) / len(res)
+        return t_md, t_db, n
+
+    def close(self):
+        if self.pool:
+            self.pool.close()
+            self.pool.join()
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
 
 
 def step_units(m):
     """(monomer-steps, DB attempts) of one bench step at the paper's rate."""
     return m.M * MD_PER_STEP, m.M * MD_PER_STEP * DT * 1e-3
+
+
+def per_step_rate(m, t_md, t_db, procs):
+    """Monomer-steps/s of `procs` concurrent oracle replicas, each doing one
+    bench step (MD_PER_STEP MD steps + the DB attempts of the paper's rate)."""
+    units, att = step_units(m)
+    return procs * units / (MD_PER_STEP * t_md + att * t_db)
+
+
+# The reference arm cannot relax the benchmark melt (the oracle needs ~1 s per
+# MD step of 1.6M monomers and thousands of soft steps): it times the oracle
+# on the generated melt in the soft first stage, n = 2 at dt = 0.001, where a
+# step from the generated state is well defined (WCA at dt = 0.01 overstretches
+# bonds of the unrelaxed melt within two steps).  The oracle's cost per step
+# does not depend on n (every pair term is one pow) or on dt.
+REF_STAGE = dict(n_exp=2.0, dt=0.001, fene_qmin=0.0)
 
 
 def run_reference(args, world, rank):
@@ -222,22 +300,30 @@ def run_reference(args, world, rank):
     m = make_melt(args.workload, 0)
     units, att = step_units(m)
     att_sample = max(1, int(round(att / MD_PER_STEP)))
-    for _ in range(args.warmup):
-        oracle_sample(m, 1, att_sample)
-    t = []
-    for _ in range(args.steps):
-        t_md, t_db = oracle_sample(m, 1, att_sample)
-        t.append(t_md + t_db * att_sample)
+    pool = OraclePool(m, m.x, m.v, **REF_STAGE)
+    try:
+        for _ in range(args.warmup):
+            pool.sample(1, att_sample)
+        t = []
+        for _ in range(args.steps):
+            t_md, t_db, procs = pool.sample(1, att_sample)
+            # one bench step of work spread over the concurrent replicas
+            t.append((MD_PER_STEP * t_md + att * t_db) / procs)
+    finally:
+        pool.close()
     total = sum(t)
-    value = m.M * args.steps / total
+    value = m.M * MD_PER_STEP * args.steps / total
+    name, ncpu = cpu_model()
+    sample = (f"per step: {procs} concurrent processes (one per host core), each 1 MD step of all {m.M} monomers "
+              f"+ {att_sample} DB attempts from the generated melt at n = 2, dt = 0.001, scaled to 50 MD steps + "
+              f"{att:g} attempts; host CPU {name}")
     line = {"metric": "monomer-timesteps/s", "value": value, "unit": "monomer-steps/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]['desc']}",
-                       "sample": f"per step: 1 MD step of all {m.M} monomers + {att_sample} DB attempts"},
-            "cpu_baseline": {"value": value, "unit": "monomer-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} x (1 MD step + {att_sample} DB attempts) on the full melt"},
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]['desc']}", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "monomer-steps/s", "cores": procs, "kind": "oracle",
+                             "sample": sample, "cpu_model": name, "host_cores": ncpu},
             "e2e": {"value": value, "unit": "monomer-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -297,6 +383,9 @@ def run_ours(args, world, rank, local):
     for i in range(args.warmup):
         st = bench_step()
         log(f"warmup step {i}: attempted {st.attempted} accepted {st.accepted} reevaluated {st.reevaluated}")
+    # the state the timed region starts from: the CPU baseline times the oracle on it
+    x_t0, u_t0 = np.zeros_like(m.x), np.zeros_like(m.v)
+    kg.kg_get_config(ctx, 0, x_t0, u_t0)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -356,18 +445,20 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    db_acc = db_att = db_re = 0
+    db_acc = db_att = db_re = db_empty = 0
     d0.record(stream)
     for _ in range(DB_SWEEPS):
         st = kg.kg_db_sweep(ctx, DB_BUDGET)
         db_acc += st.accepted
         db_att += st.attempted
         db_re += st.reevaluated
+        db_empty += st.empty
     d1.record(stream)
     torch.cuda.synchronize()
     t_sweeps = allmax(world, d0.elapsed_time(d1) / 1e3)
     db_acc_all = allsum(world, float(db_acc))
     db_att_all = allsum(world, float(db_att))
+    db_empty_all = allsum(world, float(db_empty))
     log(f"db budget: {DB_SWEEPS} sweeps, {db_att} attempts, {db_acc} accepted, {db_re} re-evaluated, {t_sweeps * 1e3:.1f} ms")
 
     # secondary: the same step in plain binary64 on this GPU (single rank), and
@@ -383,18 +474,29 @@ def run_ours(args, world, rank, local):
         return
     avg_ms = step_ms / max(n_launch, 1)
     run_skin = tuning["skin"] if tuning else args.skin
-    bpm = bytes_per_monomer(args.precision, run_skin)
+    bpm = ALGO_BYTES[args.precision]
     achieved = bpm * m.M / (avg_ms * 1e-3) / 1e9
+    bpm_skin = bytes_per_monomer_at_skin(args.precision, run_skin)
     peak, src = peaks()
     traffic = None
     if (NCU_TRAFFIC["bytes_per_monomer"] and NCU_TRAFFIC["kg_md_sha1"] == src_sha1()
             and args.precision == "mixed" and abs(run_skin - 0.5) < 1e-12):
         traffic = NCU_TRAFFIC["bytes_per_monomer"] * m.M
+    # the oracle on the same state and stage as the timed region (n = 12,
+    # dt = DT): one host core alone, then one process per host core at once
     log("oracle sample")
-    t_md, t_db = oracle_sample(m, 2, 8)
-    log(f"oracle: {t_md:.3f} s per MD step, {t_db:.4f} s per DB attempt")
-    att_step = m.M * MD_PER_STEP * DT * 1e-3
-    cpu_val = m.M * MD_PER_STEP / (MD_PER_STEP * t_md + att_step * t_db)
+    pool = OraclePool(m, x_t0, u_t0, n_exp=12.0, dt=DT, fene_qmin=FENE_QMIN)
+    try:
+        t1_md, t1_db, _ = pool.sample(2, 8, concurrent=False)
+        tn_md, tn_db, procs = pool.sample(1, 8, concurrent=True)
+    finally:
+        pool.close()
+    cpu_one = per_step_rate(m, t1_md, t1_db, 1)
+    cpu_all = per_step_rate(m, tn_md, tn_db, procs)
+    cpu_name, ncpu = cpu_model()
+    log(f"oracle: one core {t1_md:.3f} s per MD step, {t1_db:.4f} s per DB attempt; "
+        f"{procs} processes {tn_md:.3f} s per MD step each")
+    db_admissible = db_att_all - db_empty_all
     line = {
         "metric": "monomer-timesteps/s", "value": units / t_max, "unit": "monomer-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -408,19 +510,31 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs larger than L2 (working set > 129 MB), no flush"},
         "accepted_db_moves_per_s": db_acc_all / t_sweeps,
         "db": {"attempts_per_sweep": int(round(DB_BUDGET * m.M)), "sweeps": DB_SWEEPS * world,
-               "attempted": int(db_att_all), "accepted": int(db_acc_all), "reevaluated": int(db_re),
+               "attempted": int(db_att_all), "empty": int(db_att_all - db_admissible),
+               "admissible": int(db_admissible), "accepted": int(db_acc_all), "reevaluated": int(db_re),
+               "acceptance_per_attempt": db_acc_all / max(db_att_all, 1),
+               "acceptance_per_admissible": db_acc_all / max(db_admissible, 1),
                "accepted_per_s": db_acc_all / t_sweeps, "attempts_per_s": db_att_all / t_sweeps,
                "ms_per_sweep": t_sweeps * 1e3 / DB_SWEEPS, "proposal": "uniform",
+               "stage": f"n = 12, dt = {DT}",
                "timing": "CUDA events around back-to-back sweeps, stats read after each"},
         "accepted_db_moves_per_s_in_step": acc_all / t_max,
         "db_attempts_per_step": att / args.steps,
         "roofline": {"bound": "hbm", "kernel": "k_step_" + args.precision, "achieved": achieved, "peak": peak,
                      "timing": "CUDA events around each step-kernel launch, bench steps after the timed region",
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": src, "bytes_per_monomer": bpm, "avg_launch_ms": avg_ms},
-        "cpu_baseline": {"value": cpu_val, "unit": "monomer-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"2 MD steps + 8 DB attempts of the full {m.M}-monomer melt, "
-                                   f"scaled to one bench step"},
+                     "peak_source": src, "bytes_per_monomer": bpm,
+                     "bytes_model": "145 B (mixed) / 170 B (binary64) per monomer-step: list at skin 0.3",
+                     "bytes_per_monomer_at_skin": bpm_skin,
+                     "frac_at_skin": bpm_skin * m.M / (avg_ms * 1e-3) / 1e9 / peak, "skin": run_skin,
+                     "avg_launch_ms": avg_ms},
+        "cpu_baseline": {"value": cpu_all, "unit": "monomer-steps/s", "cores": procs, "kind": "oracle",
+                         "sample": f"one process per host core, each 1 MD step + 8 DB attempts of the full "
+                                   f"{m.M}-monomer melt from the timed region's starting state at n = 12, "
+                                   f"dt = {DT}, scaled to one bench step",
+                         "single_core": {"value": cpu_one, "cores": 1,
+                                         "sample": "2 MD steps + 8 DB attempts, one process"},
+                         "cpu_model": cpu_name, "host_cores": ncpu},
         "e2e": {"value": units / t_e2e, "unit": "monomer-steps/s",
                 "h2d_bytes_per_step": int(hx.numel() * 8 + hv.numel() * 8),
                 "d2h_bytes_per_step": int(hout.numel() * 8)},
@@ -620,9 +734,9 @@ def _init_weights(seed=0):
 
 def ncu_case(args):
     """A short run for kernel captures: the 1.6M-monomer melt, no prelude,
-    seven soft (n = 2, dt = 0.001) steps with a re-sort into cell order after
-    the third, so few launches precede the captured ones while the inputs stay
-    larger than L2."""
+    seven steps at dt = 0.001 of the stage --ncu-n (default n = 2), with a
+    re-sort into cell order after the third, so few launches precede the
+    captured ones while the inputs stay larger than L2."""
     import torch
 
     import paper_2109_11001_gb300 as kg
@@ -631,7 +745,7 @@ def ncu_case(args):
     p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=prec, seed=11,
                        fene_qmin=FENE_QMIN, sort_interval=3, skin=args.skin)
     ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
-    kg.kg_set_potential_schedule(ctx, [kg.stage(2.0, 10 ** 9, 0.001)])
+    kg.kg_set_potential_schedule(ctx, [kg.stage(args.ncu_n, 10 ** 9, 0.001)])
     kg.kg_load_config(ctx, 0, m.x, m.v)
     kg.kg_step(ctx, 3)          # builds the list; the 4th step first re-sorts into cell order
     kg.kg_set_counters(ctx, 3, 0)
@@ -684,6 +798,7 @@ def main():
                     help="bracket the direct-launch window (same bench steps, no graphs) with cudaProfilerStart/Stop, for ncu --profile-from-start off")
     ap.add_argument("--ncu-case", action="store_true")
     ap.add_argument("--ncu-db-budget", type=float, default=1e-3, help="DB attempts per monomer in the --ncu-case sweep")
+    ap.add_argument("--ncu-n", type=float, default=2.0, help="stage exponent n of the --ncu-case steps")
     ap.add_argument("--ppa-case", type=int, default=0, help="primitive-path steps of a capture run (0: off)")
     args = ap.parse_args()
     if args.ncu_case:

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libkg.so")
-SOURCES = ["kg_api.cu", "kg_md.cu", "kg_db.cu", "kg_obs.cu", "kg_learned.cu", "kg_mlp.cu", "kg_ppa.cu"]
+SOURCES = ["kg_api.cu", "kg_md.cu", "kg_step.cu", "kg_db.cu", "kg_obs.cu", "kg_learned.cu", "kg_mlp.cu", "kg_ppa.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

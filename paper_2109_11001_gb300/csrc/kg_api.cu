@@ -107,6 +107,7 @@ kg_status upload_stage(kg_ctx *c, const kg_stage &s)
 {
     c->stage = make_stage(c->p, s);
     KG_TRY(cudaMemcpyAsync(c->d_stage, &c->stage, sizeof(StageDev), cudaMemcpyHostToDevice, c->stream));
+    kg::graphs_reset(c);                     // the step kernel takes the stage by value
     return KG_OK;
 }
 

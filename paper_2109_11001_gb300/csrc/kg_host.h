@@ -154,6 +154,10 @@ void prof_collect(kg_ctx *c);                // fold recorded event pairs into t
 void bonded_partners(kg_ctx *c);             // bp from slot_of / comp_of
 void md_sort(kg_ctx *c);                     // re-sort the state into the last cell order
 void md_materialize(kg_ctx *c);              // mixed: x <- xb64 + dlt[cur]
+void graphs_reset(kg_ctx *c);                // drop captured step graphs (their arguments changed)
+
+// kg_step.cu
+void step_mixed_launch(kg_ctx *c, cudaStream_t st, int cur);   // the mixed path's fused step kernel
 void to_slots(kg_ctx *c, int melt, const double *in_comp, double *out_dev, int dims);
 void u_to_slots(kg_ctx *c, int melt, double *out_dev);
 void pid_to_slots(kg_ctx *c, int melt, int *out_dev);

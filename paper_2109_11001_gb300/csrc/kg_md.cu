@@ -282,82 +282,10 @@ __device__ __forceinline__ typename G::T3 force_on(const G &g, const SimDev &S, 
 }
 
 // ---------------------------------------------------------------------------
-// fused MD step: forces at x_n, then u <- u + dt F_n, x <- x + dt u, the
-// position step taken in binary32 into the displacement since the build
-// (the binary64 position is folded from it at builds and between calls)
-// F_n = F_c - gamma u + sqrt(2 gamma T / dt) g_n,  g_n = Philox normals.
+// fused MD step, binary64 path: forces at x_n, then u <- u + dt F_n,
+// x <- x + dt u with F_n = F_c - gamma u + sqrt(2 gamma T / dt) g_n,
+// g_n = Philox normals (the mixed path's step kernel is in kg_step.cu)
 // ---------------------------------------------------------------------------
-// TPM threads per monomer (1 or 2, adjacent lanes): the lanes split the
-// Verlet list (entries k = sub, sub + TPM, ...); with two, lane 0 adds the
-// bonded terms and lane 1 draws the noise while the other works, the forces
-// are combined with a shuffle, and lane 0 writes the state.
-// (256, 6): at most 40 registers, 75% occupancy; the few spills cost less than
-// the latency the extra warps hide (143 against 153 us at 1.6M monomers)
-template <int TPM>
-__global__ void __launch_bounds__(256, 6) k_step_mixed(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
-                                                   const float4 *__restrict__ shtab,
-                                                   float *__restrict__ u, const float4 *__restrict__ recb,
-                                                   const float4 *__restrict__ dcur, float4 *__restrict__ dnext,
-                                                   const float4 *__restrict__ pcur, float4 *__restrict__ pnext,
-                                                   const unsigned *__restrict__ nl, const int *__restrict__ nn,
-                                                   const int *__restrict__ slot_of, const int4 *__restrict__ bp,
-                                                   unsigned *__restrict__ flags, const long long *__restrict__ stepp)
-{
-    if (flags[0]) return;                  // a latched error stops the run
-    const SimDev &S = *Sp;
-    const StageDev &st = *stp;
-    const long long step = *stepp;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = t / TPM, sub = t % TPM;
-    const bool live = s < S.M;
-    bool rebuild = false;
-    unsigned err = 0;
-    float3 F = make_float3(0.f, 0.f, 0.f), gn = make_float3(0.f, 0.f, 0.f);
-    float4 rb = make_float4(0.f, 0.f, 0.f, 0.f), dc = rb;
-    if (live) {
-        const int slot = __ldg(slot_of + s);
-        const int m = melt_of(S, slot);
-        const MeltDev &md = S.melt[m];
-        GeoMixed g{pcur, shtab};
-        g.melt(md, m);
-        // own record rebuilt from its parts: the same bits the last step wrote to pcur
-        rb = __ldg(recb + s);
-        dc = dcur[s];
-        g.pi = make_float4(rb.x + dc.x, rb.y + dc.y, rb.z + dc.z, rb.w);
-        pair_forces<false>(g, S, st, s, nl, __ldg(nn + s), sub, TPM, F, nullptr);
-        if (sub == 0) bonded_forces<false>(g, st, md, S.rc2f, __ldg(bp + s), F, nullptr, err);
-        if (sub == TPM - 1)
-            gn = gauss3_f(draw(S.seed, m, 0, (unsigned long long)step, (uint32_t)(slot - md.off)));
-    }
-    if (TPM == 2) {                        // every lane takes part: s is shared by lanes 2i, 2i+1
-        F.x += __shfl_xor_sync(0xffffffffu, F.x, 1);
-        F.y += __shfl_xor_sync(0xffffffffu, F.y, 1);
-        F.z += __shfl_xor_sync(0xffffffffu, F.z, 1);
-        const int src = (threadIdx.x & 31) | 1;
-        gn.x = __shfl_sync(0xffffffffu, gn.x, src);
-        gn.y = __shfl_sync(0xffffffffu, gn.y, src);
-        gn.z = __shfl_sync(0xffffffffu, gn.z, src);
-    }
-    if (live) {
-        const int Mp = S.Mp;
-        float3 v = make_float3(u[s], u[Mp + s], u[2 * Mp + s]);
-        v.x += st.dtf * (F.x - st.gammaf * v.x + st.ampf * gn.x);
-        v.y += st.dtf * (F.y - st.gammaf * v.y + st.ampf * gn.y);
-        v.z += st.dtf * (F.z - st.gammaf * v.z + st.ampf * gn.z);
-        if (sub == 0) {
-            u[s] = v.x; u[Mp + s] = v.y; u[2 * Mp + s] = v.z;
-            float4 d = dc;
-            d.x += st.dtf * v.x; d.y += st.dtf * v.y; d.z += st.dtf * v.z;
-            dnext[s] = d;
-            pnext[s] = make_float4(rb.x + d.x, rb.y + d.y, rb.z + d.z, rb.w);
-            rebuild = d.x * d.x + d.y * d.y + d.z * d.z > S.half_skin2f;
-            if (!isfinite(v.x + v.y + v.z)) err |= ERR_NONFINITE;
-        }
-    }
-    if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(flags + 1, 1u);
-    if (err) atomicOr(flags, err);
-}
-
 __global__ void __launch_bounds__(256) k_step_f64(const SimDev *__restrict__ Sp, const StageDev *__restrict__ stp,
                                                  double *__restrict__ x, double *__restrict__ u,
                                                  const double4_32a *__restrict__ pcur, double4_32a *__restrict__ pnext,
@@ -970,18 +898,24 @@ static void launch_rebuild(kg_ctx *c, cudaStream_t st)
 
 static void launch_step_kernel(kg_ctx *c, cudaStream_t st, int cur)
 {
+    if (c->precision == KG_MIXED) {
+        step_mixed_launch(c, st, cur);
+        return;
+    }
     const int nb = nblk(c->M, c->block);
-    if (c->precision == KG_MIXED && c->tpm == 2)
-        k_step_mixed<2><<<nblk(2LL * c->M, c->block), c->block, 0, st>>>(
-            c->d_sim, c->d_stage, c->shtab, (float *)c->u, c->recb, c->dlt[cur], c->dlt[cur ^ 1], c->pg[cur],
-            c->pg[cur ^ 1], c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
-    else if (c->precision == KG_MIXED)
-        k_step_mixed<1><<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->shtab, (float *)c->u, c->recb,
-                                                 c->dlt[cur], c->dlt[cur ^ 1], c->pg[cur], c->pg[cur ^ 1], c->nl,
-                                                 c->nn, c->slot_of, c->bp, c->flags, c->d_step);
-    else
-        k_step_f64<<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->x, (double *)c->u, c->pos64[cur], c->pos64[cur ^ 1],
-                                       c->xb, c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
+    k_step_f64<<<nb, c->block, 0, st>>>(c->d_sim, c->d_stage, c->x, (double *)c->u, c->pos64[cur], c->pos64[cur ^ 1],
+                                        c->xb, c->nl, c->nn, c->slot_of, c->bp, c->flags, c->d_step);
+}
+
+// Captured graphs hold the step kernel's by-value arguments (stage
+// parameters among them): drop them when those change.
+void graphs_reset(kg_ctx *c)
+{
+    for (int k = 0; k < 2; ++k)
+        if (c->gexec[k]) {
+            cudaGraphExecDestroy(c->gexec[k]);
+            c->gexec[k] = nullptr;
+        }
 }
 
 void set_device_step(kg_ctx *c, long long v)

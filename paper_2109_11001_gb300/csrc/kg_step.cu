@@ -1,0 +1,345 @@
+// kg_step.cu -- the fused MD step of the mixed-precision path (binary32 forces,
+// binary64 positions folded from a binary32 displacement at list builds).
+//
+// One step: U_MLJ^n pair forces over the Verlet list (Eqs. 5-6, truncated and
+// shifted at r_c = 2^(1/6)), U_bond^n = U_MLJ^n + FENE bonds (Eq. 10),
+// kappa (1 - cos theta) bending (Eq. 4), Langevin friction and Philox noise,
+// then the leapfrog update u += dt F, x += dt u (velocity Verlet on the state
+// (x_n, u = v_{n-1/2})).
+//
+// Instruction economy is what bounds this kernel (its arithmetic per byte is
+// low, but the per-entry work of the pair loop is issued for every lane of a
+// warp up to the warp's longest list):
+//  * every parameter is a by-value kernel argument (constant bank operands,
+//    no loads, no registers held for them); a captured graph bakes them in,
+//    so graphs are re-captured when the stage changes;
+//  * the pair potential is a template on 4n, so each stage of Xi (Eq. 11)
+//    gets its own straight-line r^-n;
+//  * the pair loop runs to the warp's longest list with per-lane predicates
+//    (no divergent loop exits), ILP list entries in flight;
+//  * the image shift of an entry's stencil code q is read from a 27-entry
+//    shared-memory table of cell offsets (-1, 0, 1)^3 and scaled by the
+//    melt's cell side with one FMA per component.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "kg_host.h"
+
+namespace kg {
+
+struct MeltStep {
+    int off, nc;
+    float h, L, invL, kappa;
+};
+
+struct StepArgs {
+    const float4 *recb;      // build records: offset from the Verlet-cell corner, packed cell coordinates
+    const float4 *dcur;      // displacement since the build (this step)
+    float4 *dnext;           //   ... after this step
+    const float4 *pcur;      // gather records recb + dcur
+    float4 *pnext;           //   ... after this step
+    float *u;                // [3][Mp] velocities v_{n-1/2}
+    const unsigned *nl;      // Verlet list, column-major [maxnb][Mp], entries j | q << IDX_BITS
+    const int *nn;           // list lengths
+    const int *slot_of;      // compute index -> chain-major slot (keys the noise)
+    const int4 *bp;          // compute indices of chain partners s-2, s-1, s+1, s+2 (-1 past an end)
+    unsigned *flags;         // [0] error bits, [1] rebuild request
+    const long long *stepp;  // index of the step being run
+    unsigned long long seed;
+    int M, Mp, n_melts;
+    float rc2, half_skin2;
+    float dt, gamma, amp;    // Langevin: u += dt (F - gamma u + amp g), amp = sqrt(2 gamma T / dt)
+    float c1xn, c2x6, nf;    // fr = (6 c2 r^-6 - n c1 r^-n) / r^2  (U = c1 r^-n - c2 r^-6 + 1)
+    float kf, R0sq, inv_R0sq, qmin, kf_qmin, four_R0sq;   // FENE k_n, R0^2, continuation beyond r*
+    MeltStep melt[MAX_MELTS];
+};
+
+// r^-n from r^2, 1/r^2 and 1/r^6; N4 = 4n (0: any other n, from exp2/log2)
+template <int N4>
+__device__ __forceinline__ float inv_rn(float r2, float ir2, float ir6, float nf)
+{
+    if constexpr (N4 == 0) {
+        return exp2f(-0.5f * nf * log2f(r2));
+    } else if constexpr (N4 == 23) {                 // n = 23/4: r^-6 r^(1/4)
+        return ir6 * sqrtf(sqrtf(sqrtf(r2)));
+    } else if constexpr (N4 == 26) {                 // n = 13/2: r^-6 r^(-1/2)
+        return ir6 * sqrtf(rsqrtf(r2));
+    } else {
+        static_assert(N4 % 4 == 0, "integer n");
+        constexpr int n = N4 / 4;
+        float p;
+        if constexpr (n >= 6) {
+            p = ir6;
+#pragma unroll
+            for (int k = 3; k < n / 2; ++k) p *= ir2;
+        } else {
+            p = ir2;
+#pragma unroll
+            for (int k = 1; k < n / 2; ++k) p *= ir2;
+        }
+        if constexpr (n & 1) p *= rsqrtf(r2);
+        return p;
+    }
+}
+
+// (dU_MLJ^n/dr) / r at r^2 (binary32)
+template <int N4>
+__device__ __forceinline__ float mlj_fr32(const StepArgs &P, float r2)
+{
+    const float ir2 = __fdividef(1.0f, r2);
+    const float ir6 = ir2 * ir2 * ir2;
+    const float rn = inv_rn<N4>(r2, ir2, ir6, P.nf);
+    return (P.c2x6 * ir6 - P.c1xn * rn) * ir2;
+}
+
+__device__ __forceinline__ int melt_index(const StepArgs &P, int slot)
+{
+    int m = 0;
+    while (m + 1 < P.n_melts && slot >= P.melt[m + 1].off) ++m;
+    return m;
+}
+
+// Bond (Eq. 10) and bending (Eq. 4) forces on the monomer whose gather
+// record is pi, from its chain partners bp = (s-2, s-1, s+1, s+2).
+template <int N4>
+__device__ __forceinline__ void bonded32(const StepArgs &P, const MeltStep &md, float4 pi, int4 bp, float3 &F,
+                                         unsigned &err)
+{
+    const bool hm2 = bp.x >= 0, hm1 = bp.y >= 0, hp1 = bp.z >= 0, hp2 = bp.w >= 0;
+    float3 rm2 = make_float3(0.f, 0.f, 0.f), rm1 = rm2, rp1 = rm2, rp2 = rm2;
+    if (hm1) rm1 = rec_rel(pi, __ldg(P.pcur + bp.y), md.nc, md.h, md.L, md.invL);
+    if (hm2) rm2 = rec_rel(pi, __ldg(P.pcur + bp.x), md.nc, md.h, md.L, md.invL);
+    if (hp1) rp1 = rec_rel(pi, __ldg(P.pcur + bp.z), md.nc, md.h, md.L, md.invL);
+    if (hp2) rp2 = rec_rel(pi, __ldg(P.pcur + bp.w), md.nc, md.h, md.L, md.invL);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        if (side == 0 ? hm1 : hp1) {
+            const float3 d = side == 0 ? rm1 : rp1;
+            const float r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+            float q = 1.0f - r2 * P.inv_R0sq, fr;
+            if (P.qmin > 0.0f && q < P.qmin) {          // continuation beyond r* (kg_params.fene_qmin)
+                fr = P.kf_qmin;
+                if (!(r2 < P.four_R0sq)) err |= ERR_OVERSTRETCH;
+            } else {
+                if (!(r2 < P.R0sq)) err |= ERR_OVERSTRETCH;
+                q = fmaxf(q, 1e-6f);                    // finite even when flagged
+                fr = P.kf * __fdividef(1.0f, q);
+            }
+            const float fl = mlj_fr32<N4>(P, r2);
+            fr += r2 < P.rc2 ? fl : 0.0f;
+            F.x += fr * d.x; F.y += fr * d.y; F.z += fr * d.z;
+        }
+    }
+    const float kap = md.kappa;
+    if (kap != 0.0f) {
+        const float3 Bm2 = make_float3(rm1.x - rm2.x, rm1.y - rm2.y, rm1.z - rm2.z);
+        const float3 Bm1 = make_float3(-rm1.x, -rm1.y, -rm1.z), B0 = rp1;
+        const float3 Bp1 = make_float3(rp2.x - rp1.x, rp2.y - rp1.y, rp2.z - rp1.z);
+        if (hm1 && hp1) {                     // vertex s: force kappa (g1 - g2)
+            const float l1 = Bm1.x * Bm1.x + Bm1.y * Bm1.y + Bm1.z * Bm1.z;
+            const float l2 = B0.x * B0.x + B0.y * B0.y + B0.z * B0.z;
+            const float inv = rsqrtf(l1 * l2), cs = (Bm1.x * B0.x + Bm1.y * B0.y + Bm1.z * B0.z) * inv;
+            const float c1 = cs * __fdividef(1.0f, l1), c2 = cs * __fdividef(1.0f, l2);
+            F.x += kap * ((B0.x * inv - c1 * Bm1.x) - (Bm1.x * inv - c2 * B0.x));
+            F.y += kap * ((B0.y * inv - c1 * Bm1.y) - (Bm1.y * inv - c2 * B0.y));
+            F.z += kap * ((B0.z * inv - c1 * Bm1.z) - (Bm1.z * inv - c2 * B0.z));
+        }
+        if (hp2) {                            // vertex s+1, s its first end: -kappa g1
+            const float l1 = B0.x * B0.x + B0.y * B0.y + B0.z * B0.z;
+            const float l2 = Bp1.x * Bp1.x + Bp1.y * Bp1.y + Bp1.z * Bp1.z;
+            const float inv = rsqrtf(l1 * l2), cs = (B0.x * Bp1.x + B0.y * Bp1.y + B0.z * Bp1.z) * inv;
+            const float c1 = cs * __fdividef(1.0f, l1);
+            F.x -= kap * (Bp1.x * inv - c1 * B0.x);
+            F.y -= kap * (Bp1.y * inv - c1 * B0.y);
+            F.z -= kap * (Bp1.z * inv - c1 * B0.z);
+        }
+        if (hm2) {                            // vertex s-1, s its last end: +kappa g2
+            const float l1 = Bm2.x * Bm2.x + Bm2.y * Bm2.y + Bm2.z * Bm2.z;
+            const float l2 = Bm1.x * Bm1.x + Bm1.y * Bm1.y + Bm1.z * Bm1.z;
+            const float inv = rsqrtf(l1 * l2), cs = (Bm2.x * Bm1.x + Bm2.y * Bm1.y + Bm2.z * Bm1.z) * inv;
+            const float c2 = cs * __fdividef(1.0f, l2);
+            F.x += kap * (Bm2.x * inv - c2 * Bm1.x);
+            F.y += kap * (Bm2.y * inv - c2 * Bm1.y);
+            F.z += kap * (Bm2.z * inv - c2 * Bm1.z);
+        }
+    }
+}
+
+constexpr int STEP_ILP = 4;      // Verlet-list entries in flight per lane
+
+// TPM threads per monomer (1 or 2, adjacent lanes): the lanes split the list
+// (entries k = sub, sub + TPM, ...); with two, lane 0 adds the bonded terms
+// and lane 1 draws the noise, the forces are combined with a shuffle, and
+// lane 0 writes the state.
+// (256, 6): at most 40 registers, 75% occupancy.
+template <int N4, int TPM>
+__global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepArgs P)
+{
+    __shared__ float4 dk[27];
+    __shared__ unsigned stop;
+    if (threadIdx.x < 27) {
+        const int q = threadIdx.x;
+        dk[q] = make_float4((float)(q % 3 - 1), (float)((q / 3) % 3 - 1), (float)(q / 9 - 1), 0.f);
+    }
+    if (threadIdx.x == 0) stop = *(volatile unsigned *)P.flags;    // a latched error stops the run
+    __syncthreads();
+    if (stop) return;                                              // block-uniform
+    const long long step = *P.stepp;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = t / TPM, sub = t % TPM;
+    const bool live = s < P.M;
+    unsigned err = 0;
+    float3 F = make_float3(0.f, 0.f, 0.f), gn = F;
+    float4 rb = make_float4(0.f, 0.f, 0.f, 0.f), dc = rb, pi = rb;
+    int slot = 0, m = 0, cnt = 0;
+    if (live) {
+        slot = __ldg(P.slot_of + s);
+        m = melt_index(P, slot);
+        rb = __ldg(P.recb + s);
+        dc = __ldg(P.dcur + s);
+        // own record rebuilt from its parts: the same bits the last step wrote to pcur
+        pi = make_float4(rb.x + dc.x, rb.y + dc.y, rb.z + dc.z, rb.w);
+        cnt = __ldg(P.nn + s);
+    }
+    const MeltStep &md = P.melt[m];
+    const float h = md.h, rc2 = P.rc2;
+    const int kmax = __reduce_max_sync(0xffffffffu, cnt);
+    const unsigned *__restrict__ col = P.nl + (live ? s : 0);
+    const size_t Mp = (size_t)P.Mp;
+    for (int k0 = sub; k0 < kmax; k0 += STEP_ILP * TPM) {
+        unsigned e[STEP_ILP];
+        float4 pj[STEP_ILP];
+#pragma unroll
+        for (int i = 0; i < STEP_ILP; ++i) {
+            const int k = k0 + i * TPM;
+            e[i] = k < cnt ? __ldg(col + (size_t)k * Mp) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < STEP_ILP; ++i)
+            pj[i] = k0 + i * TPM < cnt ? __ldg(P.pcur + (e[i] & IDX_MASK)) : pi;
+#pragma unroll
+        for (int i = 0; i < STEP_ILP; ++i) {
+            const float4 q = dk[e[i] >> IDX_BITS];
+            const float dx = fmaf(q.x, h, pj[i].x - pi.x);
+            const float dy = fmaf(q.y, h, pj[i].y - pi.y);
+            const float dz = fmaf(q.z, h, pj[i].z - pi.z);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            float fr = mlj_fr32<N4>(P, r2);
+            fr = (k0 + i * TPM < cnt && r2 < rc2) ? fr : 0.0f;
+            F.x += fr * dx; F.y += fr * dy; F.z += fr * dz;
+        }
+    }
+    if (live) {
+        if (sub == 0) bonded32<N4>(P, md, pi, __ldg(P.bp + s), F, err);
+        if (sub == TPM - 1)
+            gn = gauss3_f(draw(P.seed, m, 0, (unsigned long long)step, (uint32_t)(slot - md.off)));
+    }
+    if (TPM == 2) {                        // every lane takes part: s is shared by lanes 2i, 2i+1
+        F.x += __shfl_xor_sync(0xffffffffu, F.x, 1);
+        F.y += __shfl_xor_sync(0xffffffffu, F.y, 1);
+        F.z += __shfl_xor_sync(0xffffffffu, F.z, 1);
+        const int src = (threadIdx.x & 31) | 1;
+        gn.x = __shfl_sync(0xffffffffu, gn.x, src);
+        gn.y = __shfl_sync(0xffffffffu, gn.y, src);
+        gn.z = __shfl_sync(0xffffffffu, gn.z, src);
+    }
+    bool rebuild = false;
+    if (live && sub == 0) {
+        const int Mpi = P.Mp;
+        float *__restrict__ u = P.u;
+        float3 v = make_float3(u[s], u[Mpi + s], u[2 * Mpi + s]);
+        v.x += P.dt * (F.x - P.gamma * v.x + P.amp * gn.x);
+        v.y += P.dt * (F.y - P.gamma * v.y + P.amp * gn.y);
+        v.z += P.dt * (F.z - P.gamma * v.z + P.amp * gn.z);
+        u[s] = v.x; u[Mpi + s] = v.y; u[2 * Mpi + s] = v.z;
+        float4 d = dc;
+        d.x += P.dt * v.x; d.y += P.dt * v.y; d.z += P.dt * v.z;
+        P.dnext[s] = d;
+        P.pnext[s] = make_float4(rb.x + d.x, rb.y + d.y, rb.z + d.z, rb.w);
+        rebuild = d.x * d.x + d.y * d.y + d.z * d.z > P.half_skin2;
+        if (!isfinite(v.x + v.y + v.z)) err |= ERR_NONFINITE;
+    }
+    if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(P.flags + 1, 1u);
+    if (err) atomicOr(P.flags, err);
+}
+
+// 4n of a stage exponent with its own kernel instantiation, 0 otherwise
+static int n4_of(double n)
+{
+    const double q = 4.0 * n;
+    const int k = (int)std::lround(q);
+    if (std::fabs(q - (double)k) > 1e-9) return 0;
+    switch (k) {
+        case 8: case 12: case 16: case 20: case 23: case 26: case 28:
+        case 32: case 36: case 40: case 44: case 48: return k;
+        default: return 0;
+    }
+}
+
+template <int N4>
+static void launch_n4(const StepArgs &a, int tpm, int block, long long M, cudaStream_t st)
+{
+    const int nb = (int)((tpm * M + block - 1) / block);
+    if (tpm == 2) k_step32<N4, 2><<<nb, block, 0, st>>>(a);
+    else k_step32<N4, 1><<<nb, block, 0, st>>>(a);
+}
+
+void step_mixed_launch(kg_ctx *c, cudaStream_t st, int cur)
+{
+    const StageDev &sg = c->stage;
+    StepArgs a{};
+    a.recb = c->recb;
+    a.dcur = c->dlt[cur];
+    a.dnext = c->dlt[cur ^ 1];
+    a.pcur = c->pg[cur];
+    a.pnext = c->pg[cur ^ 1];
+    a.u = (float *)c->u;
+    a.nl = c->nl;
+    a.nn = c->nn;
+    a.slot_of = c->slot_of;
+    a.bp = c->bp;
+    a.flags = c->flags;
+    a.stepp = c->d_step;
+    a.seed = c->sim.seed;
+    a.M = c->M;
+    a.Mp = c->Mp;
+    a.n_melts = c->sim.n_melts;
+    a.rc2 = c->sim.rc2f;
+    a.half_skin2 = c->sim.half_skin2f;
+    a.dt = sg.dtf;
+    a.gamma = sg.gammaf;
+    a.amp = sg.ampf;
+    a.c1xn = sg.c1xnf;
+    a.c2x6 = sg.c2x6f;
+    a.nf = sg.nf;
+    a.kf = sg.kfenef;
+    a.R0sq = sg.R0sqf;
+    a.inv_R0sq = (float)(1.0 / sg.R0sq);
+    a.qmin = sg.qminf;
+    a.kf_qmin = sg.qmin > 0 ? (float)(sg.kfene / sg.qmin) : 0.0f;
+    a.four_R0sq = (float)(4.0 * sg.R0sq);
+    for (int m = 0; m < c->sim.n_melts; ++m) {
+        const MeltDev &md = c->sim.melt[m];
+        a.melt[m] = MeltStep{md.off, md.nc, md.hf, md.Lf, md.invLf, md.kappaf};
+    }
+    const int tpm = c->tpm, blk = c->block;
+    const long long M = c->M;
+    switch (n4_of(sg.n)) {
+        case 8: launch_n4<8>(a, tpm, blk, M, st); break;
+        case 12: launch_n4<12>(a, tpm, blk, M, st); break;
+        case 16: launch_n4<16>(a, tpm, blk, M, st); break;
+        case 20: launch_n4<20>(a, tpm, blk, M, st); break;
+        case 23: launch_n4<23>(a, tpm, blk, M, st); break;
+        case 26: launch_n4<26>(a, tpm, blk, M, st); break;
+        case 28: launch_n4<28>(a, tpm, blk, M, st); break;
+        case 32: launch_n4<32>(a, tpm, blk, M, st); break;
+        case 36: launch_n4<36>(a, tpm, blk, M, st); break;
+        case 40: launch_n4<40>(a, tpm, blk, M, st); break;
+        case 44: launch_n4<44>(a, tpm, blk, M, st); break;
+        case 48: launch_n4<48>(a, tpm, blk, M, st); break;
+        default: launch_n4<0>(a, tpm, blk, M, st); break;
+    }
+}
+
+}  // namespace kg

@@ -74,7 +74,7 @@ def test_noalloc_on_a_side_stream_while_a_context_holds_the_device(kg):
     ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
     try:
         kg.kg_load_config(ctx, 0, m.x, m.v)
-        kg.kg_set_potential_schedule(ctx, [kg.stage(12.0, 10 ** 9, 0.005)])
+        kg.kg_set_potential_schedule(ctx, [kg.stage(2.0, 10 ** 9, 0.002)])    # soft first stage
         kg.kg_step(ctx, 20)
         xs = np.zeros_like(m.x)
         kg.kg_get_config(ctx, 0, xs)
