@@ -732,6 +732,69 @@ def _init_weights(seed=0):
     return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), w3, [0.0]])
 
 
+DBS_KAPPAS = [1.0, 1.5, 2.0, 2.5, 3.0, 3.5]
+DBS_STAGES = [2.0, 3.0, 4.0, 5.0, 5.75, 6.5, 7.0, 8.0, 9.0]
+
+
+def db_success(args):
+    """Double-bridging success rate per admissible attempt against Eq. 15,
+    S = 1.6 exp(-0.77 kappa - 0.35 n) (Sec. II.B, Fig. 3): melts of 50
+    chains x N = 400 at kappa = 1 ... 3.5 share one mixed context; after a dt
+    ramp each stage n of Xi up to 9 relaxes for 2000 steps, then 30 rounds of
+    100 MD steps and one sweep of M attempts per melt count admissible
+    attempts (a drawn bond with a non-empty partner set) and accepted swaps.
+    Run with the exact Metropolis-Hastings acceptance and with the paper's
+    plain Metropolis (KG_FLAG_PAPER_METROPOLIS)."""
+    import torch
+
+    import kg_inputs as KI
+    import paper_2109_11001_gb300 as kg
+    s = torch.cuda.current_stream()
+    base = KI.SEED_BASE + 7
+    melts = [KI.random_walk_melt(50, 400, 0.85, k, base + 100 * i) for i, k in enumerate(DBS_KAPPAS)]
+    out = {"workload": "6 melts of 50 chains x N=400 (20k monomers each), kappa 1-3.5, rho=0.85, mixed",
+           "rounds": 30, "attempts_per_round": "M per melt", "eq15": "S = 1.6 exp(-0.77 kappa - 0.35 n)"}
+    for name, flags in (("hastings", 0), ("paper_metropolis", kg.KG_FLAG_PAPER_METROPOLIS)):
+        p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa) for m in melts], precision=kg.KG_MIXED,
+                           seed=29, fene_qmin=FENE_QMIN, flags=flags, skin=0.4)
+        ctx = kg.kg_create(p, 0, s.cuda_stream, kg.torch_allocator())
+        table = []
+        try:
+            kg.kg_set_potential_schedule(ctx, [kg.stage(2.0, 300, 0.0005), kg.stage(2.0, 300, 0.001),
+                                               kg.stage(2.0, 300, 0.002), kg.stage(2.0, 10 ** 15, 0.005)])
+            for i, m in enumerate(melts):
+                kg.kg_load_config(ctx, i, m.x, m.v)
+            kg.kg_step(ctx, 900)
+            for n in DBS_STAGES:
+                dt = 0.005 if n < 5 else 0.008
+                kg.kg_set_potential_schedule(ctx, [kg.stage(n, 10 ** 15, dt)])
+                kg.kg_step(ctx, 2000)
+                adm = np.zeros(len(melts), dtype=np.int64)
+                acc = np.zeros(len(melts), dtype=np.int64)
+                for _ in range(30):
+                    kg.kg_step(ctx, 100)
+                    for i, m in enumerate(melts):
+                        st = kg.kg_db_sweep_k(ctx, [m.M if j == i else 0 for j in range(len(melts))])
+                        adm[i] += st.attempted - st.empty
+                        acc[i] += st.accepted
+                for i, k in enumerate(DBS_KAPPAS):
+                    table.append({"kappa": k, "n": n, "admissible": int(adm[i]), "accepted": int(acc[i]),
+                                  "S": float(acc[i] / max(adm[i], 1)),
+                                  "S_eq15": 1.6 * float(np.exp(-0.77 * k - 0.35 * n))})
+                log(f"db success {name} n={n}: " + " ".join(f"{t['S']:.4f}" for t in table[-len(melts):]))
+        finally:
+            kg.kg_destroy(ctx)
+        # weighted least squares of ln S = ln a - b kappa - d n over kappa >= 1, n <= 9 (weights: accepted)
+        rows = [t for t in table if t["accepted"] > 0]
+        A = np.array([[1.0, -t["kappa"], -t["n"]] for t in rows])
+        y = np.array([np.log(t["S"]) for t in rows])
+        w = np.sqrt(np.array([t["accepted"] for t in rows], dtype=np.float64))
+        coef, *_ = np.linalg.lstsq(A * w[:, None], y * w, rcond=None)
+        out[name] = {"table": table, "fit": {"a": float(np.exp(coef[0])), "b": float(coef[1]), "d": float(coef[2])}}
+        log(f"db success {name}: fit a {np.exp(coef[0]):.3f} b {coef[1]:.3f} d {coef[2]:.3f}")
+    print(json.dumps({"db_success": out}))
+
+
 def ncu_case(args):
     """A short run for kernel captures: the 1.6M-monomer melt, no prelude,
     seven steps at dt = 0.001 of the stage --ncu-n (default n = 2), with a
@@ -800,12 +863,17 @@ def main():
     ap.add_argument("--ncu-db-budget", type=float, default=1e-3, help="DB attempts per monomer in the --ncu-case sweep")
     ap.add_argument("--ncu-n", type=float, default=2.0, help="stage exponent n of the --ncu-case steps")
     ap.add_argument("--ppa-case", type=int, default=0, help="primitive-path steps of a capture run (0: off)")
+    ap.add_argument("--db-success", action="store_true",
+                    help="measure the DB success rate per admissible attempt over kappa and n against Eq. 15")
     args = ap.parse_args()
     if args.ncu_case:
         ncu_case(args)
         return
     if args.ppa_case:
         ppa_case(args)
+        return
+    if args.db_success:
+        db_success(args)
         return
     if args.warmup < 3:
         args.warmup = 3

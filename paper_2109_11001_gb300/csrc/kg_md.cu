@@ -535,85 +535,142 @@ __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start,
 // shift of the pair until the next build.
 //
 // A warp walks the 27 stencil cells in lockstep: for cell q every lane runs
-// the warp's largest count of that cell, lanes past their own count idle, and
-// the candidate test, exclusions and list append need no divergent control
-// flow except for the rare binary64 band check.  The candidate's offsets and
-// compute index arrive in one 16-byte load.
+// the warp's largest count of that cell; lanes past their own count load a
+// clamped (valid) record and mask it.  The candidate loop has no branch but
+// its own: the load index is clamped, the append is a predicated store, and
+// a pair inside the binary64 band is taken provisionally and counted; a lane
+// with band pairs re-walks its row after the stencil, decides each band entry
+// by the binary64 distance and compacts the row in place (order kept).  The
+// candidate's offsets and compute index arrive in one 16-byte load.  All
+// parameters are by-value kernel arguments.
 constexpr int NL_BLOCK = 128;
+
+struct MeltNl {
+    int off, cell_off, nbk, nc;
+    float h, lo, hi;
+    double L;
+};
+
+struct NlArgs {
+    const double *x;         // binary64 positions [3][Mp] (band decisions)
+    const float4 *recb;      // build records of the compute order
+    const float4 *recs;      // the same in cell order, w = compute index
+    const int *start;        // cell starts (cell order)
+    unsigned *nl;            // out: entries j | q << IDX_BITS, column-major [maxnb][Mp]
+    int *nn;                 // out: list lengths
+    unsigned *flags;
+    const int *slot_of;
+    const int4 *bp;          // chain partners (1-2 bonded: y, z)
+    int M, Mp, maxnb, n_melts;
+    double rl2;
+    MeltNl melt[MAX_MELTS];
+};
+
+__device__ __forceinline__ void st_pred(unsigned *addr, unsigned v, bool p)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.u32 [%0], %1;\n\t}"
+                 ::"l"(addr), "r"(v), "r"((unsigned)p) : "memory");
+}
+
+// binary32 squared distance of the build records of s (ri) and t (rj) for a
+// pair in stencil cell (dx, dy, dz) of s: the same expression as the build's
+__device__ __forceinline__ float nl_r2(float4 ri, float4 rj, int dx, int dy, int dz, float h)
+{
+    const float ox = ri.x - (float)dx * h, oy = ri.y - (float)dy * h, oz = ri.z - (float)dz * h;
+    const float ex = rj.x - ox, ey = rj.y - oy, ez = rj.z - oz;
+    return ex * ex + ey * ey + ez * ez;
+}
 
 // (128, 10): at most 48 registers; more resident warps hide the candidate
 // loads (tighter caps spill too much, looser ones leave the SM half idle)
-__global__ void __launch_bounds__(NL_BLOCK, 10) k_nlist(const SimDev *__restrict__ Sp, const double *__restrict__ x,
-                                                   const float4 *__restrict__ recb, const float4 *__restrict__ recs,
-                                                   const int *__restrict__ start,
-                                                   unsigned *__restrict__ nl, int *__restrict__ nn,
-                                                   unsigned *__restrict__ flags, const int *__restrict__ slot_of,
-                                                   const int4 *__restrict__ bpa)
+__global__ void __launch_bounds__(NL_BLOCK, 10) k_nlist(const __grid_constant__ NlArgs A)
 {
-    if (!flags[1] || flags[0]) return;
+    __shared__ unsigned go;
+    if (threadIdx.x == 0) go = (A.flags[1] && !A.flags[0]) ? 1u : 0u;
+    __syncthreads();
+    if (!go) return;                                         // block-uniform
     constexpr unsigned FULL = 0xffffffffu;
-    const SimDev &S = *Sp;
     const int s = blockIdx.x * NL_BLOCK + threadIdx.x;
-    const bool live = s < S.M;
-    const int sv = live ? s : S.M - 1;                       // idle lanes read valid memory, write nothing
-    const MeltDev &md = S.melt[melt_of(S, slot_of[sv])];
-    const int4 bp = bpa[sv];                                 // 1-2 bonded partners: bp.y, bp.z
-    const float4 ri = __ldg(recb + sv);
+    const bool live = s < A.M;
+    const int sv = live ? s : A.M - 1;                       // idle lanes read valid memory, write nothing
+    const int slot = __ldg(A.slot_of + sv);
+    int m = 0;
+    while (m + 1 < A.n_melts && slot >= A.melt[m + 1].off) ++m;
+    const MeltNl &md = A.melt[m];
+    const int4 bp = __ldg(A.bp + sv);                        // 1-2 bonded partners: bp.y, bp.z
+    const float4 ri = __ldg(A.recb + sv);
     const unsigned code = __float_as_uint(ri.w);
     const int cx = (int)(code & CODE_MASK), cy = (int)((code >> CODE_BITS) & CODE_MASK);
     const int cz = (int)(code >> (2 * CODE_BITS));
-    const int nc = md.nc;
-    const float h = md.hf, lo = md.nl_lo, hi = md.nl_hi;
-    const int maxnb = S.maxnb;
-    const size_t Mp = (size_t)S.Mp;
-    unsigned *__restrict__ out = nl + s;
-    int cnt = 0;
+    const int nc = md.nc, nbk = md.nbk;
+    const float h = md.h, lo = md.lo, hi = md.hi;
+    const int maxnb = A.maxnb, last = A.M - 1;
+    const size_t Mp = (size_t)A.Mp;
+    unsigned *__restrict__ out = A.nl + (live ? s : 0);
+    int cnt = 0, nband = 0;
+    unsigned err = 0;
 #pragma unroll 1
-    for (int q = 0; q < 27; ++q) {
-        const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = q / 9 - 1;
-        int xx = cx + dx, yy = cy + dy, zz = cz + dz;
-        xx = xx < 0 ? nc - 1 : (xx >= nc ? 0 : xx);
-        yy = yy < 0 ? nc - 1 : (yy >= nc ? 0 : yy);
+    for (int dz = -1; dz <= 1; ++dz) {
+        int zz = cz + dz;
         zz = zz < 0 ? nc - 1 : (zz >= nc ? 0 : zz);
-        const int cell = md_cell(md, xx, yy, zz);
-        const int k0 = start[cell];
-        int n = live ? start[cell + 1] - k0 : 0;
-        if (n > MAX_CELL_OCC) {
-            atomicOr(flags, ERR_NL_CAPACITY);
-            n = 0;
-        }
-        const int nmax = __reduce_max_sync(FULL, n);
-        const float ox = ri.x - (float)dx * h, oy = ri.y - (float)dy * h, oz = ri.z - (float)dz * h;
-        const unsigned tag = (unsigned)q << IDX_BITS;
-        for (int j = 0; j < nmax; ++j) {
-            const bool valid = j < n;
-            float4 rj = make_float4(1e30f, 1e30f, 1e30f, __int_as_float(-1));
-            if (valid) rj = __ldg(recs + k0 + j);
-            const int t = __float_as_int(rj.w);
-            const float ex = rj.x - ox, ey = rj.y - oy, ez = rj.z - oz;
-            const float r2 = ex * ex + ey * ey + ez * ez;
-            bool take = r2 < hi && t != s && t != bp.y && t != bp.z;
-            if (take && r2 >= lo) take = dist2_exact(x, S.Mp, md.L, s, t) < S.rl2;   // rare: inside the band
-            if (take) {
-                if (cnt < maxnb) out[(size_t)cnt * Mp] = (unsigned)t | tag;
-                ++cnt;
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            int yy = cy + dy;
+            yy = yy < 0 ? nc - 1 : (yy >= nc ? 0 : yy);
+            const int rowb = md.cell_off + (((zz >> 2) * nbk + (yy >> 2)) * nbk << 6) + ((zz & 3) << 4) + ((yy & 3) << 2);
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                int xx = cx + dx;
+                xx = xx < 0 ? nc - 1 : (xx >= nc ? 0 : xx);
+                const int cell = rowb + ((xx >> 2) << 6) + (xx & 3);
+                const int k0 = __ldg(A.start + cell);
+                int n = live ? __ldg(A.start + cell + 1) - k0 : 0;
+                if (n > MAX_CELL_OCC) {
+                    err = ERR_NL_CAPACITY;
+                    n = 0;
+                }
+                const int nmax = __reduce_max_sync(FULL, n);
+                const float ox = ri.x - (float)dx * h, oy = ri.y - (float)dy * h, oz = ri.z - (float)dz * h;
+                const unsigned tag = (unsigned)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) << IDX_BITS;
+                for (int j = 0; j < nmax; ++j) {
+                    const float4 rj = __ldg(A.recs + min(k0 + j, last));
+                    const int t = __float_as_int(rj.w);
+                    const float ex = rj.x - ox, ey = rj.y - oy, ez = rj.z - oz;
+                    const float r2 = ex * ex + ey * ey + ez * ez;
+                    const bool take = (j < n) & (r2 < hi) & (t != s) & (t != bp.y) & (t != bp.z);
+                    nband += (take & (r2 >= lo)) ? 1 : 0;
+                    st_pred(out + (size_t)cnt * Mp, (unsigned)t | tag, take & (cnt < maxnb));
+                    cnt += take ? 1 : 0;
+                }
             }
         }
     }
+    if (nband > 0 && cnt <= maxnb) {                         // rare: decide the band entries in binary64
+        int w = 0;
+        for (int k = 0; k < cnt; ++k) {
+            const unsigned e = out[(size_t)k * Mp];
+            const int t = (int)(e & IDX_MASK), q = (int)(e >> IDX_BITS);
+            const float r2 = nl_r2(ri, __ldg(A.recb + t), q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1, h);
+            const bool keep = r2 < lo || dist2_exact(A.x, A.Mp, md.L, s, t) < A.rl2;
+            if (keep) out[(size_t)(w++) * Mp] = e;
+        }
+        cnt = w;
+    }
     if (live) {
-        nn[s] = cnt < maxnb ? cnt : maxnb;
+        A.nn[s] = cnt < maxnb ? cnt : maxnb;
         if (cnt > maxnb) {
-            atomicOr(flags, ERR_NL_CAPACITY);
-            atomicMax(flags + 3, (unsigned)cnt);
+            err |= ERR_NL_CAPACITY;
+            atomicMax(A.flags + 3, (unsigned)cnt);
         }
     }
+    if (err) atomicOr(A.flags, err);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(flags + 4, 1u) == gridDim.x - 1) {
-            flags[1] = 0u;
-            flags[4] = 0u;
-            flags[5] += 1u;                    // Verlet builds completed
+        if (atomicAdd(A.flags + 4, 1u) == gridDim.x - 1) {
+            A.flags[1] = 0u;
+            A.flags[4] = 0u;
+            A.flags[5] += 1u;                    // Verlet builds completed
         }
     }
 }
@@ -878,6 +935,30 @@ void rebuild_md(kg_ctx *c)
     launch_rebuild(c, c->stream);
 }
 
+static NlArgs nl_args(const kg_ctx *c)
+{
+    NlArgs a{};
+    a.x = c->x;
+    a.recb = c->recb;
+    a.recs = c->recs;
+    a.start = c->cstart;
+    a.nl = c->nl;
+    a.nn = c->nn;
+    a.flags = c->flags;
+    a.slot_of = c->slot_of;
+    a.bp = c->bp;
+    a.M = c->M;
+    a.Mp = c->Mp;
+    a.maxnb = c->maxnb;
+    a.n_melts = c->sim.n_melts;
+    a.rl2 = c->sim.rl2;
+    for (int m = 0; m < c->sim.n_melts; ++m) {
+        const MeltDev &md = c->sim.melt[m];
+        a.melt[m] = MeltNl{md.off, md.cell_off, md.nbk, md.nc, md.hf, md.nl_lo, md.nl_hi, md.L};
+    }
+    return a;
+}
+
 static void launch_rebuild(kg_ctx *c, cudaStream_t st)
 {
     const bool mixed = c->precision == KG_MIXED;
@@ -892,8 +973,7 @@ static void launch_rebuild(kg_ctx *c, cudaStream_t st)
                                                c->recs);
     k_cellsort<<<nblk(c->ncell_md, 256), 256, 0, st>>>(c->cstart, c->clist, c->recs, c->ccount, c->ncell_md,
                                                        c->flags);
-    k_nlist<<<nblk(c->M, NL_BLOCK), NL_BLOCK, 0, st>>>(c->d_sim, c->x, c->recb, c->recs, c->cstart, c->nl,
-                                                       c->nn, c->flags, c->slot_of, c->bp);
+    k_nlist<<<nblk(c->M, NL_BLOCK), NL_BLOCK, 0, st>>>(nl_args(c));
 }
 
 static void launch_step_kernel(kg_ctx *c, cudaStream_t st, int cur)

@@ -167,32 +167,105 @@ __device__ __forceinline__ void bonded32(const StepArgs &P, const MeltStep &md, 
 }
 
 constexpr int STEP_ILP = 4;      // Verlet-list entries in flight per lane
+constexpr int STEP_CH = 8;       // list entries per lane in one staged chunk
+constexpr int STEP_WAIT_MAX = 1 << 22;   // bounded mbarrier waits (each try_wait suspends briefly)
+
+// ---------------------------------------------------------------------------
+// list staging: each warp streams its monomers' Verlet-list columns into
+// shared memory with cp.async.bulk (one 4 * 32/TPM-byte segment per column,
+// issued by lane 0), double-buffered, completion counted by an mbarrier per
+// buffer; the gathers of one chunk then depend on a shared-memory load while
+// the next chunk's list bytes stream from HBM
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// true once the barrier's phase `parity` has completed; false after
+// STEP_WAIT_MAX polls
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < STEP_WAIT_MAX; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 // TPM threads per monomer (1 or 2, adjacent lanes): the lanes split the list
 // (entries k = sub, sub + TPM, ...); with two, lane 0 adds the bonded terms
 // and lane 1 draws the noise, the forces are combined with a shuffle, and
-// lane 0 writes the state.
+// lane 0 writes the state.  The bonded terms and the noise run while the
+// first list chunks stream in.
 // (256, 6): at most 40 registers, 75% occupancy.
+// Dynamic shared memory: per warp two buffers of STEP_CH * 32 entries.
 template <int N4, int TPM>
 __global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepArgs P)
 {
+    constexpr int MW = 32 / TPM;                 // monomers per warp
+    constexpr int CC = STEP_CH * TPM;            // list columns per chunk
+    constexpr uint32_t SEG = 4u * MW;            // bytes of one column segment
+    extern __shared__ __align__(128) unsigned step_smem[];
     __shared__ float4 dk[27];
+    __shared__ __align__(8) unsigned long long bars[2 * 8];
     __shared__ unsigned stop;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned *buf = step_smem + (size_t)wid * (2 * CC * MW);
+    const uint32_t bar0 = smem_u32(&bars[2 * wid]), bar1 = smem_u32(&bars[2 * wid + 1]);
     if (threadIdx.x < 27) {
         const int q = threadIdx.x;
         dk[q] = make_float4((float)(q % 3 - 1), (float)((q / 3) % 3 - 1), (float)(q / 9 - 1), 0.f);
     }
+    if (lane == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     if (threadIdx.x == 0) stop = *(volatile unsigned *)P.flags;    // a latched error stops the run
     __syncthreads();
     if (stop) return;                                              // block-uniform
-    const long long step = *P.stepp;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = t / TPM, sub = t % TPM;
+    const int s = t / TPM, sub = t % TPM, im = lane / TPM;
     const bool live = s < P.M;
+    const int cnt = live ? __ldg(P.nn + s) : 0;
+    const int kmax = __reduce_max_sync(0xffffffffu, cnt);
+    const int nch = (kmax + CC - 1) / CC;
+    const int wbase = (blockIdx.x * blockDim.x + wid * 32) / TPM;  // first monomer of the warp
+    const unsigned *__restrict__ gsrc = P.nl + wbase;
+    const size_t Mp = (size_t)P.Mp;
+    auto issue = [&](int c) {                                      // lane 0: chunk c into buffer c & 1
+        const int cols = min(CC, kmax - c * CC);
+        const uint32_t bar = (c & 1) ? bar1 : bar0;
+        const uint32_t dst = smem_u32(buf + (c & 1) * (CC * MW));
+        mbar_expect_tx(bar, (uint32_t)cols * SEG);
+        for (int k = 0; k < cols; ++k) bulk_g2s(dst + k * SEG, gsrc + (size_t)(c * CC + k) * Mp, SEG, bar);
+    };
+    if (lane == 0) {
+        if (nch > 0) issue(0);
+        if (nch > 1) issue(1);
+    }
+    const long long step = *P.stepp;
     unsigned err = 0;
     float3 F = make_float3(0.f, 0.f, 0.f), gn = F;
     float4 rb = make_float4(0.f, 0.f, 0.f, 0.f), dc = rb, pi = rb;
-    int slot = 0, m = 0, cnt = 0;
+    int slot = 0, m = 0;
     if (live) {
         slot = __ldg(P.slot_of + s);
         m = melt_index(P, slot);
@@ -200,52 +273,68 @@ __global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepA
         dc = __ldg(P.dcur + s);
         // own record rebuilt from its parts: the same bits the last step wrote to pcur
         pi = make_float4(rb.x + dc.x, rb.y + dc.y, rb.z + dc.z, rb.w);
-        cnt = __ldg(P.nn + s);
     }
     const MeltStep &md = P.melt[m];
-    const float h = md.h, rc2 = P.rc2;
-    const int kmax = __reduce_max_sync(0xffffffffu, cnt);
-    const unsigned *__restrict__ col = P.nl + (live ? s : 0);
-    const size_t Mp = (size_t)P.Mp;
-    for (int k0 = sub; k0 < kmax; k0 += STEP_ILP * TPM) {
-        unsigned e[STEP_ILP];
-        float4 pj[STEP_ILP];
-#pragma unroll
-        for (int i = 0; i < STEP_ILP; ++i) {
-            const int k = k0 + i * TPM;
-            e[i] = k < cnt ? __ldg(col + (size_t)k * Mp) : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < STEP_ILP; ++i)
-            pj[i] = k0 + i * TPM < cnt ? __ldg(P.pcur + (e[i] & IDX_MASK)) : pi;
-#pragma unroll
-        for (int i = 0; i < STEP_ILP; ++i) {
-            const float4 q = dk[e[i] >> IDX_BITS];
-            const float dx = fmaf(q.x, h, pj[i].x - pi.x);
-            const float dy = fmaf(q.y, h, pj[i].y - pi.y);
-            const float dz = fmaf(q.z, h, pj[i].z - pi.z);
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            float fr = mlj_fr32<N4>(P, r2);
-            fr = (k0 + i * TPM < cnt && r2 < rc2) ? fr : 0.0f;
-            F.x += fr * dx; F.y += fr * dy; F.z += fr * dz;
-        }
-    }
     if (live) {
         if (sub == 0) bonded32<N4>(P, md, pi, __ldg(P.bp + s), F, err);
         if (sub == TPM - 1)
             gn = gauss3_f(draw(P.seed, m, 0, (unsigned long long)step, (uint32_t)(slot - md.off)));
     }
+    // pair loop: an entry past the lane's own list becomes the lane's own
+    // record with the zero shift (code 13), a valid gather whose term is masked
+    const float h = md.h, rc2 = P.rc2;
+    const unsigned self = (unsigned)(live ? s : 0) | (13u << IDX_BITS);
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+        ok = __all_sync(0xffffffffu, ok && mbar_wait((c & 1) ? bar1 : bar0, (uint32_t)((c >> 1) & 1)));
+        if (!ok) break;                                            // warp-uniform
+        const unsigned *cb = buf + (c & 1) * (CC * MW);
+#pragma unroll
+        for (int j0 = 0; j0 < STEP_CH; j0 += STEP_ILP) {
+            if (c * CC + TPM * j0 >= kmax) break;                  // warp-uniform: no lane has entries left
+            unsigned e[STEP_ILP];
+            float4 pj[STEP_ILP];
+#pragma unroll
+            for (int i = 0; i < STEP_ILP; ++i) {
+                const int kk = sub + TPM * (j0 + i);
+                e[i] = c * CC + kk < cnt ? cb[kk * MW + im] : self;
+            }
+#pragma unroll
+            for (int i = 0; i < STEP_ILP; ++i) pj[i] = __ldg(P.pcur + (e[i] & IDX_MASK));
+#pragma unroll
+            for (int i = 0; i < STEP_ILP; ++i) {
+                const float4 q = dk[e[i] >> IDX_BITS];
+                const float dx = fmaf(q.x, h, pj[i].x - pi.x);
+                const float dy = fmaf(q.y, h, pj[i].y - pi.y);
+                const float dz = fmaf(q.z, h, pj[i].z - pi.z);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                float fr = mlj_fr32<N4>(P, r2);
+                fr = (c * CC + sub + TPM * (j0 + i) < cnt && r2 < rc2) ? fr : 0.0f;
+                F.x += fr * dx; F.y += fr * dy; F.z += fr * dz;
+            }
+        }
+        __syncwarp();                                              // every lane is done with buffer c & 1
+        if (lane == 0 && c + 2 < nch) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // reads before the async refill
+            issue(c + 2);
+        }
+    }
+    if (!ok) {                                                     // a staged chunk never arrived
+        err |= ERR_TIMEOUT;
+        if (lane == 0)                                             // let the copies in flight land
+            for (int c = 0; c < min(nch, 2); ++c) mbar_wait(c & 1 ? bar1 : bar0, 0u);
+    }
     if (TPM == 2) {                        // every lane takes part: s is shared by lanes 2i, 2i+1
         F.x += __shfl_xor_sync(0xffffffffu, F.x, 1);
         F.y += __shfl_xor_sync(0xffffffffu, F.y, 1);
         F.z += __shfl_xor_sync(0xffffffffu, F.z, 1);
-        const int src = (threadIdx.x & 31) | 1;
+        const int src = lane | 1;
         gn.x = __shfl_sync(0xffffffffu, gn.x, src);
         gn.y = __shfl_sync(0xffffffffu, gn.y, src);
         gn.z = __shfl_sync(0xffffffffu, gn.z, src);
     }
     bool rebuild = false;
-    if (live && sub == 0) {
+    if (live && sub == 0 && ok) {
         const int Mpi = P.Mp;
         float *__restrict__ u = P.u;
         float3 v = make_float3(u[s], u[Mpi + s], u[2 * Mpi + s]);
@@ -281,8 +370,9 @@ template <int N4>
 static void launch_n4(const StepArgs &a, int tpm, int block, long long M, cudaStream_t st)
 {
     const int nb = (int)((tpm * M + block - 1) / block);
-    if (tpm == 2) k_step32<N4, 2><<<nb, block, 0, st>>>(a);
-    else k_step32<N4, 1><<<nb, block, 0, st>>>(a);
+    const size_t smem = (size_t)(block / 32) * 2 * STEP_CH * 32 * sizeof(unsigned);
+    if (tpm == 2) k_step32<N4, 2><<<nb, block, smem, st>>>(a);
+    else k_step32<N4, 1><<<nb, block, smem, st>>>(a);
 }
 
 void step_mixed_launch(kg_ctx *c, cudaStream_t st, int cur)

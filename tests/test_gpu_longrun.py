@@ -1,0 +1,146 @@
+"""Long-run statistics: the mixed-precision GPU path against the binary64
+oracle, and against the binary64 GPU path.
+
+Chaos separates two trajectories within a few hundred steps even from the
+same state and seeds, so long runs compare statistically (parity bar:
+<R^2(n)>/n, l_K and the bond and cos(theta) histograms within 2 standard
+errors).
+
+* 16 independent melts of 20 chains x N = 50 (kappa = 1.5, rho = 0.85) advance
+  together in one mixed-precision context; the oracle runs the same 16 melts,
+  same seeds and noise streams, one process per melt.  Both sides: the
+  soft-to-WCA relaxation, then 20,000 WCA steps (dt = 0.01) with 100 DB
+  attempts per melt every 50 steps, sampled every 100 steps after the first
+  2,000.  Each melt's time average is one independent sample; melt i of both
+  sides starts from the same state, so the comparison is paired: the standard
+  error is that of the 16 differences (their spread / 4).
+* Every scalar summary must agree within 2 standard errors: l_K (Eq. 14 fitted
+  over N/4 <= n <= N/2), <R^2(n)>/n averaged over that range, <R^2(1)> (mean
+  squared bond) and the bond-bond correlation (<R^2(2)> - 2 <R^2(1)>) / 2.
+* The vectors (<R^2(n)>/n at all n, every populated histogram bin: about 80
+  comparisons, correlated) are checked family-wise: at least 85% of them
+  within 2 standard errors and none beyond 3.5 (for independent comparisons
+  at the null, about 1% of runs would exceed 3.5 somewhere).
+"""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import kg_inputs as KI
+from oracle import kuhn
+from oracle import longrun
+
+pytestmark = pytest.mark.gpu
+
+RELAX = [(2.0, 300, 0.0005), (2.0, 300, 0.001), (4.0, 300, 0.0015), (6.5, 300, 0.0025), (9.0, 300, 0.004),
+         (12.0, 300, 0.005)]
+N_MELTS, N_CH, N, KAPPA = 16, 20, 50, 1.5
+PROD, EVERY, SKIP, K, NBINS, SEED = 20000, 100, 2000, 100, 40, 11
+
+
+@pytest.fixture(scope="module")
+def kg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2109_11001_gb300 as kg
+    kg.load()
+    return kg
+
+
+def _melts():
+    base = KI.config(1)["seed"]
+    return [KI.random_walk_melt(N_CH, N, 0.85, KAPPA, base + 100 * i) for i in range(N_MELTS)]
+
+
+def _summaries(r2n):
+    """Per-melt scalar summaries from a time-averaged <R^2(n)>."""
+    n = np.arange(N // 4, N // 2 + 1)
+    return {"l_K": kuhn.fit_lk(r2n), "R2(n)/n, N/4..N/2": float(np.mean(r2n[n] / n)),
+            "<R^2(1)>": float(r2n[1]), "bond-bond": float((r2n[2] - 2 * r2n[1]) / 2)}
+
+
+def _z(a, b):
+    """Paired z of the mean difference: sample i of both sides started from the
+    same state (axis 0 = samples), so the large-scale structure the two
+    trajectories keep in common cancels in a - b."""
+    d = np.asarray(a) - np.asarray(b)
+    return d.mean(axis=0) / (d.std(axis=0, ddof=1) / np.sqrt(len(d)))
+
+
+def _run_gpu(kg, melts):
+    import torch
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa) for m in melts], precision=kg.KG_MIXED,
+                       seed=SEED, fene_qmin=0.01)
+    ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+    r2 = np.zeros((N_MELTS, PROD // EVERY, N))
+    bh = np.zeros((N_MELTS, PROD // EVERY, NBINS))
+    ch = np.zeros_like(bh)
+    ns = 0
+    try:
+        kg.kg_set_potential_schedule(ctx, [kg.stage(n, k, dt) for n, k, dt in RELAX] +
+                                     [kg.stage(12.0, 10 ** 9, 0.01)])
+        for i, m in enumerate(melts):
+            kg.kg_load_config(ctx, i, m.x, m.v)
+        kg.kg_step(ctx, sum(k for _, k, _ in RELAX))
+        for i in range(PROD // 50):
+            kg.kg_step(ctx, 50)
+            kg.kg_db_sweep_k(ctx, [K] * N_MELTS)
+            done = (i + 1) * 50
+            if done > SKIP and done % EVERY == 0:
+                for mm in range(N_MELTS):
+                    kg.kg_observables(ctx, mm, r2[mm, ns], bh[mm, ns], ch[mm, ns], NBINS)
+                ns += 1
+    finally:
+        kg.kg_destroy(ctx)
+    return r2[:, :ns], bh[:, :ns], ch[:, :ns]
+
+
+def _run_oracle(melts):
+    jobs = [dict(x=m.x, u=m.v, n_chains=N_CH, chain_len=N, box=m.box, kappa=KAPPA, seed=SEED, stream=i,
+                 fene_qmin=0.01, relax=RELAX, prod_stage=(12.0, 0.01), prod=PROD, every=EVERY, sweep_every=50,
+                 skip=SKIP, K=K, nbins=NBINS) for i, m in enumerate(melts)]
+    with mp.get_context("spawn").Pool(min(N_MELTS, mp.cpu_count())) as pool:
+        res = pool.map(longrun.trajectory, jobs, chunksize=1)
+    return (np.stack([r["r2n"] for r in res]), np.stack([r["bond"] for r in res]),
+            np.stack([r["cos"] for r in res]))
+
+
+def test_long_run_statistics_of_batched_mixed_melts_match_the_oracle(kg):
+    melts = _melts()
+    gr2, gbh, gch = _run_gpu(kg, melts)
+    or2, obh, och = _run_oracle(melts)
+    assert gr2.shape == or2.shape and gr2.shape[1] >= 150
+    # per-melt time averages: 16 independent samples per side
+    g_r2, o_r2 = gr2.mean(axis=1), or2.mean(axis=1)
+    g_sum = [_summaries(r) for r in g_r2]
+    o_sum = [_summaries(r) for r in o_r2]
+    report = {}
+    for key in g_sum[0]:
+        a = np.array([s[key] for s in g_sum])
+        b = np.array([s[key] for s in o_sum])
+        report[key] = (a.mean(), b.mean(), float(_z(a, b)))
+    print("scalar summaries (GPU mean, oracle mean, z):", report)
+    for key, (a, b, z) in report.items():
+        assert abs(z) < 2.0, (key, a, b, z)
+    # vectors: <R^2(n)>/n at every n, populated histogram bins (per-melt frequencies)
+    n = np.arange(1, N)
+    z_r2 = _z(g_r2[:, 1:] / n, o_r2[:, 1:] / n)
+    gb, ob = gbh.sum(axis=1), obh.sum(axis=1)
+    gb, ob = gb / gb.sum(axis=1, keepdims=True), ob / ob.sum(axis=1, keepdims=True)
+    pop = obh.sum(axis=(0, 1)) >= 200
+    z_b = _z(gb[:, pop], ob[:, pop])
+    gc, oc = gch.sum(axis=1), och.sum(axis=1)
+    gc, oc = gc / gc.sum(axis=1, keepdims=True), oc / oc.sum(axis=1, keepdims=True)
+    popc = och.sum(axis=(0, 1)) >= 200
+    z_c = _z(gc[:, popc], oc[:, popc])
+    zall = np.concatenate([z_r2, z_b, z_c])
+    print(f"vectors: {len(zall)} comparisons, {np.mean(np.abs(zall) < 2):.3f} within 2, max |z| "
+          f"{np.abs(zall).max():.2f} (R2 {np.abs(z_r2).max():.2f}, bond {np.abs(z_b).max():.2f}, "
+          f"cos {np.abs(z_c).max():.2f})")
+    assert len(z_b) >= 5 and len(z_c) >= 15
+    assert np.mean(np.abs(zall) < 2.0) >= 0.85, zall
+    assert np.abs(zall).max() < 3.5, zall
