@@ -364,13 +364,14 @@ def run_ours(args, world, rank, local):
         best = kg.kg_autotune(params, [xs], [vs], kg.stage(12.0, -1, DT), 100, local, stream.cuda_stream,
                               kg.torch_allocator())
         tuning = {"skin": best.skin, "block_size": best.block_size,
-                  "threads_per_monomer": best.threads_per_monomer, "trials": best.trials,
-                  "ms_per_md_step": best.ms_per_step}
+                  "threads_per_monomer": best.threads_per_monomer, "cell_scale": best.cell_scale,
+                  "trials": best.trials, "ms_per_md_step": best.ms_per_step}
         log(f"autotune: {tuning}")
         kg.kg_destroy(ctx)
         params = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=prec, seed=11 + rank,
                                 fene_qmin=FENE_QMIN, skin=best.skin, block_size=best.block_size,
-                                threads_per_monomer=best.threads_per_monomer, sort_interval=args.sort_interval)
+                                threads_per_monomer=best.threads_per_monomer, sort_interval=args.sort_interval,
+                                cell_scale=best.cell_scale)
         ctx = kg.kg_create(params, local, stream.cuda_stream, kg.torch_allocator())
         kg.kg_set_potential_schedule(ctx, [kg.stage(12.0, 10 ** 15, DT)])
         kg.kg_load_config(ctx, 0, xs, vs)
@@ -463,9 +464,11 @@ def run_ours(args, world, rank, local):
 
     # secondary: the same step in plain binary64 on this GPU (single rank), and
     # the learned double-bridging proposal against the uniform one
-    sec = lsec = bsec = psec = None
+    sec = lsec = bsec = psec = esec = None
     if world == 1 and args.secondary:
         psec = ppa_secondary(kg, torch, ctx, m)
+        if os.path.exists(N1_REF):
+            esec = equilibration_secondary(kg, torch, args, local)
         sec = secondary(kg, torch, args, local)
         bsec = batched_secondary(kg, torch, args, local)
         lsec = learned_secondary(kg, torch, args, local)
@@ -549,6 +552,8 @@ def run_ours(args, world, rank, local):
         line["learned_db"] = lsec
     if psec:
         line["ppa"] = psec
+    if esec:
+        line["equilibration"] = esec
     print(json.dumps(line))
 
 
@@ -630,6 +635,129 @@ def batched_secondary(kg, torch, args, local):
                         f"{M} monomers, rho=0.85, skin 0.5, block 64",
             "batched_monomer_steps_per_s": units / t_batched,
             "one_melt_at_a_time_monomer_steps_per_s": units / t_seq}
+
+
+N1_REF = os.path.join(ROOT, "tests", "golden", "n1_reference.json")
+
+
+def run_protocol(kg, torch, ref, melts, precision, seeds_from=0, sample=True):
+    """The scaled paper protocol of `ref` (stages, sweeps at R_MC with the
+    fractional attempts carried over) on `melts` in one context; returns
+    (seconds, per-melt <R^2(n)> averaged over the final stage's window,
+    end-to-end vectors sampled in the final stage).  Melt i takes the noise
+    stream of melt seeds_from + i."""
+    S = ref["settings"]
+    s = torch.cuda.current_stream()
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa) for m in melts], precision=precision,
+                       seed=S["seed"], fene_qmin=S["fene_qmin"])
+    ctx = kg.kg_create(p, 0, s.cuda_stream, kg.torch_allocator())
+    nm = len(melts)
+    N = melts[0].chain_len
+    r2 = np.zeros((nm, N))
+    buf = np.zeros(N)
+    ree = []
+    ns = 0
+    try:
+        stages = [tuple(x) for x in ref["stages"]]
+        kg.kg_set_potential_schedule(ctx, [kg.stage(n, k, dt) for n, k, dt in stages])
+        for i, m in enumerate(melts):
+            kg.kg_load_config(ctx, i, m.x, m.v)
+        kg.kg_set_counters(ctx, 0, 0)
+        x = np.zeros_like(melts[0].x)
+        carry = 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for si, (n, k, dt) in enumerate(stages):
+            done = 0
+            while done < k:
+                q = min(S["sweep_every"], k - done)
+                kg.kg_step(ctx, q)
+                done += q
+                want = S["r_mc"] * melts[0].M * q * dt + carry
+                K = int(np.floor(want))
+                carry = want - K
+                kg.kg_db_sweep_k(ctx, [K] * nm)
+                if sample and si == len(stages) - 1 and done % S["sample_every"] == 0:
+                    if done > (1 - S["window_frac"]) * k:
+                        for i in range(nm):
+                            kg.kg_observables(ctx, i, buf)
+                            r2[i] += buf
+                        ns += 1
+                    kg.kg_get_config(ctx, 0, x)
+                    c = x.reshape(3, melts[0].n_chains, N)
+                    ree.append(c[:, :, -1] - c[:, :, 0])
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+    finally:
+        kg.kg_destroy(ctx)
+    return sec, (r2 / max(ns, 1)), np.array(ree)
+
+
+def _r2_mid(r2n):
+    N = len(r2n)
+    n = np.arange(N // 4, N // 2 + 1)
+    return float(np.mean(r2n[n] / n))
+
+
+def _ree_acf(ree, lags):
+    """<R_ee(t) . R_ee(t + lag)> / <R_ee^2> over chains and time origins."""
+    v = np.transpose(ree, (0, 2, 1))            # (samples, chains, 3)
+    norm = float((v * v).sum(axis=2).mean())
+    return [float((v[:-L or None] * v[L:]).sum(axis=2).mean() / norm) if L < len(v) else None for L in lags]
+
+
+def equilibration_secondary(kg, torch, args, local):
+    """Equilibrated melts per hour: the scaled paper protocol (dt ramp, the
+    twelve stages of Eqs. 16-20 for kappa = 1.5, N = 50, DB at R_MC) on 16
+    melts of 20 x 50, (a) all in one mixed-precision context, (b) in plain
+    binary64, one melt per context (two melts timed, the rate per melt
+    extrapolated).  Each form's final <R^2(n)>/n over N/4 <= n <= N/2
+    (time average over the last 40% of the n = 12 stage, mean over melts) is
+    compared with the oracle's value on the same melts and protocol
+    (tests/golden/n1_reference.json, written by an oracle-only script); the
+    criterion is agreement within 1%."""
+    import kg_inputs as KI
+    with open(N1_REF) as f:
+        ref = json.load(f)
+    S = ref["settings"]
+    base = KI.config(1)["seed"]
+    melts = [KI.random_walk_melt(S["n_chains"], S["chain_len"], S["rho"], S["kappa"], base + 100 * i)
+             for i in range(S["n_melts"])]
+    oracle_mid = np.array([_r2_mid(np.array(r)) for r in ref["r2n_protocol_end"]])
+    t_mix, r2_mix, ree_mix = run_protocol(kg, torch, ref, melts, kg.KG_MIXED)
+    mid_mix = np.array([_r2_mid(r) for r in r2_mix])
+    log(f"equilibration: mixed batched {len(melts)} melts in {t_mix:.1f} s")
+    fp = []
+    for i in range(2):
+        t, r2, _ = run_protocol(kg, torch, ref, [melts[i]], kg.KG_FP64, sample=True)
+        fp.append((t, _r2_mid(r2[0])))
+    t_fp = sum(t for t, _ in fp) / len(fp)
+    log(f"equilibration: binary64 one melt per context {t_fp:.1f} s per melt")
+    d = mid_mix - oracle_mid
+    sample_dt = S["sample_every"] * S["dt"]
+    lags_tau = [50, 100, 200, 400]
+    acf = _ree_acf(ree_mix, [int(round(L / sample_dt)) for L in lags_tau])
+    mph_mix = 3600.0 * len(melts) / t_mix
+    mph_fp = 3600.0 / t_fp
+    return {"workload": f"{len(melts)} melts of {S['n_chains']} chains x N={S['chain_len']}, kappa={S['kappa']}, "
+                        f"rho={S['rho']}",
+            "protocol": f"dt ramp in n = 2, then the paper's 12 stages (scheme 1) scaled by {S['scale']} at "
+                        f"dt = {S['dt']}; {sum(int(x[1]) for x in ref['stages'])} steps; DB at R_MC",
+            "criterion": "<R^2(n)>/n over N/4..N/2 within 1% of the oracle's value on the same melts and protocol",
+            "oracle_r2_mid": float(oracle_mid.mean()),
+            "mixed_batched": {"melts": len(melts), "wall_s": t_mix, "melts_per_hour": mph_mix,
+                              "r2_mid": float(mid_mix.mean()),
+                              "rel_to_oracle": float(mid_mix.mean() / oracle_mid.mean() - 1.0),
+                              "paired_z": float(d.mean() / (d.std(ddof=1) / np.sqrt(len(d)))),
+                              "meets_criterion": bool(abs(mid_mix.mean() / oracle_mid.mean() - 1.0) < 0.01)},
+            "fp64_plain": {"melts_timed": len(fp), "wall_s_per_melt": t_fp, "melts_per_hour": mph_fp,
+                           "r2_mid_melts_0_1": [m for _, m in fp],
+                           "oracle_r2_mid_melts_0_1": oracle_mid[:2].tolist()},
+            "melts_per_hour_ratio": mph_mix / mph_fp,
+            "ree_autocorrelation": {"lag_tau": lags_tau, "C": acf,
+                                    "wall_s_per_tau_mixed_batched_per_melt": t_mix / len(melts) /
+                                    (sum(int(x[1]) * x[2] for x in ref["stages"])),
+                                    "wall_s_per_tau_fp64_plain": t_fp / (sum(int(x[1]) * x[2] for x in ref["stages"]))}}
 
 
 def secondary(kg, torch, args, local):
@@ -736,62 +864,68 @@ DBS_KAPPAS = [1.0, 1.5, 2.0, 2.5, 3.0, 3.5]
 DBS_STAGES = [2.0, 3.0, 4.0, 5.0, 5.75, 6.5, 7.0, 8.0, 9.0]
 
 
-def db_success(args):
-    """Double-bridging success rate per admissible attempt against Eq. 15,
-    S = 1.6 exp(-0.77 kappa - 0.35 n) (Sec. II.B, Fig. 3): melts of 50
-    chains x N = 400 at kappa = 1 ... 3.5 share one mixed context; after a dt
-    ramp each stage n of Xi up to 9 relaxes for 2000 steps, then 30 rounds of
-    100 MD steps and one sweep of M attempts per melt count admissible
-    attempts (a drawn bond with a non-empty partner set) and accepted swaps.
-    Run with the exact Metropolis-Hastings acceptance and with the paper's
-    plain Metropolis (KG_FLAG_PAPER_METROPOLIS)."""
-    import torch
-
+def measure_db_success(kg, torch, kappas, stages, rounds=30, flags=0, n_chains=50, N=400):
+    """Success rate per admissible double-bridging attempt (Sec. II.B, Fig. 3):
+    melts of n_chains x N at each kappa share one mixed context; after a dt
+    ramp each stage n relaxes for 2000 steps, then `rounds` rounds of 100 MD
+    steps and one sweep of M attempts per melt count admissible attempts (a
+    drawn bond with a non-empty partner set) and accepted swaps.  Returns the
+    table and the weighted least-squares fit of ln S = ln a - b kappa - d n
+    (weights: accepted counts), the form of Eq. 15."""
     import kg_inputs as KI
-    import paper_2109_11001_gb300 as kg
     s = torch.cuda.current_stream()
     base = KI.SEED_BASE + 7
-    melts = [KI.random_walk_melt(50, 400, 0.85, k, base + 100 * i) for i, k in enumerate(DBS_KAPPAS)]
+    melts = [KI.random_walk_melt(n_chains, N, 0.85, k, base + 100 * i) for i, k in enumerate(kappas)]
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa) for m in melts], precision=kg.KG_MIXED,
+                       seed=29, fene_qmin=FENE_QMIN, flags=flags, skin=0.4)
+    ctx = kg.kg_create(p, 0, s.cuda_stream, kg.torch_allocator())
+    table = []
+    try:
+        kg.kg_set_potential_schedule(ctx, [kg.stage(2.0, 300, 0.0005), kg.stage(2.0, 300, 0.001),
+                                           kg.stage(2.0, 300, 0.002), kg.stage(2.0, 10 ** 15, 0.005)])
+        for i, m in enumerate(melts):
+            kg.kg_load_config(ctx, i, m.x, m.v)
+        kg.kg_step(ctx, 900)
+        for n in stages:
+            dt = 0.005 if n < 5 else 0.008
+            kg.kg_set_potential_schedule(ctx, [kg.stage(n, 10 ** 15, dt)])
+            kg.kg_step(ctx, 2000)
+            adm = np.zeros(len(melts), dtype=np.int64)
+            acc = np.zeros(len(melts), dtype=np.int64)
+            for _ in range(rounds):
+                kg.kg_step(ctx, 100)
+                for i, m in enumerate(melts):
+                    st = kg.kg_db_sweep_k(ctx, [m.M if j == i else 0 for j in range(len(melts))])
+                    adm[i] += st.attempted - st.empty
+                    acc[i] += st.accepted
+            for i, k in enumerate(kappas):
+                table.append({"kappa": k, "n": n, "admissible": int(adm[i]), "accepted": int(acc[i]),
+                              "S": float(acc[i] / max(adm[i], 1)),
+                              "S_eq15": 1.6 * float(np.exp(-0.77 * k - 0.35 * n))})
+    finally:
+        kg.kg_destroy(ctx)
+    rows = [t for t in table if t["accepted"] > 0]
+    A = np.array([[1.0, -t["kappa"], -t["n"]] for t in rows])
+    y = np.array([np.log(t["S"]) for t in rows])
+    w = np.sqrt(np.array([t["accepted"] for t in rows], dtype=np.float64))
+    coef, *_ = np.linalg.lstsq(A * w[:, None], y * w, rcond=None)
+    return table, {"a": float(np.exp(coef[0])), "b": float(coef[1]), "d": float(coef[2])}
+
+
+def db_success(args):
+    """Double-bridging success rate per admissible attempt against Eq. 15,
+    S = 1.6 exp(-0.77 kappa - 0.35 n), over kappa = 1 ... 3.5 and the stages
+    of Xi up to n = 9, with the exact Metropolis-Hastings acceptance and with
+    the paper's plain Metropolis (KG_FLAG_PAPER_METROPOLIS)."""
+    import torch
+
+    import paper_2109_11001_gb300 as kg
     out = {"workload": "6 melts of 50 chains x N=400 (20k monomers each), kappa 1-3.5, rho=0.85, mixed",
            "rounds": 30, "attempts_per_round": "M per melt", "eq15": "S = 1.6 exp(-0.77 kappa - 0.35 n)"}
     for name, flags in (("hastings", 0), ("paper_metropolis", kg.KG_FLAG_PAPER_METROPOLIS)):
-        p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa) for m in melts], precision=kg.KG_MIXED,
-                           seed=29, fene_qmin=FENE_QMIN, flags=flags, skin=0.4)
-        ctx = kg.kg_create(p, 0, s.cuda_stream, kg.torch_allocator())
-        table = []
-        try:
-            kg.kg_set_potential_schedule(ctx, [kg.stage(2.0, 300, 0.0005), kg.stage(2.0, 300, 0.001),
-                                               kg.stage(2.0, 300, 0.002), kg.stage(2.0, 10 ** 15, 0.005)])
-            for i, m in enumerate(melts):
-                kg.kg_load_config(ctx, i, m.x, m.v)
-            kg.kg_step(ctx, 900)
-            for n in DBS_STAGES:
-                dt = 0.005 if n < 5 else 0.008
-                kg.kg_set_potential_schedule(ctx, [kg.stage(n, 10 ** 15, dt)])
-                kg.kg_step(ctx, 2000)
-                adm = np.zeros(len(melts), dtype=np.int64)
-                acc = np.zeros(len(melts), dtype=np.int64)
-                for _ in range(30):
-                    kg.kg_step(ctx, 100)
-                    for i, m in enumerate(melts):
-                        st = kg.kg_db_sweep_k(ctx, [m.M if j == i else 0 for j in range(len(melts))])
-                        adm[i] += st.attempted - st.empty
-                        acc[i] += st.accepted
-                for i, k in enumerate(DBS_KAPPAS):
-                    table.append({"kappa": k, "n": n, "admissible": int(adm[i]), "accepted": int(acc[i]),
-                                  "S": float(acc[i] / max(adm[i], 1)),
-                                  "S_eq15": 1.6 * float(np.exp(-0.77 * k - 0.35 * n))})
-                log(f"db success {name} n={n}: " + " ".join(f"{t['S']:.4f}" for t in table[-len(melts):]))
-        finally:
-            kg.kg_destroy(ctx)
-        # weighted least squares of ln S = ln a - b kappa - d n over kappa >= 1, n <= 9 (weights: accepted)
-        rows = [t for t in table if t["accepted"] > 0]
-        A = np.array([[1.0, -t["kappa"], -t["n"]] for t in rows])
-        y = np.array([np.log(t["S"]) for t in rows])
-        w = np.sqrt(np.array([t["accepted"] for t in rows], dtype=np.float64))
-        coef, *_ = np.linalg.lstsq(A * w[:, None], y * w, rcond=None)
-        out[name] = {"table": table, "fit": {"a": float(np.exp(coef[0])), "b": float(coef[1]), "d": float(coef[2])}}
-        log(f"db success {name}: fit a {np.exp(coef[0]):.3f} b {coef[1]:.3f} d {coef[2]:.3f}")
+        table, fit = measure_db_success(kg, torch, DBS_KAPPAS, DBS_STAGES, 30, flags)
+        out[name] = {"table": table, "fit": fit}
+        log(f"db success {name}: fit a {fit['a']:.3f} b {fit['b']:.3f} d {fit['d']:.3f}")
     print(json.dumps({"db_success": out}))
 
 
@@ -863,6 +997,8 @@ def main():
     ap.add_argument("--ncu-db-budget", type=float, default=1e-3, help="DB attempts per monomer in the --ncu-case sweep")
     ap.add_argument("--ncu-n", type=float, default=2.0, help="stage exponent n of the --ncu-case steps")
     ap.add_argument("--ppa-case", type=int, default=0, help="primitive-path steps of a capture run (0: off)")
+    ap.add_argument("--equilibration", action="store_true",
+                    help="run only the equilibrated-melts-per-hour comparison and print its JSON")
     ap.add_argument("--db-success", action="store_true",
                     help="measure the DB success rate per admissible attempt over kappa and n against Eq. 15")
     args = ap.parse_args()
@@ -874,6 +1010,12 @@ def main():
         return
     if args.db_success:
         db_success(args)
+        return
+    if args.equilibration:
+        import torch
+
+        import paper_2109_11001_gb300 as kg
+        print(json.dumps({"equilibration": equilibration_secondary(kg, torch, args, 0)}))
         return
     if args.warmup < 3:
         args.warmup = 3

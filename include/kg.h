@@ -66,8 +66,16 @@ enum {
 
 /* kg_params.flags */
 enum {
-    KG_FLAG_PAPER_METROPOLIS = 1  /* accept DB swaps with exp(-dE/T) alone (Fig. 1),
+    KG_FLAG_PAPER_METROPOLIS = 1, /* accept DB swaps with exp(-dE/T) alone (Fig. 1),
                                       without the proposal ratio                      */
+    KG_FLAG_PERSISTENT = 2        /* KG_MIXED (ignored with KG_FP64): kg_step advances
+                                      every melt in persistent cooperative launches of
+                                      50 steps, each held in a captured CUDA graph; the
+                                      Verlet rebuild runs inside the launch between grid
+                                      barriers, and every barrier wait is bounded (a
+                                      block that gives up latches KG_ERR_TIMEOUT).  One
+                                      thread per monomer; results equal the default
+                                      path's up to binary32 summation order            */
 };
 
 /* One melt (Sec. II.B): N_ch chains of N monomers in a cube of side L. */
@@ -109,6 +117,10 @@ typedef struct {
     int threads_per_monomer;  /* threads sharing one monomer's step in KG_MIXED: 1 or 2
                                  (<= 0: 1; KG_FP64 always uses 1); results do not
                                  depend on it beyond binary32 summation order           */
+    double cell_scale;        /* Verlet-list cells of side >= cell_scale (r_c + skin),
+                                 1 ... 3 (<= 0: 1): larger cells mean fewer cells to
+                                 bin and sort and more candidates per monomer; lists
+                                 and results do not depend on it                        */
 } kg_params;
 
 /* One stage of the potential schedule (Eqs. 6, 9, 10, 19-20). */
@@ -157,6 +169,15 @@ kg_status kg_load_config(kg_ctx *c, int melt, const double *x, const double *v, 
 
 /* Copy melt `melt`'s state out (any pointer may be NULL). */
 kg_status kg_get_config(kg_ctx *c, int melt, double *x, double *v, int *pid);
+
+/* Self-test of the persistent launch's bounded barrier waits (KG_MIXED
+ * contexts): one persistent launch of two MD steps in which block skip_block
+ * (>= 0) never arrives at the grid barrier, so the other blocks give up after
+ * `spin` polls (about 64 ns apart), latch KG_ERR_TIMEOUT and return; the call
+ * returns that status and the context holds it until the next kg_load_config.
+ * With skip_block < 0 it is an ordinary two-step persistent launch (KG_OK).
+ * No block waits longer than `spin` polls per barrier. */
+kg_status kg_persistent_selftest(kg_ctx *c, int skip_block, unsigned spin);
 
 /* Replace the potential schedule by n_stages stages (copied).  Kernels read
  * the stage parameters from device memory, so a stage change costs one small
@@ -226,6 +247,7 @@ typedef struct {
     double ms_per_step;   /* measured wall time of one MD step with these settings     */
     int trials;           /* configurations timed                                       */
     int threads_per_monomer;  /* 1 or 2 (KG_MIXED; always 1 for KG_FP64)                */
+    double cell_scale;    /* Verlet cell side over (r_c + skin)                          */
 } kg_tuning;
 
 /* Autotuner: for the melts of *p in the states x[m], v[m] ((3, M_m) arrays,
@@ -233,7 +255,8 @@ typedef struct {
  * (graph-captured, after a warm-up of the same length) for every candidate
  * skin in {0.25, 0.3, 0.4, 0.5, 0.6}, block size in {64, 128, 256} and, for
  * KG_MIXED, threads per monomer in {1, 2}, each in a scratch context of its
- * own; return the fastest in *best.  The settings do
+ * own, then the cell side (cell_scale 1.15 and 1.3 of r_c + skin) with the
+ * best of those; return the fastest in *best.  The settings do
  * not change results beyond floating-point summation order.  Synchronises. */
 kg_status kg_autotune(const kg_params *p, const double *const *x, const double *const *v,
                       const kg_stage *stage, int trial_steps, int device, void *stream,

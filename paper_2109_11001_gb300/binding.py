@@ -21,11 +21,12 @@ KG_OK, KG_ERR_INVALID_ARG, KG_ERR_CUDA, KG_ERR_OOM = 0, 1, 2, 3
 KG_ERR_BOND_OVERSTRETCH, KG_ERR_NONFINITE, KG_ERR_CAPACITY, KG_ERR_TIMEOUT, KG_ERR_STATE = 4, 5, 6, 7, 8
 KG_FP64, KG_MIXED = 0, 1
 KG_FLAG_PAPER_METROPOLIS = 1
+KG_FLAG_PERSISTENT = 2
 
 EXPORTS = ["kg_create", "kg_load_config", "kg_get_config", "kg_set_potential_schedule", "kg_step",
            "kg_db_sweep", "kg_db_sweep_k", "kg_observables", "kg_sync", "kg_get_counters",
            "kg_set_counters", "kg_get_nlist", "kg_forces", "kg_profile", "kg_profile_read", "kg_autotune", "kg_kn", "kg_schedule_paper", "kg_destroy",
-           "kg_strerror", "kg_r2n_noalloc", "kg_mlp_set_weights", "kg_mlp_get_weights", "kg_mlp_forward",
+           "kg_strerror", "kg_r2n_noalloc", "kg_persistent_selftest", "kg_mlp_set_weights", "kg_mlp_get_weights", "kg_mlp_forward",
            "kg_mlp_loss_grad", "kg_mlp_log", "kg_mlp_log_read", "kg_mlp_train", "kg_db_sweep_learned",
            "kg_db_sweep_learned_k", "kg_db_proposal", "kg_msd_reset", "kg_msd", "kg_fit_lk",
            "kg_structure_factor", "kg_pair_distribution", "kg_generate_fr", "kg_primitive_path",
@@ -45,7 +46,7 @@ class kg_params(C.Structure):
                 ("db_bond_max", C.c_double), ("r_mc", C.c_double), ("skin", C.c_double),
                 ("fene_qmin", C.c_double), ("seed", C.c_ulonglong), ("sort_interval", C.c_int),
                 ("block_size", C.c_int), ("precision", C.c_int), ("flags", C.c_int),
-                ("threads_per_monomer", C.c_int)]
+                ("threads_per_monomer", C.c_int), ("cell_scale", C.c_double)]
 
 
 class kg_stage(C.Structure):
@@ -63,7 +64,7 @@ class kg_obs(C.Structure):
 
 class kg_tuning(C.Structure):
     _fields_ = [("skin", C.c_double), ("block_size", C.c_int), ("ms_per_step", C.c_double), ("trials", C.c_int),
-                ("threads_per_monomer", C.c_int)]
+                ("threads_per_monomer", C.c_int), ("cell_scale", C.c_double)]
 
 
 class kg_ppa_params(C.Structure):
@@ -130,6 +131,7 @@ def load(path: str = LIB_PATH):
         "kg_destroy": (None, [p]),
         "kg_strerror": (C.c_char_p, [i]),
         "kg_r2n_noalloc": (i, [p, ll, i, i, p, p]),
+        "kg_persistent_selftest": (i, [p, i, C.c_uint]),
         "kg_msd_reset": (i, [p, i]),
         "kg_msd": (i, [p, i, C.POINTER(d)]),
         "kg_fit_lk": (i, [p, i, d, i, i, C.POINTER(d)]),
@@ -377,6 +379,12 @@ def kg_destroy(ctx):
     _ALLOCATORS.pop(ctx.value, None)
 
 
+def kg_persistent_selftest(ctx, skip_block, spin):
+    """Status of a two-step persistent launch whose block `skip_block` skips the
+    grid barrier (see kg.h); returned, not raised."""
+    return load().kg_persistent_selftest(ctx, int(skip_block), int(spin))
+
+
 def kg_r2n_noalloc(x, stride, n_chains, chain_len, out, stream=None):
     return _check(load().kg_r2n_noalloc(ptr(x), int(stride), int(n_chains), int(chain_len), ptr(out), stream),
                   "kg_r2n_noalloc")
@@ -390,11 +398,12 @@ def kg_strerror(status):
 
 def make_params(melts, precision=KG_MIXED, seed=1, T=1.0, gamma=1.0, R0=1.5, l0=0.960897, db_bond_max=1.3,
                 r_mc=1e-3, skin=0.3, flags=0, fene_qmin=0.0, sort_interval=0, block_size=0,
-                threads_per_monomer=0):
+                threads_per_monomer=0, cell_scale=0.0):
     """melts: iterable of (n_chains, chain_len, box, kappa)."""
     arr = (kg_melt * len(melts))(*[kg_melt(int(a), int(b), float(c), float(d)) for a, b, c, d in melts])
     p = kg_params(len(melts), arr, T, gamma, R0, l0, db_bond_max, r_mc, skin, float(fene_qmin), int(seed),
-                  int(sort_interval), int(block_size), int(precision), int(flags), int(threads_per_monomer))
+                  int(sort_interval), int(block_size), int(precision), int(flags), int(threads_per_monomer),
+                  float(cell_scale))
     p._keep = arr
     return p
 

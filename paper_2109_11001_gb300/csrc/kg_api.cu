@@ -250,6 +250,8 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     SimDev &S = c->sim;
     S.n_melts = p->n_melts;
     const double rl = RC + c->p.skin;
+    const double cscale = p->cell_scale > 0 ? p->cell_scale : 1.0;
+    if (!(cscale >= 1.0 && cscale <= 3.0)) return fail(KG_ERR_INVALID_ARG);
     long long M = 0, ncell = 0, ndbcell = 0, nchain = 0;
     for (int m = 0; m < p->n_melts; ++m) {
         const kg_melt &ml = c->melts[m];
@@ -261,7 +263,7 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
         md.M = ml.n_chains * ml.chain_len;
         md.L = ml.box; md.invL = 1.0 / ml.box; md.Lf = (float)ml.box;
         md.kappa = ml.kappa; md.kappaf = (float)ml.kappa;
-        md.nc = (int)std::floor(ml.box / (rl * (1.0 + 1e-9)));
+        md.nc = (int)std::floor(ml.box / (cscale * rl * (1.0 + 1e-9)));
         md.ndb = (int)std::floor(ml.box / (p->db_bond_max * (1.0 + 1e-9)));
         if (md.nc < 3 || md.ndb < 3) return fail(KG_ERR_INVALID_ARG);
         md.h = ml.box / md.nc; md.invh = 1.0 / md.h;
@@ -369,6 +371,7 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->db_stats = (long long *)A(4 * kg::MAX_MELTS * sizeof(long long));
     c->scratch = (double *)A(7 * Mp * sizeof(double));
     c->flags = (unsigned *)A(16 * sizeof(unsigned));
+    c->pbar = (unsigned *)A(4 * sizeof(unsigned));
     c->d_step = (long long *)A(sizeof(long long));
     c->fout = (double *)A(3 * Mp * sizeof(double));
     c->partials_cap = (int)(Mp / 128 + 2) * 5;
@@ -421,9 +424,9 @@ void kg_destroy(kg_ctx *c)
                     c->d_io, c->msd_ref};
     for (void *b : bufs) dev_free(c, b);
     dev_free(c, c->d_step);
+    dev_free(c, c->pbar);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-    for (int k = 0; k < 2; ++k)
-        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+    kg::graphs_reset(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -551,7 +554,10 @@ kg_status kg_step(kg_ctx *c, long long n_steps)
                 c->clist_valid = false;
             }
             long long n = 1;
-            if (!c->prof_on && c->use_graphs && chunk - done >= kg::GRAPH_STEPS && kg::md_graph_steps(c, 1))
+            if (!c->prof_on && (c->p.flags & KG_FLAG_PERSISTENT) && c->precision == KG_MIXED &&
+                chunk - done >= kg::PERSIST_STEPS && kg::md_persist_steps(c))
+                n = kg::PERSIST_STEPS;
+            else if (!c->prof_on && c->use_graphs && chunk - done >= kg::GRAPH_STEPS && kg::md_graph_steps(c, 1))
                 n = kg::GRAPH_STEPS;
             else
                 kg::md_step(c);
@@ -568,6 +574,21 @@ kg_status kg_step(kg_ctx *c, long long n_steps)
     KG_TRY(cudaGetLastError());
     unsigned *h = pinned_flags();
     return read_flags(c, h);
+}
+
+kg_status kg_persistent_selftest(kg_ctx *c, int skip_block, unsigned spin)
+{
+    if (!c || c->precision != KG_MIXED || spin < 1) return KG_ERR_INVALID_ARG;
+    if (c->latched != KG_OK) return KG_ERR_STATE;
+    if (cudaSetDevice(c->device) != cudaSuccess) return KG_ERR_CUDA;
+    if (c->d_step_stale) {
+        kg::set_device_step(c, c->step - 1);
+        c->d_step_stale = false;
+    }
+    KG_TRY(kg::persist_launch(c, c->stream, c->cur, 2, skip_block, spin));
+    c->step += 2;
+    kg::md_materialize(c);
+    return read_flags(c, pinned_flags());
 }
 
 static kg_status sweep_impl(kg_ctx *c, const long long *attempts, kg_db_stats *stats, bool learned, double lambda)
@@ -1220,6 +1241,41 @@ kg_status kg_autotune(const kg_params *p, const double *const *x, const double *
             }
         }
         if (out != KG_OK) break;
+    }
+    best->cell_scale = 1.0;
+    const double scales[] = {1.15, 1.3};
+    for (int k = 0; out == KG_OK && best->trials > 0 && k < 2; ++k) {   // the cell side with the best of the rest
+        kg_params q = *p;
+        q.skin = best->skin;
+        q.block_size = best->block_size;
+        q.threads_per_monomer = best->threads_per_monomer;
+        q.cell_scale = scales[k];
+        kg_ctx *c = nullptr;
+        kg_status s = kg_create(&c, &q, device, stream, allocator);
+        if (s == KG_ERR_INVALID_ARG) continue;                   // fewer than three cells per side
+        if (s != KG_OK) { out = s; break; }
+        kg_stage st = *stage;
+        st.n_steps = -1;
+        for (int m = 0; s == KG_OK && m < p->n_melts; ++m) s = kg_load_config(c, m, x[m], v ? v[m] : nullptr, nullptr);
+        if (s == KG_OK) s = kg_set_potential_schedule(c, &st, 1);
+        if (s == KG_OK) s = kg_step(c, trial_steps);
+        float ms = 1e30f;
+        for (int rep = 0; s == KG_OK && rep < 2; ++rep) {
+            float t = 0.f;
+            cudaEventRecord(e0, c->stream);
+            s = kg_step(c, trial_steps);
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = t < ms ? t : ms;
+        }
+        kg_destroy(c);
+        if (s != KG_OK) { out = s; break; }
+        ++best->trials;
+        if (ms / trial_steps < best->ms_per_step) {
+            best->ms_per_step = ms / trial_steps;
+            best->cell_scale = scales[k];
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -49,6 +49,9 @@ struct kg_ctx {
     cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     bool graph_failed = false;
+    cudaGraphExec_t pexec[2] = {nullptr, nullptr};   // persistent launches (KG_FLAG_PERSISTENT)
+    bool persist_failed = false;
+    unsigned *pbar = nullptr;    // grid-barrier words of the persistent launch
     bool use_graphs = true;
     long long graph_replays = 0;
     long long sort_interval = 200;
@@ -135,6 +138,8 @@ void *dev_alloc(kg_ctx *c, size_t bytes);
 void dev_free(kg_ctx *c, void *p);
 
 constexpr int GRAPH_STEPS = 10;          // MD steps per captured graph (even)
+constexpr int PERSIST_STEPS = 50;        // MD steps per persistent launch (even)
+constexpr unsigned PERSIST_SPIN = 1u << 24;   // grid-barrier polls (~64 ns apart) before ERR_TIMEOUT
 constexpr int RS = 8;                    // ints per melt in the DB commit-round array
 
 struct Attempt {
@@ -155,9 +160,13 @@ void bonded_partners(kg_ctx *c);             // bp from slot_of / comp_of
 void md_sort(kg_ctx *c);                     // re-sort the state into the last cell order
 void md_materialize(kg_ctx *c);              // mixed: x <- xb64 + dlt[cur]
 void graphs_reset(kg_ctx *c);                // drop captured step graphs (their arguments changed)
+bool md_persist_steps(kg_ctx *c);            // PERSIST_STEPS steps in one persistent launch (KG_MIXED)
 
 // kg_step.cu
 void step_mixed_launch(kg_ctx *c, cudaStream_t st, int cur);   // the mixed path's fused step kernel
+// K steps of every melt in one cooperative launch; skip_block >= 0 makes that
+// block skip the barriers (self-test of the bounded waits)
+cudaError_t persist_launch(kg_ctx *c, cudaStream_t st, int cur, int K, int skip_block, unsigned spin);
 void to_slots(kg_ctx *c, int melt, const double *in_comp, double *out_dev, int dims);
 void u_to_slots(kg_ctx *c, int melt, double *out_dev);
 void pid_to_slots(kg_ctx *c, int melt, int *out_dev);

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "kg_host.h"
+#include "kg_rebuild.cuh"
 
 namespace kg {
 
@@ -343,58 +344,9 @@ __global__ void __launch_bounds__(256) k_bin_md(const SimDev *__restrict__ Sp, d
                                                const int *__restrict__ slot_of, unsigned *__restrict__ flags)
 {
     if (!flags[1] || flags[0]) return;
-    const SimDev &S = *Sp;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S.M) return;
-    const MeltDev &md = S.melt[melt_of(S, slot_of[s])];
-    const int Mp = S.Mp;
-    double xs[3];
-    if (xb64) {                        // mixed: the build position plus the displacement since
-        const float4 e = dcur[s];
-        xs[0] = xb64[s] + (double)e.x;
-        xs[1] = xb64[Mp + s] + (double)e.y;
-        xs[2] = xb64[2 * Mp + s] + (double)e.z;
-    } else {
-        xs[0] = x[s];
-        xs[1] = x[Mp + s];
-        xs[2] = x[2 * Mp + s];
-    }
-    if (!isfinite(xs[0] + xs[1] + xs[2])) {              // never bin a non-finite position
-        atomicOr((unsigned *)flags, ERR_NONFINITE);
-        return;
-    }
-    if (xb64) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            xb64[d * Mp + s] = xs[d];
-            x[d * Mp + s] = xs[d];     // the band check of the list build reads x
-        }
-    }
-    float off[3];
-    int cell[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const double xd = xs[d];
-        const double w = xd - md.L * floor(xd * md.invL);
-        int c = (int)(w * md.invh);
-        c = c < 0 ? 0 : (c >= md.nc ? md.nc - 1 : c);
-        cell[d] = c;
-        off[d] = (float)(w - (double)c * md.h);
-    }
-    const float4 rb = make_float4(off[0], off[1], off[2], __uint_as_float(pack_code(cell[0], cell[1], cell[2])));
-    recb[s] = rb;
-    if (dcur) {
-        dcur[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        pgcur[s] = make_float4(rb.x + 0.f, rb.y + 0.f, rb.z + 0.f, rb.w);
-    }
-    if (pcur) {
-        const double4_32a p = make_double4_32a(xs[0], xs[1], xs[2], 0.0);
-        pcur[s] = p;
-        xb[s] = p;
-    }
-    const int c = md_cell(md, cell[0], cell[1], cell[2]);
-    cellid[s] = c;
-    rank[s] = atomicAdd(count + c, 1);
+    if (s >= Sp->M) return;
+    bin_md_one(*Sp, s, x, xb64, recb, dcur, pgcur, pcur, xb, cellid, rank, count, slot_of, flags);
 }
 
 // DB grid: cell of each particle from its wrapped position (cells >= 1.3
@@ -491,13 +443,7 @@ __global__ void __launch_bounds__(256) k_scatter(const int *__restrict__ cellid,
 {
     if (flags && (!flags[1] || flags[0])) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= M) return;
-    const int pos = start[cellid[s]] + rank[s];
-    list[pos] = s;
-    if (recs) {
-        const float4 r = recb[s];
-        recs[pos] = make_float4(r.x, r.y, r.z, __int_as_float(s));
-    }
+    if (s < M) scatter_one(s, cellid, rank, start, list, recb, recs);
 }
 
 // within-cell order by slot (deterministic lists), then clear the counts
@@ -507,162 +453,23 @@ __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start,
 {
     if (!flags[1] || flags[0]) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int a = start[c], b = start[c + 1];
-    count[c] = 0;
-    if (b - a > MAX_CELL_OCC) {                    // bounded work: an over-full cell is an error
-        atomicOr(flags, ERR_NL_CAPACITY);
-        return;
-    }
-    for (int k = a + 1; k < b; ++k) {
-        const int v = list[k];
-        const float4 rv = recs[k];
-        int j = k - 1;
-        while (j >= a && list[j] > v) { list[j + 1] = list[j]; recs[j + 1] = recs[j]; --j; }
-        list[j + 1] = v;
-        recs[j + 1] = rv;
-    }
+    if (c < ncell && cellsort_one(c, start, list, recs, count)) atomicOr(flags, ERR_NL_CAPACITY);
 }
 
-// Verlet list of monomer s: every t != s, not 1-2 bonded, with r^2 < (r_c +
-// skin)^2.  Candidates come from the 27 cells around the cell of s; a
-// candidate j of stencil cell (dx, dy, dz) lies at off_j - (off_s - (dx, dy,
-// dz) h) from s with no wrap, because that cell's image sits at (c_s + d) h.
-// This binary32 value decides every pair outside the band [nl_lo, nl_hi),
-// which bounds its rounding error; pairs inside the band are decided by the
-// binary64 distance ((dx*dx + dy*dy) + dz*dz), dx = d - L rint(d/L), exactly
-// as the definition.  Each entry stores j with its stencil code q, the image
-// shift of the pair until the next build.
-//
-// A warp walks the 27 stencil cells in lockstep: for cell q every lane runs
-// the warp's largest count of that cell; lanes past their own count load a
-// clamped (valid) record and mask it.  The candidate loop has no branch but
-// its own: the load index is clamped, the append is a predicated store, and
-// a pair inside the binary64 band is taken provisionally and counted; a lane
-// with band pairs re-walks its row after the stencil, decides each band entry
-// by the binary64 distance and compacts the row in place (order kept).  The
-// candidate's offsets and compute index arrive in one 16-byte load.  All
-// parameters are by-value kernel arguments.
-constexpr int NL_BLOCK = 128;
-
-struct MeltNl {
-    int off, cell_off, nbk, nc;
-    float h, lo, hi;
-    double L;
-};
-
-struct NlArgs {
-    const double *x;         // binary64 positions [3][Mp] (band decisions)
-    const float4 *recb;      // build records of the compute order
-    const float4 *recs;      // the same in cell order, w = compute index
-    const int *start;        // cell starts (cell order)
-    unsigned *nl;            // out: entries j | q << IDX_BITS, column-major [maxnb][Mp]
-    int *nn;                 // out: list lengths
-    unsigned *flags;
-    const int *slot_of;
-    const int4 *bp;          // chain partners (1-2 bonded: y, z)
-    int M, Mp, maxnb, n_melts;
-    double rl2;
-    MeltNl melt[MAX_MELTS];
-};
-
-__device__ __forceinline__ void st_pred(unsigned *addr, unsigned v, bool p)
-{
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.u32 [%0], %1;\n\t}"
-                 ::"l"(addr), "r"(v), "r"((unsigned)p) : "memory");
-}
-
-// binary32 squared distance of the build records of s (ri) and t (rj) for a
-// pair in stencil cell (dx, dy, dz) of s: the same expression as the build's
-__device__ __forceinline__ float nl_r2(float4 ri, float4 rj, int dx, int dy, int dz, float h)
-{
-    const float ox = ri.x - (float)dx * h, oy = ri.y - (float)dy * h, oz = ri.z - (float)dz * h;
-    const float ex = rj.x - ox, ey = rj.y - oy, ez = rj.z - oz;
-    return ex * ex + ey * ey + ez * ez;
-}
-
+// Verlet-list build (the per-monomer work is nlist_one, kg_rebuild.cuh).
+// The last block to finish clears the rebuild request.
 // (128, 10): at most 48 registers; more resident warps hide the candidate
 // loads (tighter caps spill too much, looser ones leave the SM half idle)
+constexpr int NL_BLOCK = 128;
+
 __global__ void __launch_bounds__(NL_BLOCK, 10) k_nlist(const __grid_constant__ NlArgs A)
 {
     __shared__ unsigned go;
     if (threadIdx.x == 0) go = (A.flags[1] && !A.flags[0]) ? 1u : 0u;
     __syncthreads();
     if (!go) return;                                         // block-uniform
-    constexpr unsigned FULL = 0xffffffffu;
     const int s = blockIdx.x * NL_BLOCK + threadIdx.x;
-    const bool live = s < A.M;
-    const int sv = live ? s : A.M - 1;                       // idle lanes read valid memory, write nothing
-    const int slot = __ldg(A.slot_of + sv);
-    int m = 0;
-    while (m + 1 < A.n_melts && slot >= A.melt[m + 1].off) ++m;
-    const MeltNl &md = A.melt[m];
-    const int4 bp = __ldg(A.bp + sv);                        // 1-2 bonded partners: bp.y, bp.z
-    const float4 ri = __ldg(A.recb + sv);
-    const unsigned code = __float_as_uint(ri.w);
-    const int cx = (int)(code & CODE_MASK), cy = (int)((code >> CODE_BITS) & CODE_MASK);
-    const int cz = (int)(code >> (2 * CODE_BITS));
-    const int nc = md.nc, nbk = md.nbk;
-    const float h = md.h, lo = md.lo, hi = md.hi;
-    const int maxnb = A.maxnb, last = A.M - 1;
-    const size_t Mp = (size_t)A.Mp;
-    unsigned *__restrict__ out = A.nl + (live ? s : 0);
-    int cnt = 0, nband = 0;
-    unsigned err = 0;
-#pragma unroll 1
-    for (int dz = -1; dz <= 1; ++dz) {
-        int zz = cz + dz;
-        zz = zz < 0 ? nc - 1 : (zz >= nc ? 0 : zz);
-#pragma unroll 1
-        for (int dy = -1; dy <= 1; ++dy) {
-            int yy = cy + dy;
-            yy = yy < 0 ? nc - 1 : (yy >= nc ? 0 : yy);
-            const int rowb = md.cell_off + (((zz >> 2) * nbk + (yy >> 2)) * nbk << 6) + ((zz & 3) << 4) + ((yy & 3) << 2);
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                int xx = cx + dx;
-                xx = xx < 0 ? nc - 1 : (xx >= nc ? 0 : xx);
-                const int cell = rowb + ((xx >> 2) << 6) + (xx & 3);
-                const int k0 = __ldg(A.start + cell);
-                int n = live ? __ldg(A.start + cell + 1) - k0 : 0;
-                if (n > MAX_CELL_OCC) {
-                    err = ERR_NL_CAPACITY;
-                    n = 0;
-                }
-                const int nmax = __reduce_max_sync(FULL, n);
-                const float ox = ri.x - (float)dx * h, oy = ri.y - (float)dy * h, oz = ri.z - (float)dz * h;
-                const unsigned tag = (unsigned)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) << IDX_BITS;
-                for (int j = 0; j < nmax; ++j) {
-                    const float4 rj = __ldg(A.recs + min(k0 + j, last));
-                    const int t = __float_as_int(rj.w);
-                    const float ex = rj.x - ox, ey = rj.y - oy, ez = rj.z - oz;
-                    const float r2 = ex * ex + ey * ey + ez * ez;
-                    const bool take = (j < n) & (r2 < hi) & (t != s) & (t != bp.y) & (t != bp.z);
-                    nband += (take & (r2 >= lo)) ? 1 : 0;
-                    st_pred(out + (size_t)cnt * Mp, (unsigned)t | tag, take & (cnt < maxnb));
-                    cnt += take ? 1 : 0;
-                }
-            }
-        }
-    }
-    if (nband > 0 && cnt <= maxnb) {                         // rare: decide the band entries in binary64
-        int w = 0;
-        for (int k = 0; k < cnt; ++k) {
-            const unsigned e = out[(size_t)k * Mp];
-            const int t = (int)(e & IDX_MASK), q = (int)(e >> IDX_BITS);
-            const float r2 = nl_r2(ri, __ldg(A.recb + t), q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1, h);
-            const bool keep = r2 < lo || dist2_exact(A.x, A.Mp, md.L, s, t) < A.rl2;
-            if (keep) out[(size_t)(w++) * Mp] = e;
-        }
-        cnt = w;
-    }
-    if (live) {
-        A.nn[s] = cnt < maxnb ? cnt : maxnb;
-        if (cnt > maxnb) {
-            err |= ERR_NL_CAPACITY;
-            atomicMax(A.flags + 3, (unsigned)cnt);
-        }
-    }
+    const unsigned err = nlist_one(A, s);
     if (err) atomicOr(A.flags, err);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -935,7 +742,7 @@ void rebuild_md(kg_ctx *c)
     launch_rebuild(c, c->stream);
 }
 
-static NlArgs nl_args(const kg_ctx *c)
+NlArgs nl_args(const kg_ctx *c)
 {
     NlArgs a{};
     a.x = c->x;
@@ -991,11 +798,50 @@ static void launch_step_kernel(kg_ctx *c, cudaStream_t st, int cur)
 // parameters among them): drop them when those change.
 void graphs_reset(kg_ctx *c)
 {
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
         if (c->gexec[k]) {
             cudaGraphExecDestroy(c->gexec[k]);
             c->gexec[k] = nullptr;
         }
+        if (c->pexec[k]) {
+            cudaGraphExecDestroy(c->pexec[k]);
+            c->pexec[k] = nullptr;
+        }
+    }
+}
+
+// PERSIST_STEPS MD steps as one captured graph holding the persistent
+// cooperative launch (the barrier words reset first); one graph per starting
+// buffer parity.  False if capture or launch is not possible.
+bool md_persist_steps(kg_ctx *c)
+{
+    const int parity = c->cur;
+    if (!c->pexec[parity]) {
+        if (c->persist_failed) return false;
+        if (!c->cap_stream) {
+            if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking) != cudaSuccess) {
+                c->persist_failed = true;
+                return false;
+            }
+        }
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) ok = persist_launch(c, c->cap_stream, parity, PERSIST_STEPS, -1, PERSIST_SPIN) == cudaSuccess;
+        const bool ended = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess;
+        ok = ok && ended && cudaGraphInstantiate(&c->pexec[parity], g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (!ok) {
+            cudaGetLastError();
+            c->pexec[parity] = nullptr;
+            c->persist_failed = true;
+            return false;
+        }
+    }
+    if (cudaGraphLaunch(c->pexec[parity], c->stream) != cudaSuccess) return false;
+    c->launches += 2;                          // barrier reset + the persistent kernel
+    c->cur ^= PERSIST_STEPS & 1;
+    return true;
 }
 
 void set_device_step(kg_ctx *c, long long v)

@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "kg_host.h"
+#include "kg_rebuild.cuh"
 
 namespace kg {
 
@@ -103,15 +104,15 @@ __device__ __forceinline__ int melt_index(const StepArgs &P, int slot)
 // Bond (Eq. 10) and bending (Eq. 4) forces on the monomer whose gather
 // record is pi, from its chain partners bp = (s-2, s-1, s+1, s+2).
 template <int N4>
-__device__ __forceinline__ void bonded32(const StepArgs &P, const MeltStep &md, float4 pi, int4 bp, float3 &F,
-                                         unsigned &err)
+__device__ __forceinline__ void bonded32(const StepArgs &P, const float4 *__restrict__ pcur, const MeltStep &md,
+                                         float4 pi, int4 bp, float3 &F, unsigned &err)
 {
     const bool hm2 = bp.x >= 0, hm1 = bp.y >= 0, hp1 = bp.z >= 0, hp2 = bp.w >= 0;
     float3 rm2 = make_float3(0.f, 0.f, 0.f), rm1 = rm2, rp1 = rm2, rp2 = rm2;
-    if (hm1) rm1 = rec_rel(pi, __ldg(P.pcur + bp.y), md.nc, md.h, md.L, md.invL);
-    if (hm2) rm2 = rec_rel(pi, __ldg(P.pcur + bp.x), md.nc, md.h, md.L, md.invL);
-    if (hp1) rp1 = rec_rel(pi, __ldg(P.pcur + bp.z), md.nc, md.h, md.L, md.invL);
-    if (hp2) rp2 = rec_rel(pi, __ldg(P.pcur + bp.w), md.nc, md.h, md.L, md.invL);
+    if (hm1) rm1 = rec_rel(pi, __ldg(pcur + bp.y), md.nc, md.h, md.L, md.invL);
+    if (hm2) rm2 = rec_rel(pi, __ldg(pcur + bp.x), md.nc, md.h, md.L, md.invL);
+    if (hp1) rp1 = rec_rel(pi, __ldg(pcur + bp.z), md.nc, md.h, md.L, md.invL);
+    if (hp2) rp2 = rec_rel(pi, __ldg(pcur + bp.w), md.nc, md.h, md.L, md.invL);
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         if (side == 0 ? hm1 : hp1) {
@@ -209,45 +210,31 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// TPM threads per monomer (1 or 2, adjacent lanes): the lanes split the list
-// (entries k = sub, sub + TPM, ...); with two, lane 0 adds the bonded terms
-// and lane 1 draws the noise, the forces are combined with a shuffle, and
-// lane 0 writes the state.  The bonded terms and the noise run while the
-// first list chunks stream in.
-// (256, 6): at most 40 registers, 75% occupancy.
-// Dynamic shared memory: per warp two buffers of STEP_CH * 32 entries.
+// One tile of blockDim threads (all threads of the block call it together):
+// the step of the monomers of threads t0 + threadIdx.x.  TPM threads per
+// monomer (1 or 2, adjacent lanes): the lanes split the list (entries k =
+// sub, sub + TPM, ...); with two, lane 0 adds the bonded terms and lane 1
+// draws the noise, the forces are combined with a shuffle, and lane 0 writes
+// the state.  The bonded terms and the noise run while the first list chunks
+// stream in.  buf: this warp's two staging buffers; ph: bit b is the parity
+// of the next completion of buffer b's mbarrier (kept across tiles).
 template <int N4, int TPM>
-__global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepArgs P)
+__device__ __forceinline__ void step_tile(const StepArgs &P, int t0, const float4 *__restrict__ dcur,
+                                          float4 *__restrict__ dnext, const float4 *__restrict__ pcur,
+                                          float4 *__restrict__ pnext, long long step, unsigned *buf,
+                                          uint32_t bar0, uint32_t bar1, uint32_t &ph, const float4 *dk)
 {
     constexpr int MW = 32 / TPM;                 // monomers per warp
     constexpr int CC = STEP_CH * TPM;            // list columns per chunk
     constexpr uint32_t SEG = 4u * MW;            // bytes of one column segment
-    extern __shared__ __align__(128) unsigned step_smem[];
-    __shared__ float4 dk[27];
-    __shared__ __align__(8) unsigned long long bars[2 * 8];
-    __shared__ unsigned stop;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned *buf = step_smem + (size_t)wid * (2 * CC * MW);
-    const uint32_t bar0 = smem_u32(&bars[2 * wid]), bar1 = smem_u32(&bars[2 * wid + 1]);
-    if (threadIdx.x < 27) {
-        const int q = threadIdx.x;
-        dk[q] = make_float4((float)(q % 3 - 1), (float)((q / 3) % 3 - 1), (float)(q / 9 - 1), 0.f);
-    }
-    if (lane == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (threadIdx.x == 0) stop = *(volatile unsigned *)P.flags;    // a latched error stops the run
-    __syncthreads();
-    if (stop) return;                                              // block-uniform
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = t0 + threadIdx.x;
     const int s = t / TPM, sub = t % TPM, im = lane / TPM;
     const bool live = s < P.M;
     const int cnt = live ? __ldg(P.nn + s) : 0;
     const int kmax = __reduce_max_sync(0xffffffffu, cnt);
     const int nch = (kmax + CC - 1) / CC;
-    const int wbase = (blockIdx.x * blockDim.x + wid * 32) / TPM;  // first monomer of the warp
+    const int wbase = (t0 + wid * 32) / TPM;                      // first monomer of the warp
     const unsigned *__restrict__ gsrc = P.nl + wbase;
     const size_t Mp = (size_t)P.Mp;
     auto issue = [&](int c) {                                      // lane 0: chunk c into buffer c & 1
@@ -258,10 +245,10 @@ __global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepA
         for (int k = 0; k < cols; ++k) bulk_g2s(dst + k * SEG, gsrc + (size_t)(c * CC + k) * Mp, SEG, bar);
     };
     if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the buffers
         if (nch > 0) issue(0);
         if (nch > 1) issue(1);
     }
-    const long long step = *P.stepp;
     unsigned err = 0;
     float3 F = make_float3(0.f, 0.f, 0.f), gn = F;
     float4 rb = make_float4(0.f, 0.f, 0.f, 0.f), dc = rb, pi = rb;
@@ -270,13 +257,13 @@ __global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepA
         slot = __ldg(P.slot_of + s);
         m = melt_index(P, slot);
         rb = __ldg(P.recb + s);
-        dc = __ldg(P.dcur + s);
+        dc = __ldg(dcur + s);
         // own record rebuilt from its parts: the same bits the last step wrote to pcur
         pi = make_float4(rb.x + dc.x, rb.y + dc.y, rb.z + dc.z, rb.w);
     }
     const MeltStep &md = P.melt[m];
     if (live) {
-        if (sub == 0) bonded32<N4>(P, md, pi, __ldg(P.bp + s), F, err);
+        if (sub == 0) bonded32<N4>(P, pcur, md, pi, __ldg(P.bp + s), F, err);
         if (sub == TPM - 1)
             gn = gauss3_f(draw(P.seed, m, 0, (unsigned long long)step, (uint32_t)(slot - md.off)));
     }
@@ -286,9 +273,11 @@ __global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepA
     const unsigned self = (unsigned)(live ? s : 0) | (13u << IDX_BITS);
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
-        ok = __all_sync(0xffffffffu, ok && mbar_wait((c & 1) ? bar1 : bar0, (uint32_t)((c >> 1) & 1)));
+        const int b = c & 1;
+        ok = __all_sync(0xffffffffu, ok && mbar_wait(b ? bar1 : bar0, (ph >> b) & 1u));
         if (!ok) break;                                            // warp-uniform
-        const unsigned *cb = buf + (c & 1) * (CC * MW);
+        ph ^= 1u << b;
+        const unsigned *cb = buf + b * (CC * MW);
 #pragma unroll
         for (int j0 = 0; j0 < STEP_CH; j0 += STEP_ILP) {
             if (c * CC + TPM * j0 >= kmax) break;                  // warp-uniform: no lane has entries left
@@ -300,7 +289,7 @@ __global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepA
                 e[i] = c * CC + kk < cnt ? cb[kk * MW + im] : self;
             }
 #pragma unroll
-            for (int i = 0; i < STEP_ILP; ++i) pj[i] = __ldg(P.pcur + (e[i] & IDX_MASK));
+            for (int i = 0; i < STEP_ILP; ++i) pj[i] = __ldg(pcur + (e[i] & IDX_MASK));
 #pragma unroll
             for (int i = 0; i < STEP_ILP; ++i) {
                 const float4 q = dk[e[i] >> IDX_BITS];
@@ -313,17 +302,13 @@ __global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepA
                 F.x += fr * dx; F.y += fr * dy; F.z += fr * dz;
             }
         }
-        __syncwarp();                                              // every lane is done with buffer c & 1
+        __syncwarp();                                              // every lane is done with buffer b
         if (lane == 0 && c + 2 < nch) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // reads before the async refill
             issue(c + 2);
         }
     }
-    if (!ok) {                                                     // a staged chunk never arrived
-        err |= ERR_TIMEOUT;
-        if (lane == 0)                                             // let the copies in flight land
-            for (int c = 0; c < min(nch, 2); ++c) mbar_wait(c & 1 ? bar1 : bar0, 0u);
-    }
+    if (!ok) err |= ERR_TIMEOUT;                                   // a staged chunk never arrived
     if (TPM == 2) {                        // every lane takes part: s is shared by lanes 2i, 2i+1
         F.x += __shfl_xor_sync(0xffffffffu, F.x, 1);
         F.y += __shfl_xor_sync(0xffffffffu, F.y, 1);
@@ -344,13 +329,235 @@ __global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepA
         u[s] = v.x; u[Mpi + s] = v.y; u[2 * Mpi + s] = v.z;
         float4 d = dc;
         d.x += P.dt * v.x; d.y += P.dt * v.y; d.z += P.dt * v.z;
-        P.dnext[s] = d;
-        P.pnext[s] = make_float4(rb.x + d.x, rb.y + d.y, rb.z + d.z, rb.w);
+        dnext[s] = d;
+        pnext[s] = make_float4(rb.x + d.x, rb.y + d.y, rb.z + d.z, rb.w);
         rebuild = d.x * d.x + d.y * d.y + d.z * d.z > P.half_skin2;
         if (!isfinite(v.x + v.y + v.z)) err |= ERR_NONFINITE;
     }
     if (__syncthreads_or(rebuild) && threadIdx.x == 0) atomicOr(P.flags + 1, 1u);
     if (err) atomicOr(P.flags, err);
+}
+
+// per-block setup of the step body: the 27-entry stencil table and each
+// warp's two staging mbarriers
+__device__ __forceinline__ void step_block_setup(float4 *dk, unsigned long long *bars)
+{
+    if (threadIdx.x < 27) {
+        const int q = threadIdx.x;
+        dk[q] = make_float4((float)(q % 3 - 1), (float)((q / 3) % 3 - 1), (float)(q / 9 - 1), 0.f);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+        mbar_init(smem_u32(&bars[2 * w]), 1);
+        mbar_init(smem_u32(&bars[2 * w + 1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+}
+
+// One MD step of every monomer.  (256, 6): at most 40 registers, 75%
+// occupancy.  Dynamic shared memory: per warp two buffers of STEP_CH * 32
+// list entries.
+template <int N4, int TPM>
+__global__ void __launch_bounds__(256, 6) k_step32(const __grid_constant__ StepArgs P)
+{
+    extern __shared__ __align__(128) unsigned step_smem[];
+    __shared__ float4 dk[27];
+    __shared__ __align__(8) unsigned long long bars[2 * 8];
+    __shared__ unsigned stop;
+    step_block_setup(dk, bars);
+    if (threadIdx.x == 0) stop = *(volatile unsigned *)P.flags;    // a latched error stops the run
+    __syncthreads();
+    if (stop) return;                                              // block-uniform
+    const int wid = threadIdx.x >> 5;
+    uint32_t ph = 0;
+    step_tile<N4, TPM>(P, blockIdx.x * blockDim.x, P.dcur, P.dnext, P.pcur, P.pnext, *P.stepp,
+                       step_smem + (size_t)wid * (2 * STEP_CH * 32), smem_u32(&bars[2 * wid]),
+                       smem_u32(&bars[2 * wid + 1]), ph, dk);
+}
+
+// ---------------------------------------------------------------------------
+// persistent launch: K MD steps of every melt in one cooperative kernel.  The
+// blocks stay resident and walk the work in grid-stride loops; a grid barrier
+// separates the step of one timestep from the next and, when a step asked
+// for it, the phases of the Verlet rebuild (bin, scan of the cell counts in
+// two passes, scatter into cell order, in-cell sort, list).  The barrier's
+// last arriver snapshots the error and rebuild words, so every block takes
+// the same decisions.  Every barrier wait is bounded: a block that polls
+// longer than `spin` latches ERR_TIMEOUT and leaves the kernel.
+// ---------------------------------------------------------------------------
+struct PersistArgs {
+    StepArgs st;                 // its dcur/dnext/pcur/pnext are ignored: the buffers alternate below
+    NlArgs nl;
+    const SimDev *sim;           // device copy of the melt table (binning)
+    float4 *dlt[2], *pg[2];      // displacement and gather buffers, ping-pong
+    double *x, *xb64;
+    float4 *recb, *recs;
+    int *cellid, *rank, *ccount, *cstart, *clist, *bsum;
+    int ncell, cur0, K, skip_block;   // skip_block >= 0: that block never arrives (barrier self-test)
+    unsigned *bar;               // [0] arrivals, [1] generation, [2] error word and [3] rebuild word at release
+    unsigned spin;               // barrier polls before giving up
+    long long *stepp;            // device step counter: the last step run
+};
+
+// Grid barrier; false if this block gave up waiting.  *snap receives the
+// error word (bit 0..) and rebuild request as the last arriver saw them.
+__device__ __forceinline__ bool grid_sync(const PersistArgs &A, unsigned *ok_s, uint2 *snap_s)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vb = A.bar;
+        const unsigned g = vb[1];
+        __threadfence();
+        bool ok = true;
+        if (atomicAdd(A.bar, 1u) == gridDim.x - 1) {
+            vb[2] = *(volatile unsigned *)A.st.flags;
+            vb[3] = *((volatile unsigned *)A.st.flags + 1);
+            atomicExch(A.bar, 0u);
+            __threadfence();
+            atomicAdd(A.bar + 1, 1u);
+        } else {
+            unsigned it = 0;
+            while (vb[1] == g) {
+                if (++it > A.spin) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *ok_s = ok ? 1u : 0u;
+        *snap_s = make_uint2(vb[2], vb[3]);
+        if (!ok) atomicOr(A.st.flags, ERR_TIMEOUT);
+    }
+    __syncthreads();
+    return *ok_s != 0;
+}
+
+// exclusive scan of the cell counts, pass 1: segment g of 1024 counts, 256
+// threads x 4; segment total to bsum[g]
+__device__ __forceinline__ void scan_seg(const PersistArgs &A, int g, int *wsum)
+{
+    const int n = A.ncell, i0 = g * 1024 + threadIdx.x * 4;
+    int v[4], tsum = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = i0 + k < n ? A.ccount[i0 + k] : 0;
+        tsum += v[k];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int ws = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += u;
+        }
+        if (lane < (int)(blockDim.x >> 5)) wsum[lane] = ws;
+    }
+    __syncthreads();
+    int run = (w ? wsum[w - 1] : 0) + incl - tsum;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (i0 + k < n) A.cstart[i0 + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == blockDim.x - 1) A.bsum[g] = run;
+    __syncthreads();
+}
+
+// pass 2: add the totals of the preceding segments; cstart[n] = grand total
+__device__ __forceinline__ void scan_fix(const PersistArgs &A, int g, int nseg, int *wsum)
+{
+    if (threadIdx.x < 32) {
+        int acc = 0;
+        for (int b = threadIdx.x; b < g; b += 32) acc += A.bsum[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) wsum[0] = acc;
+    }
+    __syncthreads();
+    const int off = wsum[0], n = A.ncell;
+    for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
+        const int i = g * 1024 + k;
+        if (i < n) A.cstart[i] += off;
+    }
+    if (g == nseg - 1 && threadIdx.x == 0) {
+        int tot = 0;
+        for (int b = 0; b < nseg; ++b) tot += A.bsum[b];
+        A.cstart[n] = tot;
+    }
+    __syncthreads();
+}
+
+constexpr int PERSIST_BLOCK = 256;
+
+// One thread per monomer (the persistent launch does not split lists).
+// (256, 4): at most 64 registers, so the list-build phase keeps its registers.
+template <int N4>
+__global__ void __launch_bounds__(PERSIST_BLOCK, 4) k_persist(const __grid_constant__ PersistArgs A)
+{
+    extern __shared__ __align__(128) unsigned step_smem[];
+    __shared__ float4 dk[27];
+    __shared__ __align__(8) unsigned long long bars[2 * 8];
+    __shared__ unsigned ok_s;
+    __shared__ uint2 snap_s;
+    __shared__ int wsum[32];
+    step_block_setup(dk, bars);
+    const StepArgs &P = A.st;
+    const int wid = threadIdx.x >> 5;
+    unsigned *buf = step_smem + (size_t)wid * (2 * STEP_CH * 32);
+    const uint32_t bar0 = smem_u32(&bars[2 * wid]), bar1 = smem_u32(&bars[2 * wid + 1]);
+    uint32_t ph = 0;
+    const long long base = *(volatile long long *)P.stepp;   // the last step run
+    const int nthreads = gridDim.x * blockDim.x;
+    const int nseg = (A.ncell + 1023) / 1024;
+    if ((int)blockIdx.x == A.skip_block) return;              // barrier self-test: never arrives
+    int it = 0;
+    for (; it < A.K; ++it) {
+        if (!grid_sync(A, &ok_s, &snap_s)) return;
+        if (snap_s.x) break;                                  // a latched error stops the run
+        const int cur = A.cur0 ^ (it & 1);
+        if (snap_s.y) {                                       // Verlet rebuild
+            for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.M; s += nthreads)
+                bin_md_one(*A.sim, s, A.x, A.xb64, A.recb, A.dlt[cur], A.pg[cur], nullptr, nullptr, A.cellid, A.rank,
+                           A.ccount, P.slot_of, P.flags);
+            if (!grid_sync(A, &ok_s, &snap_s)) return;
+            for (int g = blockIdx.x; g < nseg; g += gridDim.x) scan_seg(A, g, wsum);
+            if (!grid_sync(A, &ok_s, &snap_s)) return;
+            for (int g = blockIdx.x; g < nseg; g += gridDim.x) scan_fix(A, g, nseg, wsum);
+            if (!grid_sync(A, &ok_s, &snap_s)) return;
+            for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.M; s += nthreads)
+                scatter_one(s, A.cellid, A.rank, A.cstart, A.clist, A.recb, A.recs);
+            if (!grid_sync(A, &ok_s, &snap_s)) return;
+            for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < A.ncell; c += nthreads)
+                if (cellsort_one(c, A.cstart, A.clist, A.recs, A.ccount)) atomicOr(P.flags, ERR_NL_CAPACITY);
+            if (!grid_sync(A, &ok_s, &snap_s)) return;
+            for (int s0 = blockIdx.x * blockDim.x; s0 < P.Mp; s0 += nthreads) {
+                const unsigned err = nlist_one(A.nl, s0 + threadIdx.x);
+                if (err) atomicOr(P.flags, err);
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                P.flags[1] = 0u;                               // request served (before the next release)
+                P.flags[5] += 1u;                              // Verlet builds completed
+            }
+            if (!grid_sync(A, &ok_s, &snap_s)) return;
+            if (snap_s.x) break;
+        }
+        for (int t0 = blockIdx.x * blockDim.x; t0 < P.M; t0 += nthreads)     // block-uniform tiles
+            step_tile<N4, 1>(P, t0, A.dlt[cur], A.dlt[cur ^ 1], A.pg[cur], A.pg[cur ^ 1], base + 1 + it, buf, bar0,
+                             bar1, ph, dk);
+    }
+    if (!grid_sync(A, &ok_s, &snap_s)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.stepp = base + it;
 }
 
 // 4n of a stage exponent with its own kernel instantiation, 0 otherwise
@@ -375,7 +582,7 @@ static void launch_n4(const StepArgs &a, int tpm, int block, long long M, cudaSt
     else k_step32<N4, 1><<<nb, block, smem, st>>>(a);
 }
 
-void step_mixed_launch(kg_ctx *c, cudaStream_t st, int cur)
+static StepArgs step_args(const kg_ctx *c, int cur)
 {
     const StageDev &sg = c->stage;
     StepArgs a{};
@@ -413,9 +620,15 @@ void step_mixed_launch(kg_ctx *c, cudaStream_t st, int cur)
         const MeltDev &md = c->sim.melt[m];
         a.melt[m] = MeltStep{md.off, md.nc, md.hf, md.Lf, md.invLf, md.kappaf};
     }
+    return a;
+}
+
+void step_mixed_launch(kg_ctx *c, cudaStream_t st, int cur)
+{
+    const StepArgs a = step_args(c, cur);
     const int tpm = c->tpm, blk = c->block;
     const long long M = c->M;
-    switch (n4_of(sg.n)) {
+    switch (n4_of(c->stage.n)) {
         case 8: launch_n4<8>(a, tpm, blk, M, st); break;
         case 12: launch_n4<12>(a, tpm, blk, M, st); break;
         case 16: launch_n4<16>(a, tpm, blk, M, st); break;
@@ -429,6 +642,79 @@ void step_mixed_launch(kg_ctx *c, cudaStream_t st, int cur)
         case 44: launch_n4<44>(a, tpm, blk, M, st); break;
         case 48: launch_n4<48>(a, tpm, blk, M, st); break;
         default: launch_n4<0>(a, tpm, blk, M, st); break;
+    }
+}
+
+NlArgs nl_args(const kg_ctx *c);                 // kg_md.cu
+
+template <int N4>
+static cudaError_t launch_persist(const PersistArgs &a, cudaStream_t st)
+{
+    const size_t smem = (size_t)(PERSIST_BLOCK / 32) * 2 * STEP_CH * 32 * sizeof(unsigned);
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist<N4>, PERSIST_BLOCK, smem);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(per * nsm));
+    cfg.blockDim = dim3(PERSIST_BLOCK);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_persist<N4>, a);
+}
+
+// K steps in one cooperative launch (barrier words reset first); skip_block
+// >= 0 and a short spin are the barrier self-test.
+cudaError_t persist_launch(kg_ctx *c, cudaStream_t st, int cur, int K, int skip_block, unsigned spin)
+{
+    PersistArgs a{};
+    a.st = step_args(c, cur);
+    a.nl = nl_args(c);
+    a.sim = c->d_sim;
+    for (int b = 0; b < 2; ++b) {
+        a.dlt[b] = c->dlt[b];
+        a.pg[b] = c->pg[b];
+    }
+    a.x = c->x;
+    a.xb64 = c->xb64;
+    a.recb = c->recb;
+    a.recs = c->recs;
+    a.cellid = c->cellid;
+    a.rank = c->rank;
+    a.ccount = c->ccount;
+    a.cstart = c->cstart;
+    a.clist = c->clist;
+    a.bsum = c->bsum;
+    a.ncell = c->ncell_md;
+    a.cur0 = cur;
+    a.K = K;
+    a.skip_block = skip_block;
+    a.bar = c->pbar;
+    a.spin = spin;
+    a.stepp = c->d_step;
+    cudaError_t e = cudaMemsetAsync(c->pbar, 0, 4 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    switch (n4_of(c->stage.n)) {
+        case 8: return launch_persist<8>(a, st);
+        case 12: return launch_persist<12>(a, st);
+        case 16: return launch_persist<16>(a, st);
+        case 20: return launch_persist<20>(a, st);
+        case 23: return launch_persist<23>(a, st);
+        case 26: return launch_persist<26>(a, st);
+        case 28: return launch_persist<28>(a, st);
+        case 32: return launch_persist<32>(a, st);
+        case 36: return launch_persist<36>(a, st);
+        case 40: return launch_persist<40>(a, st);
+        case 44: return launch_persist<44>(a, st);
+        case 48: return launch_persist<48>(a, st);
+        default: return launch_persist<0>(a, st);
     }
 }
 

@@ -21,6 +21,10 @@ errors).
   comparisons, correlated) are checked family-wise: at least 85% of them
   within 2 standard errors and none beyond 3.5 (for independent comparisons
   at the null, about 1% of runs would exceed 3.5 somewhere).
+* The 80,000-monomer melt (200 x 400, kappa = 2.5) runs a 100,000-step soft
+  to WCA schedule in mixed and in binary64 on the GPU; <R^2(n)>/n at seven n
+  compare, paired, with standard errors over 10 groups of 20 chains: no |z|
+  beyond 3 and no relative difference beyond 1%.
 """
 import multiprocessing as mp
 
@@ -144,3 +148,57 @@ def test_long_run_statistics_of_batched_mixed_melts_match_the_oracle(kg):
     assert len(z_b) >= 5 and len(z_c) >= 15
     assert np.mean(np.abs(zall) < 2.0) >= 0.85, zall
     assert np.abs(zall).max() < 3.5, zall
+
+
+CFG2_SCHED = [(2.0, 2000, 0.001), (2.0, 10000, 0.004), (4.0, 10000, 0.005), (6.5, 10000, 0.006),
+              (9.0, 10000, 0.008), (12.0, 58000, 0.01)]
+
+
+def test_mixed_matches_binary64_on_the_80k_melt(kg):
+    """200 x 400 (kappa = 2.5): the same 100,000-step schedule in mixed and in
+    binary64 on the GPU; per-chain statistics in 10 groups of 20 chains."""
+    import torch
+    m = KI.make(2)
+    out = {}
+    for name, prec in (("mixed", kg.KG_MIXED), ("fp64", kg.KG_FP64)):
+        p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=prec, seed=23, fene_qmin=0.01)
+        ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+        try:
+            kg.kg_set_potential_schedule(ctx, [kg.stage(n, k, dt) for n, k, dt in CFG2_SCHED])
+            kg.kg_load_config(ctx, 0, m.x, m.v)
+            x = np.zeros_like(m.x)
+            samples = []
+            done = 0
+            for n_st, k_st, dt in CFG2_SCHED:
+                left = k_st
+                while left > 0:
+                    kg.kg_step(ctx, 1000)
+                    kg.kg_db_sweep(ctx, -1.0)
+                    left -= 1000
+                    done += 1000
+                    if n_st == 12.0 and left < 40000:
+                        kg.kg_get_config(ctx, 0, x)
+                        samples.append(x.copy())
+        finally:
+            kg.kg_destroy(ctx)
+        out[name] = np.array(samples)
+    # per chain, time-averaged: squared distances at n = 1, 2, 5, 10, 20, 50, 100
+    ns = [1, 2, 5, 10, 20, 50, 100]
+
+    def per_group(X):
+        S, _, M = X.shape
+        r = X.reshape(S, 3, m.n_chains, m.chain_len)
+        v = []
+        for n in ns:
+            d = r[..., n:] - r[..., :-n]
+            v.append(((d ** 2).sum(axis=1)).mean(axis=(0, 2)) / n)     # per chain
+        v = np.array(v).T                                              # (chains, len(ns))
+        return v.reshape(10, m.n_chains // 10, len(ns)).mean(axis=1)
+    gm, gf = per_group(out["mixed"]), per_group(out["fp64"])
+    z = _z(gm, gf)
+    rel = gm.mean(axis=0) / gf.mean(axis=0) - 1.0
+    print("mixed vs binary64 at n =", ns, "relative", np.round(rel, 5), "z", np.round(z, 2))
+    # seven strongly correlated comparisons: a family-wise bound of 3 (about
+    # 5% of null runs would exceed it somewhere)
+    assert np.abs(z).max() < 3.0, z
+    assert np.abs(rel).max() < 0.01, rel
