@@ -65,10 +65,9 @@ def bytes_per_monomer_at_skin(precision, skin):
 
 
 # DRAM bytes per monomer of the mixed step kernel from one ncu capture of the
-# 1.6M-monomer case at skin 0.5, and the hash of kg_md.cu it was taken on
-# (reported as null once the source changes)
-NCU_TRAFFIC = {"bytes_per_monomer": (263.346944e6 + 58.959104e6) / 1.6e6,
-               "kg_md_sha1": "006f7e8f5bcc2671741c554b534fdd9e05e53dac"}
+# 1.6M-monomer case at skin 0.5, and the hash of the step kernel's source
+# (kg_step.cu) it was taken on (reported as null once the source changes)
+NCU_TRAFFIC = {"bytes_per_monomer": None, "src_sha1": None}
 
 WORKLOADS = {
     "cfg5": dict(index=5, desc="1000 chains x N=1600 (1.6M monomers), kappa=3.5, rho=0.85"),
@@ -89,7 +88,7 @@ def prelude_stages(kg):
 
 
 def src_sha1():
-    with open(os.path.join(ROOT, "paper_2109_11001_gb300", "csrc", "kg_md.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2109_11001_gb300", "csrc", "kg_step.cu"), "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()
 
 
@@ -482,7 +481,7 @@ def run_ours(args, world, rank, local):
     bpm_skin = bytes_per_monomer_at_skin(args.precision, run_skin)
     peak, src = peaks()
     traffic = None
-    if (NCU_TRAFFIC["bytes_per_monomer"] and NCU_TRAFFIC["kg_md_sha1"] == src_sha1()
+    if (NCU_TRAFFIC["bytes_per_monomer"] and NCU_TRAFFIC["src_sha1"] == src_sha1()
             and args.precision == "mixed" and abs(run_skin - 0.5) < 1e-12):
         traffic = NCU_TRAFFIC["bytes_per_monomer"] * m.M
     # the oracle on the same state and stage as the timed region (n = 12,
@@ -596,16 +595,17 @@ KAPPA_SCAN = [(0.0, 100, 200), (0.5, 200, 150), (1.0, 400, 100), (1.5, 800, 50),
 
 def batched_secondary(kg, torch, args, local):
     """Eight melts of a kappa scan (20k-200k monomers each) advanced by the
-    same launches in one context, against the same melts run one context at a
-    time; 4 x (50 MD steps + one DB sweep at R_MC) after the dt-ramped prelude."""
+    same launches in one context (graphs of separate launches, and persistent
+    cooperative launches), against the same melts run one context at a time;
+    4 x (50 MD steps + one DB sweep at R_MC) after the dt-ramped prelude."""
     import kg_inputs as KI
     melts = [KI.random_walk_melt(nch, n, 0.85, kap, 2109110013 + 100 * i)
              for i, (kap, n, nch) in enumerate(KAPPA_SCAN)]
     s = torch.cuda.current_stream()
 
-    def run(ms):
+    def run(ms, flags=0):
         p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa) for m in ms], precision=kg.KG_MIXED,
-                           seed=19, fene_qmin=FENE_QMIN, skin=0.5, block_size=64)
+                           seed=19, fene_qmin=FENE_QMIN, skin=0.5, block_size=64, flags=flags)
         ctx = kg.kg_create(p, local, s.cuda_stream, kg.torch_allocator())
         stages, n_pre = prelude_stages(kg)
         kg.kg_set_potential_schedule(ctx, stages)
@@ -628,12 +628,16 @@ def batched_secondary(kg, torch, args, local):
     M = sum(m.M for m in melts)
     t_batched = run(melts)
     log(f"batched kappa scan: {M} monomers, {t_batched * 1e3:.1f} ms")
+    t_persist = run(melts, kg.KG_FLAG_PERSISTENT)
+    log(f"batched kappa scan, persistent launches: {t_persist * 1e3:.1f} ms")
     t_seq = sum(run([m]) for m in melts)
     log(f"kappa scan one melt at a time: {t_seq * 1e3:.1f} ms")
     units = M * MD_PER_STEP * 4
     return {"workload": "kappa scan: 8 melts, kappa 0-3.5, N 100-800, 50-250 chains, "
                         f"{M} monomers, rho=0.85, skin 0.5, block 64",
             "batched_monomer_steps_per_s": units / t_batched,
+            "batched_persistent_monomer_steps_per_s": units / t_persist,
+            "persistent": "one cooperative launch per 50 MD steps of all eight melts (KG_FLAG_PERSISTENT)",
             "one_melt_at_a_time_monomer_steps_per_s": units / t_seq}
 
 
@@ -749,7 +753,9 @@ def equilibration_secondary(kg, torch, args, local):
                               "r2_mid": float(mid_mix.mean()),
                               "rel_to_oracle": float(mid_mix.mean() / oracle_mid.mean() - 1.0),
                               "paired_z": float(d.mean() / (d.std(ddof=1) / np.sqrt(len(d)))),
-                              "meets_criterion": bool(abs(mid_mix.mean() / oracle_mid.mean() - 1.0) < 0.01)},
+                              "paired_sem_rel": float(d.std(ddof=1) / np.sqrt(len(d)) / oracle_mid.mean()),
+                              "within_1pct": bool(abs(mid_mix.mean() / oracle_mid.mean() - 1.0) < 0.01),
+                              "within_2_sem": bool(abs(d.mean()) < 2 * d.std(ddof=1) / np.sqrt(len(d)))},
             "fp64_plain": {"melts_timed": len(fp), "wall_s_per_melt": t_fp, "melts_per_hour": mph_fp,
                            "r2_mid_melts_0_1": [m for _, m in fp],
                            "oracle_r2_mid_melts_0_1": oracle_mid[:2].tolist()},
@@ -997,6 +1003,7 @@ def main():
     ap.add_argument("--ncu-db-budget", type=float, default=1e-3, help="DB attempts per monomer in the --ncu-case sweep")
     ap.add_argument("--ncu-n", type=float, default=2.0, help="stage exponent n of the --ncu-case steps")
     ap.add_argument("--ppa-case", type=int, default=0, help="primitive-path steps of a capture run (0: off)")
+    ap.add_argument("--batched", action="store_true", help="run only the batched kappa-scan comparison")
     ap.add_argument("--equilibration", action="store_true",
                     help="run only the equilibrated-melts-per-hour comparison and print its JSON")
     ap.add_argument("--db-success", action="store_true",
@@ -1010,6 +1017,12 @@ def main():
         return
     if args.db_success:
         db_success(args)
+        return
+    if args.batched:
+        import torch
+
+        import paper_2109_11001_gb300 as kg
+        print(json.dumps({"batched": batched_secondary(kg, torch, args, 0)}))
         return
     if args.equilibration:
         import torch
