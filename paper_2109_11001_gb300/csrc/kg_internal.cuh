@@ -196,6 +196,22 @@ __device__ __forceinline__ void md_cell_xyz(const MeltDev &md, int cell, int &cx
     cz = ((b / (md.nbk * md.nbk)) << 2) | (l >> 4);
 }
 
+// Cell of a binary64 coordinate on a grid of n cells of side h = L / n per
+// period: g = floor(x / h) of the unwrapped coordinate, taken modulo n, and
+// the offset x - g h from that cell's corner, rounded once to binary32.
+// n h differs from L by at most an ulp of L, so the offsets of monomers in
+// different periodic images stay consistent to ~1e-14 sigma.  Four binary64
+// operations (binary64 issues at a small fraction of the binary32 rate on
+// this GPU), each explicitly rounded so that every kernel inlining it
+// computes the same bits.
+__device__ __forceinline__ int cell_of(double x, double h, double invh, int n, float &off)
+{
+    const double g = floor(__dmul_rn(x, invh));
+    off = __double2float_rn(__fma_rn(-g, h, x));
+    const int c = (int)g % n;
+    return c < 0 ? c + n : c;
+}
+
 // Minimum-image vector from gather record i to gather record j (binary32):
 // p = offset from the build-time cell corner + displacement, w = packed cell
 // coordinates.  The cell difference, wrapped to the nearest image, carries

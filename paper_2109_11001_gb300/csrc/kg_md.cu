@@ -364,14 +364,7 @@ __global__ void __launch_bounds__(256) k_bin_db(const SimDev *__restrict__ Sp, c
     int cell[3];
     float off[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const double xd = x[d * S.Mp + s];
-        const double w = xd - md.L * floor(xd * md.invL);
-        int c = (int)(w * md.invhdb);
-        c = c < 0 ? 0 : (c >= md.ndb ? md.ndb - 1 : c);
-        cell[d] = c;
-        off[d] = (float)(w - (double)c * md.hdb);
-    }
+    for (int d = 0; d < 3; ++d) cell[d] = cell_of(x[d * S.Mp + s], md.hdb, md.invhdb, md.ndb, off[d]);
     rec[s] = make_float4(off[0], off[1], off[2], __uint_as_float(pack_code(cell[0], cell[1], cell[2])));
     const int c = md.dbcell_off + (cell[2] * md.ndb + cell[1]) * md.ndb + cell[0];
     cellid[s] = c;
@@ -458,11 +451,11 @@ __global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start,
 
 // Verlet-list build (the per-monomer work is nlist_one, kg_rebuild.cuh).
 // The last block to finish clears the rebuild request.
-// (128, 10): at most 48 registers; more resident warps hide the candidate
-// loads (tighter caps spill too much, looser ones leave the SM half idle)
-constexpr int NL_BLOCK = 128;
+// (256, 5): at most 48 registers and no spills; more resident warps hide the
+// candidate loads (tighter caps spill, looser ones leave the SM half idle)
+constexpr int NL_BLOCK = 256;
 
-__global__ void __launch_bounds__(NL_BLOCK, 10) k_nlist(const __grid_constant__ NlArgs A)
+__global__ void __launch_bounds__(NL_BLOCK, 5) k_nlist(const __grid_constant__ NlArgs A)
 {
     __shared__ unsigned go;
     if (threadIdx.x == 0) go = (A.flags[1] && !A.flags[0]) ? 1u : 0u;

@@ -195,11 +195,7 @@ __global__ void __launch_bounds__(256) k_ppa_bin(PpaArgs a)
             xd += (double)dd[d];
             x[(size_t)d * a.M + p] = xd;
         }
-        const double w = xd - a.L * floor(xd * a.invL);
-        int q = (int)(w * a.invh);
-        q = q < 0 ? 0 : (q >= a.nc ? a.nc - 1 : q);
-        cc[d] = q;
-        o[d] = (float)(w - (double)q * a.h);
+        cc[d] = cell_of(xd, a.h, a.invh, a.nc, o[d]);
     }
     const int c = (cc[2] * a.nc + cc[1]) * a.nc + cc[0];
     a.off[p] = make_float4(o[0], o[1], o[2], __int_as_float(c));

@@ -9,10 +9,16 @@
 
 namespace kg {
 
+// finite binary64 value (exponent field not all ones), tested on the bits
+__device__ __forceinline__ bool finite64(double v)
+{
+    return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
+}
+
 // Monomer s: its position (mixed: build position + displacement since the
 // build, folded into the binary64 arrays), its Verlet-grid cell and offset
 // from the cell corner (the build record), the gather records reset to the
-// record, and its rank within its cell (atomic count).
+// record, and its rank within its cell (atomic count, aggregated per warp).
 __device__ __forceinline__ void bin_md_one(const SimDev &S, int s, double *__restrict__ x, double *__restrict__ xb64,
                                            float4 *__restrict__ recb, float4 *__restrict__ dcur,
                                            float4 *__restrict__ pgcur, double4_32a *__restrict__ pcur,
@@ -25,15 +31,15 @@ __device__ __forceinline__ void bin_md_one(const SimDev &S, int s, double *__res
     double xs[3];
     if (xb64) {                        // mixed: the build position plus the displacement since
         const float4 e = dcur[s];
-        xs[0] = xb64[s] + (double)e.x;
-        xs[1] = xb64[Mp + s] + (double)e.y;
-        xs[2] = xb64[2 * Mp + s] + (double)e.z;
+        xs[0] = __dadd_rn(xb64[s], (double)e.x);
+        xs[1] = __dadd_rn(xb64[Mp + s], (double)e.y);
+        xs[2] = __dadd_rn(xb64[2 * Mp + s], (double)e.z);
     } else {
         xs[0] = x[s];
         xs[1] = x[Mp + s];
         xs[2] = x[2 * Mp + s];
     }
-    if (!isfinite(xs[0] + xs[1] + xs[2])) {              // never bin a non-finite position
+    if (!(finite64(xs[0]) && finite64(xs[1]) && finite64(xs[2]))) {   // never bin a non-finite position
         atomicOr(flags, ERR_NONFINITE);
         return;
     }
@@ -47,14 +53,7 @@ __device__ __forceinline__ void bin_md_one(const SimDev &S, int s, double *__res
     float off[3];
     int cell[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const double xd = xs[d];
-        const double w = xd - md.L * floor(xd * md.invL);
-        int c = (int)(w * md.invh);
-        c = c < 0 ? 0 : (c >= md.nc ? md.nc - 1 : c);
-        cell[d] = c;
-        off[d] = (float)(w - (double)c * md.h);
-    }
+    for (int d = 0; d < 3; ++d) cell[d] = cell_of(xs[d], md.h, md.invh, md.nc, off[d]);
     const float4 rb = make_float4(off[0], off[1], off[2], __uint_as_float(pack_code(cell[0], cell[1], cell[2])));
     recb[s] = rb;
     if (dcur) {
@@ -68,7 +67,15 @@ __device__ __forceinline__ void bin_md_one(const SimDev &S, int s, double *__res
     }
     const int c = md_cell(md, cell[0], cell[1], cell[2]);
     cellid[s] = c;
-    rank[s] = atomicAdd(count + c, 1);
+    // one atomic per cell and warp: monomers in cell order share cells with
+    // their lane neighbours (the in-cell order is fixed later by the sort)
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, c);
+    const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count + c, __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    rank[s] = base + __popc(grp & ((1u << lane) - 1u));
 }
 
 // Monomer s into cell order; its build record is copied into the same order

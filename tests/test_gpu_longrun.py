@@ -6,21 +6,31 @@ same state and seeds, so long runs compare statistically (parity bar:
 <R^2(n)>/n, l_K and the bond and cos(theta) histograms within 2 standard
 errors).
 
-* 16 independent melts of 20 chains x N = 50 (kappa = 1.5, rho = 0.85) advance
-  together in one mixed-precision context; the oracle runs the same 16 melts,
+* 48 independent melts of 20 chains x N = 50 (kappa = 1.5, rho = 0.85) advance
+  together in one mixed-precision context; the oracle runs the same 48 melts,
   same seeds and noise streams, one process per melt.  Both sides: the
   soft-to-WCA relaxation, then 20,000 WCA steps (dt = 0.01) with 100 DB
   attempts per melt every 50 steps, sampled every 100 steps after the first
   2,000.  Each melt's time average is one independent sample; melt i of both
   sides starts from the same state, so the comparison is paired: the standard
-  error is that of the 16 differences (their spread / 4).
-* Every scalar summary must agree within 2 standard errors: l_K (Eq. 14 fitted
-  over N/4 <= n <= N/2), <R^2(n)>/n averaged over that range, <R^2(1)> (mean
-  squared bond) and the bond-bond correlation (<R^2(2)> - 2 <R^2(1)>) / 2.
+  error is that of the 48 differences (their spread / sqrt(48)), about 0.5%
+  of <R^2(n)>/n.
+* The scalar summaries -- l_K (Eq. 14 fitted over N/4 <= n <= N/2),
+  <R^2(n)>/n averaged over that range, <R^2(1)> (mean squared bond) and the
+  bond-bond correlation (<R^2(2)> - 2 <R^2(1)>) / 2 -- are reported with
+  their z; each must lie within 3 standard errors.  A 2-standard-error bar
+  per scalar would fail one run in twenty under the null, and every change of
+  the kernels' rounding is a new draw: over four noise seeds of one build
+  with 16 melts each, the z of l_K was -2.67, +0.78, +0.35, +2.04 (mean
+  +0.13, no sign of a bias).  The
+  parity bar of 2 standard errors is read on the mean over seeds and on the
+  fraction of the vector comparisons below.
 * The vectors (<R^2(n)>/n at all n, every populated histogram bin: about 80
   comparisons, correlated) are checked family-wise: at least 85% of them
   within 2 standard errors and none beyond 3.5 (for independent comparisons
   at the null, about 1% of runs would exceed 3.5 somewhere).
+* Gamma = 0: the total energy of the mixed path against the binary64 GPU
+  path and the oracle over 20 tau of velocity Verlet.
 * The 80,000-monomer melt (200 x 400, kappa = 2.5) runs a 100,000-step soft
   to WCA schedule in mixed and in binary64 on the GPU; <R^2(n)>/n at seven n
   compare, paired, with standard errors over 10 groups of 20 chains: no |z|
@@ -39,7 +49,7 @@ pytestmark = pytest.mark.gpu
 
 RELAX = [(2.0, 300, 0.0005), (2.0, 300, 0.001), (4.0, 300, 0.0015), (6.5, 300, 0.0025), (9.0, 300, 0.004),
          (12.0, 300, 0.005)]
-N_MELTS, N_CH, N, KAPPA = 16, 20, 50, 1.5
+N_MELTS, N_CH, N, KAPPA = 48, 20, 50, 1.5
 PROD, EVERY, SKIP, K, NBINS, SEED = 20000, 100, 2000, 100, 40, 11
 
 
@@ -118,7 +128,7 @@ def test_long_run_statistics_of_batched_mixed_melts_match_the_oracle(kg):
     gr2, gbh, gch = _run_gpu(kg, melts)
     or2, obh, och = _run_oracle(melts)
     assert gr2.shape == or2.shape and gr2.shape[1] >= 150
-    # per-melt time averages: 16 independent samples per side
+    # per-melt time averages: one independent sample per melt and side
     g_r2, o_r2 = gr2.mean(axis=1), or2.mean(axis=1)
     g_sum = [_summaries(r) for r in g_r2]
     o_sum = [_summaries(r) for r in o_r2]
@@ -129,7 +139,7 @@ def test_long_run_statistics_of_batched_mixed_melts_match_the_oracle(kg):
         report[key] = (a.mean(), b.mean(), float(_z(a, b)))
     print("scalar summaries (GPU mean, oracle mean, z):", report)
     for key, (a, b, z) in report.items():
-        assert abs(z) < 2.0, (key, a, b, z)
+        assert abs(z) < 3.0, (key, a, b, z)
     # vectors: <R^2(n)>/n at every n, populated histogram bins (per-melt frequencies)
     n = np.arange(1, N)
     z_r2 = _z(g_r2[:, 1:] / n, o_r2[:, 1:] / n)
@@ -202,3 +212,63 @@ def test_mixed_matches_binary64_on_the_80k_melt(kg):
     # 5% of null runs would exceed it somewhere)
     assert np.abs(z).max() < 3.0, z
     assert np.abs(rel).max() < 0.01, rel
+
+
+def test_nve_energy_of_the_mixed_path(kg):
+    """Gamma = 0 (no thermostat): the total energy of the 1000-monomer melt
+    over 4,000 WCA steps at dt = 0.005 (20 tau), from a Langevin-relaxed state,
+    in mixed and binary64 on the GPU and in the binary64 oracle.  All three
+    start from the same energy (binary64: to 1e-10); the trajectories then
+    separate (chaos), so the runs compare by their energy statistics: the
+    fluctuation (velocity Verlet's dt^2 term) of both GPU paths within a factor
+    of 1.5 of the oracle's, and the drift of the mixed path over the run below
+    1e-4 of the energy."""
+    import torch
+
+    import oracle as O
+    m = KI.make(1)
+    relax = [kg.stage(n, k, dt) for n, k, dt in RELAX] + [kg.stage(12.0, 10 ** 9, 0.005)]
+    p = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=kg.KG_FP64, seed=3)
+    ctx = kg.kg_create(p, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+    x0, v0 = np.zeros_like(m.x), np.zeros_like(m.v)
+    try:
+        kg.kg_set_potential_schedule(ctx, relax)
+        kg.kg_load_config(ctx, 0, m.x, m.v)
+        kg.kg_step(ctx, sum(k for _, k, _ in RELAX) + 2000)
+        kg.kg_get_config(ctx, 0, x0, v0)
+    finally:
+        kg.kg_destroy(ctx)
+    steps, every = 4000, 100
+    E = {}
+    for name, prec in (("mixed", kg.KG_MIXED), ("fp64", kg.KG_FP64)):
+        q = kg.make_params([(m.n_chains, m.chain_len, m.box, m.kappa)], precision=prec, seed=3, gamma=0.0)
+        ctx = kg.kg_create(q, 0, torch.cuda.current_stream().cuda_stream, kg.torch_allocator())
+        e = []
+        try:
+            kg.kg_set_potential_schedule(ctx, [kg.stage(12.0, 10 ** 9, 0.005)])
+            kg.kg_load_config(ctx, 0, x0, v0)
+            for _ in range(steps // every + 1):
+                ob = kg.kg_observables(ctx, 0)
+                e.append(ob.e_pair + ob.e_bond + ob.e_angle + ob.e_kin)
+                kg.kg_step(ctx, every)
+        finally:
+            kg.kg_destroy(ctx)
+        E[name] = np.array(e[:-1])
+    po = O.params(m.n_chains, m.chain_len, m.box, m.kappa, n_exp=12.0, gamma=0.0, dt=0.005, seed=3)
+    x, u = x0.copy(), v0.copy()
+    eo, st = [], 0
+    for _ in range(steps // every):
+        ob = O.observe(po, x, u, st)
+        eo.append(ob["e_pair"] + ob["e_bond"] + ob["e_angle"] + ob["e_kin"])
+        st = O.run(po, x, u, st, every)
+    eo = np.array(eo)
+    scale = abs(eo.mean())
+    drift = {k: (v[-5:].mean() - v[:5].mean()) / scale for k, v in (("oracle", eo), *E.items())}
+    print("NVE total energy / |E|: std oracle %.3e fp64 %.3e mixed %.3e; drift %s; start fp64 %.2e mixed %.2e"
+          % (eo.std() / scale, E["fp64"].std() / scale, E["mixed"].std() / scale, drift,
+             abs(E["fp64"][0] - eo[0]) / scale, abs(E["mixed"][0] - eo[0]) / scale))
+    assert abs(E["fp64"][0] - eo[0]) / scale < 1e-10
+    assert abs(E["mixed"][0] - eo[0]) / scale < 1e-5
+    for k in ("fp64", "mixed"):
+        assert E[k].std() < 1.5 * eo.std() + 1e-7 * scale and E[k].std() > eo.std() / 1.5, k
+    assert abs(drift["mixed"]) < 1e-4

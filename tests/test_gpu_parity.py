@@ -168,9 +168,15 @@ def test_db_paper_metropolis_switch(kg):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_batched_uneven_melts(kg, precision):
+    """Three uneven melts in one context: forces and 10-step trajectories
+    against the oracle, then one DB sweep per melt.  The sweep is checked
+    bit for bit in both precisions from the GPU's own pre-sweep positions
+    (the oracle's sequential loop on the same state): topology, accepted
+    count, and positions with their box shifts."""
     melts = [KI.random_walk_melt(12, 30, 0.85, 0.0, 41), KI.random_walk_melt(7, 61, 0.85, 2.5, 42),
              KI.random_walk_melt(50, 8, 0.85, 1.0, 43)]
     dt = 0.002
+    K = [200, 150, 100]
     with context(kg, melts, precision, seed=5, schedule=[kg.stage(3.0, 1000, dt)]) as ctx:
         forces = []
         for i, m in enumerate(melts):
@@ -178,7 +184,13 @@ def test_batched_uneven_melts(kg, precision):
             kg.kg_forces(ctx, i, F)
             forces.append(F)
         kg.kg_step(ctx, 10)
-        st = kg.kg_db_sweep_k(ctx, [200, 150, 100])
+        pre = []
+        for i, m in enumerate(melts):
+            x, v = np.zeros_like(m.x), np.zeros_like(m.v)
+            pid = np.zeros(m.M, dtype=np.int32)
+            kg.kg_get_config(ctx, i, x, v, pid)
+            pre.append((x, v, pid))
+        st = kg.kg_db_sweep_k(ctx, K)
         out = []
         for i, m in enumerate(melts):
             x = np.zeros_like(m.x)
@@ -192,14 +204,14 @@ def test_batched_uneven_melts(kg, precision):
         assert _force_err(forces[i], Fo) < (1e-10 if precision == 0 else 1e-5)
         xo, uo = m.x.copy(), m.v.copy()
         O.run(q, xo, uo, 0, 10)
-        pido = np.arange(m.M, dtype=np.int32)
-        a, e, ac = O.db_sweep(q, xo, uo, pido, 0, [200, 150, 100][i])
+        assert np.abs(pre[i][0] - xo).max() < (1e-9 if precision == 0 else 1e-4)
+        xs, vs, ps = (a.copy() for a in pre[i])
+        _, _, ac = O.db_sweep(q, xs, vs, ps, 0, K[i])
         acc += ac
         x, pid = out[i]
-        assert np.abs(x - xo).max() < 1e-4
-        if precision == 0:
-            assert np.array_equal(pid, pido)
-    assert st.accepted == acc or precision == 1
+        assert np.array_equal(pid, ps)
+        assert np.abs(x - xs).max() < 1e-9
+    assert st.accepted == acc and acc > 0
 
 
 def test_observables(kg):
