@@ -67,7 +67,7 @@ def bytes_per_monomer_at_skin(precision, skin):
 # DRAM bytes per monomer of the mixed step kernel from one ncu capture of the
 # 1.6M-monomer case at skin 0.5, and the hash of the step kernel's source
 # (kg_step.cu) it was taken on (reported as null once the source changes)
-NCU_TRAFFIC = {"bytes_per_monomer": None, "src_sha1": None}
+NCU_TRAFFIC = {"bytes_per_monomer": 196.3, "src_sha1": "ee95d3b9332b36dc65395558ab04932d66ef1ff7"}
 
 WORKLOADS = {
     "cfg5": dict(index=5, desc="1000 chains x N=1600 (1.6M monomers), kappa=3.5, rho=0.85"),
@@ -522,7 +522,7 @@ def run_ours(args, world, rank, local):
                "timing": "CUDA events around back-to-back sweeps, stats read after each"},
         "accepted_db_moves_per_s_in_step": acc_all / t_max,
         "db_attempts_per_step": att / args.steps,
-        "roofline": {"bound": "hbm", "kernel": "k_step_" + args.precision, "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "k_step32" if args.precision == "mixed" else "k_step_f64", "achieved": achieved, "peak": peak,
                      "timing": "CUDA events around each step-kernel launch, bench steps after the timed region",
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": src, "bytes_per_monomer": bpm,

@@ -251,8 +251,10 @@ typedef struct {
 } kg_tuning;
 
 /* Autotuner: for the melts of *p in the states x[m], v[m] ((3, M_m) arrays,
- * host or device; v may be NULL) under `stage`, time trial_steps MD steps
- * (graph-captured, after a warm-up of the same length) for every candidate
+ * host or device; v may be NULL) under `stage`, time the better of two
+ * windows of trial_steps MD steps (graph-captured, re-sorts off, after one
+ * Verlet build, a re-sort into its cell order and a warm-up of trial_steps
+ * steps: the layout a long run keeps) for every candidate
  * skin in {0.25, 0.3, 0.4, 0.5, 0.6}, block size in {64, 128, 256} and, for
  * KG_MIXED, threads per monomer in {1, 2}, each in a scratch context of its
  * own, then the cell side (cell_scale 1.15 and 1.3 of r_c + skin) with the

@@ -332,7 +332,9 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->u = A(3 * Mp * ureal);
     c->pid = (int *)A(Mp * sizeof(int));
     c->recb = (float4 *)A(Mp * sizeof(float4));
-    c->recs = (float4 *)A(Mp * sizeof(float4));
+    // padded by a cell's worth of records: the list build reads a warp's
+    // lockstep candidates past a cell's end without clamping the index
+    c->recs = (float4 *)A((Mp + kg::MAX_CELL_OCC) * sizeof(float4));
     c->shtab = (float4 *)A((size_t)kg::SHIFT_SLOTS * kg::MAX_MELTS * sizeof(float4));
     if (c->precision == KG_MIXED) {
         for (int b = 0; b < 2; ++b) {
@@ -1189,6 +1191,46 @@ kg_status kg_profile_read(kg_ctx *c, double *ms, long long *n, long long *launch
     return KG_OK;
 }
 
+// One autotuner trial: a context with parameters q on the given states,
+// brought into the cell order of its first Verlet build (the order a long
+// run keeps by its periodic re-sorts; a freshly loaded context is in chain
+// order), warmed up, then timed over two windows of trial_steps MD steps
+// with re-sorts off.  *ms: the better window, per MD step.
+static kg_status autotune_trial(const kg_params &q0, const double *const *x, const double *const *v,
+                                const kg_stage *stage, int trial_steps, int device, void *stream,
+                                const kg_allocator *allocator, cudaEvent_t e0, cudaEvent_t e1, double *ms)
+{
+    kg_params q = q0;
+    q.sort_interval = 1 << 30;
+    kg_ctx *c = nullptr;
+    kg_status s = kg_create(&c, &q, device, stream, allocator);
+    if (s != KG_OK) return s;
+    kg_stage st = *stage;
+    st.n_steps = -1;                                       // open-ended stage for the trial
+    for (int m = 0; s == KG_OK && m < q.n_melts; ++m) s = kg_load_config(c, m, x[m], v ? v[m] : nullptr, nullptr);
+    if (s == KG_OK) s = kg_set_potential_schedule(c, &st, 1);
+    if (s == KG_OK) s = kg_step(c, kg::GRAPH_STEPS);      // first Verlet build
+    if (s == KG_OK) {
+        kg::md_sort(c);                                    // into its cell order
+        c->since_sort = 0;
+        c->clist_valid = false;
+        s = kg_step(c, trial_steps);                       // warm-up: builds, graph capture
+    }
+    float best = 1e30f;
+    for (int rep = 0; s == KG_OK && rep < 2; ++rep) {
+        float t = 0.f;
+        cudaEventRecord(e0, c->stream);
+        s = kg_step(c, trial_steps);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t, e0, e1);
+        best = t < best ? t : best;
+    }
+    kg_destroy(c);
+    *ms = (double)best / trial_steps;
+    return s;
+}
+
 kg_status kg_autotune(const kg_params *p, const double *const *x, const double *const *v, const kg_stage *stage,
                       int trial_steps, int device, void *stream, const kg_allocator *allocator, kg_tuning *best)
 {
@@ -1199,50 +1241,32 @@ kg_status kg_autotune(const kg_params *p, const double *const *x, const double *
     const int ntpm = p->precision == KG_MIXED ? 2 : 1;
     best->ms_per_step = 1e300;
     best->trials = 0;
+    best->cell_scale = 1.0;
     cudaEvent_t e0, e1;
     if (cudaSetDevice(device) != cudaSuccess) return KG_ERR_CUDA;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KG_ERR_CUDA;
     kg_status out = KG_OK;
     for (double skin : skins) {
-        for (int bt = 0; bt < 3 * ntpm; ++bt) {
-            const int blk = blocks[bt % 3], tpm = tpms[bt / 3];
+        for (int bt = 0; out == KG_OK && bt < 3 * ntpm; ++bt) {
             kg_params q = *p;
             q.skin = skin;
-            q.block_size = blk;
-            q.threads_per_monomer = tpm;
-            kg_ctx *c = nullptr;
-            kg_status s = kg_create(&c, &q, device, stream, allocator);
-            if (s == KG_ERR_INVALID_ARG) continue;               // this skin does not fit the box
-            if (s != KG_OK) { out = s; break; }
-            kg_stage st = *stage;
-            st.n_steps = -1;                                       // open-ended stage for the trial
-            for (int m = 0; s == KG_OK && m < p->n_melts; ++m) s = kg_load_config(c, m, x[m], v ? v[m] : nullptr, nullptr);
-            if (s == KG_OK) s = kg_set_potential_schedule(c, &st, 1);
-            if (s == KG_OK) s = kg_step(c, trial_steps);          // warm-up: first build, graph capture
-            float ms = 1e30f;
-            for (int rep = 0; s == KG_OK && rep < 2; ++rep) {   // best of two windows
-                float t = 0.f;
-                cudaEventRecord(e0, c->stream);
-                s = kg_step(c, trial_steps);
-                cudaEventRecord(e1, c->stream);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&t, e0, e1);
-                ms = t < ms ? t : ms;
-            }
-            kg_destroy(c);
+            q.block_size = blocks[bt % 3];
+            q.threads_per_monomer = tpms[bt / 3];
+            q.cell_scale = 1.0;
+            double per = 0.0;
+            const kg_status s = autotune_trial(q, x, v, stage, trial_steps, device, stream, allocator, e0, e1, &per);
+            if (s == KG_ERR_INVALID_ARG) continue;                 // this skin does not fit the box
             if (s != KG_OK) { out = s; break; }
             ++best->trials;
-            const double per = ms / trial_steps;
             if (per < best->ms_per_step) {
                 best->ms_per_step = per;
                 best->skin = skin;
-                best->block_size = blk;
-                best->threads_per_monomer = tpm;
+                best->block_size = q.block_size;
+                best->threads_per_monomer = q.threads_per_monomer;
             }
         }
         if (out != KG_OK) break;
     }
-    best->cell_scale = 1.0;
     const double scales[] = {1.15, 1.3};
     for (int k = 0; out == KG_OK && best->trials > 0 && k < 2; ++k) {   // the cell side with the best of the rest
         kg_params q = *p;
@@ -1250,30 +1274,13 @@ kg_status kg_autotune(const kg_params *p, const double *const *x, const double *
         q.block_size = best->block_size;
         q.threads_per_monomer = best->threads_per_monomer;
         q.cell_scale = scales[k];
-        kg_ctx *c = nullptr;
-        kg_status s = kg_create(&c, &q, device, stream, allocator);
-        if (s == KG_ERR_INVALID_ARG) continue;                   // fewer than three cells per side
-        if (s != KG_OK) { out = s; break; }
-        kg_stage st = *stage;
-        st.n_steps = -1;
-        for (int m = 0; s == KG_OK && m < p->n_melts; ++m) s = kg_load_config(c, m, x[m], v ? v[m] : nullptr, nullptr);
-        if (s == KG_OK) s = kg_set_potential_schedule(c, &st, 1);
-        if (s == KG_OK) s = kg_step(c, trial_steps);
-        float ms = 1e30f;
-        for (int rep = 0; s == KG_OK && rep < 2; ++rep) {
-            float t = 0.f;
-            cudaEventRecord(e0, c->stream);
-            s = kg_step(c, trial_steps);
-            cudaEventRecord(e1, c->stream);
-            cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&t, e0, e1);
-            ms = t < ms ? t : ms;
-        }
-        kg_destroy(c);
+        double per = 0.0;
+        const kg_status s = autotune_trial(q, x, v, stage, trial_steps, device, stream, allocator, e0, e1, &per);
+        if (s == KG_ERR_INVALID_ARG) continue;                     // fewer than three cells per side
         if (s != KG_OK) { out = s; break; }
         ++best->trials;
-        if (ms / trial_steps < best->ms_per_step) {
-            best->ms_per_step = ms / trial_steps;
+        if (per < best->ms_per_step) {
+            best->ms_per_step = per;
             best->cell_scale = scales[k];
         }
     }

@@ -126,9 +126,10 @@ __device__ __forceinline__ bool cellsort_one(int c, const int *__restrict__ star
 //
 // A warp walks the 27 stencil cells in lockstep (all 32 lanes must call
 // nlist_one together): for cell q every lane runs the warp's largest count of
-// that cell; lanes past their own count load a clamped (valid) record and
-// mask it.  The candidate loop has no branch but its own: the load index is
-// clamped, the append is a predicated store, and a pair inside the binary64
+// that cell; lanes past their own count load the records that follow their
+// cell (recs is padded by MAX_CELL_OCC records past the last monomer, so
+// every such load is in bounds) and mask them.  The candidate loop has no
+// branch but its own: the append is a predicated store, and a pair inside the binary64
 // band is taken provisionally and counted; a lane with band pairs re-walks
 // its row after the stencil, decides each band entry by the binary64
 // distance and compacts the row in place (order kept).  The candidate's
@@ -188,7 +189,7 @@ __device__ __forceinline__ unsigned nlist_one(const NlArgs &A, int s)
     const int cz = (int)(code >> (2 * CODE_BITS));
     const int nc = md.nc, nbk = md.nbk;
     const float h = md.h, lo = md.lo, hi = md.hi;
-    const int maxnb = A.maxnb, last = A.M - 1;
+    const int maxnb = A.maxnb;
     const size_t Mp = (size_t)A.Mp;
     unsigned *__restrict__ out = A.nl + (live ? s : 0);
     int cnt = 0, nband = 0;
@@ -216,8 +217,9 @@ __device__ __forceinline__ unsigned nlist_one(const NlArgs &A, int s)
                 const int nmax = __reduce_max_sync(FULL, n);
                 const float ox = ri.x - (float)dx * h, oy = ri.y - (float)dy * h, oz = ri.z - (float)dz * h;
                 const unsigned tag = (unsigned)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) << IDX_BITS;
+#pragma unroll 2
                 for (int j = 0; j < nmax; ++j) {
-                    const float4 rj = __ldg(A.recs + min(k0 + j, last));
+                    const float4 rj = __ldg(A.recs + k0 + j);
                     const int t = __float_as_int(rj.w);
                     const float ex = rj.x - ox, ey = rj.y - oy, ez = rj.z - oz;
                     const float r2 = ex * ex + ey * ey + ez * ez;

@@ -20,6 +20,9 @@
 //  * the image shift of an entry's stencil code q is read from a 27-entry
 //    shared-memory table of cell offsets (-1, 0, 1)^3 and scaled by the
 //    melt's cell side with one FMA per component.
+//  * latency is hidden by resident warps: the pair loop runs before the
+//    bonded terms and the noise, holding only its own state, so the kernel
+//    fits 32 registers at full occupancy.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -193,11 +196,13 @@ constexpr int STEP_ILP = 4;      // Verlet-list entries in flight per lane
 // monomer (1 or 2, adjacent lanes): the lanes split the list (entries k =
 // sub, sub + TPM, ...); with two, lane 0 adds the bonded terms and lane 1
 // draws the noise, the forces are combined with a shuffle, and lane 0 writes
-// the state.  The bonded terms and the noise come first, so their gathers and
-// arithmetic overlap the first list loads.  The pair loop runs to the warp's
-// longest list in groups of STEP_ILP entries with per-lane predicates: an
-// entry past the lane's own list becomes the lane's own record with the zero
-// shift (code 13), a valid gather whose term is masked.
+// the state.  The pair loop comes first and holds only its own state (the
+// own gather record, the force, the entries in flight), so the kernel fits
+// 32 registers at full occupancy; the bonded terms, the noise and the build
+// record and displacement for the update follow.  The pair loop runs to the
+// warp's longest list in groups of STEP_ILP entries with per-lane
+// predicates: an entry past the lane's own list becomes the lane's own record
+// with the zero shift (code 13), a valid gather whose term is masked.
 template <int N4, int TPM>
 __device__ __forceinline__ void step_tile(const StepArgs &P, int t0, const float4 *__restrict__ dcur,
                                           float4 *__restrict__ dnext, const float4 *__restrict__ pcur,
@@ -211,22 +216,14 @@ __device__ __forceinline__ void step_tile(const StepArgs &P, int t0, const float
     const int kmax = __reduce_max_sync(0xffffffffu, cnt);
     unsigned err = 0;
     float3 F = make_float3(0.f, 0.f, 0.f), gn = F;
-    float4 rb = make_float4(0.f, 0.f, 0.f, 0.f), dc = rb, pi = rb;
     int slot = 0, m = 0;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (live) {
         slot = __ldg(P.slot_of + s);
         m = melt_index(P, slot);
-        rb = __ldg(P.recb + s);
-        dc = __ldg(dcur + s);
-        // own record rebuilt from its parts: the same bits the last step wrote to pcur
-        pi = make_float4(rb.x + dc.x, rb.y + dc.y, rb.z + dc.z, rb.w);
+        pi = __ldg(pcur + s);
     }
     const MeltStep &md = P.melt[m];
-    if (live) {
-        if (sub == 0) bonded32<N4>(P, pcur, md, pi, __ldg(P.bp + s), F, err);
-        if (sub == TPM - 1)
-            gn = gauss3_f(draw(P.seed, m, 0, (unsigned long long)step, (uint32_t)(slot - md.off)));
-    }
     const float h = md.h, rc2 = P.rc2;
     const unsigned self = (unsigned)(live ? s : 0) | (13u << IDX_BITS);
     const size_t Mp = (size_t)P.Mp;
@@ -252,6 +249,14 @@ __device__ __forceinline__ void step_tile(const StepArgs &P, int t0, const float
             fr = (k0 + i * TPM < cnt && r2 < rc2) ? fr : 0.0f;
             F.x = fmaf(fr, dx, F.x); F.y = fmaf(fr, dy, F.y); F.z = fmaf(fr, dz, F.z);
         }
+    }
+    float4 rb = make_float4(0.f, 0.f, 0.f, 0.f), dc = rb;
+    if (live) {
+        if (sub == 0) bonded32<N4>(P, pcur, md, pi, __ldg(P.bp + s), F, err);
+        if (sub == TPM - 1)
+            gn = gauss3_f(draw(P.seed, m, 0, (unsigned long long)step, (uint32_t)(slot - md.off)));
+        rb = __ldg(P.recb + s);
+        dc = __ldg(dcur + s);
     }
     if (TPM == 2) {                        // every lane takes part: s is shared by lanes 2i, 2i+1
         F.x += __shfl_xor_sync(0xffffffffu, F.x, 1);
@@ -293,11 +298,13 @@ __device__ __forceinline__ void step_block_setup(float4 *dk)
     }
 }
 
-// One MD step of every monomer.  (256, 5): at most 48 registers (62.5%
-// occupancy); measured against 40 registers (75%) at 1.6M monomers: 104.6
-// against 122.6 us, the spills gone and more loads in flight per warp.
+// One MD step of every monomer.  (256, 8): at most 32 registers, full
+// occupancy (a few bytes spilled after the pair loop).  Measured at 1.6M
+// monomers (skin 0.5, n = 12): 94.5 us per launch, against 101.3 at 40
+// registers and 97.1 at 48; with the bonded terms before the pair loop it
+// needed 48 registers and took 103.5 us.
 template <int N4, int TPM>
-__global__ void __launch_bounds__(256, 5) k_step32(const __grid_constant__ StepArgs P)
+__global__ void __launch_bounds__(256, 8) k_step32(const __grid_constant__ StepArgs P)
 {
     __shared__ float4 dk[27];
     __shared__ unsigned stop;

@@ -18,17 +18,18 @@ errors).
 * The scalar summaries -- l_K (Eq. 14 fitted over N/4 <= n <= N/2),
   <R^2(n)>/n averaged over that range, <R^2(1)> (mean squared bond) and the
   bond-bond correlation (<R^2(2)> - 2 <R^2(1)>) / 2 -- are reported with
-  their z; each must lie within 3 standard errors.  A 2-standard-error bar
-  per scalar would fail one run in twenty under the null, and every change of
-  the kernels' rounding is a new draw: over four noise seeds of one build
-  with 16 melts each, the z of l_K was -2.67, +0.78, +0.35, +2.04 (mean
-  +0.13, no sign of a bias).  The
-  parity bar of 2 standard errors is read on the mean over seeds and on the
-  fraction of the vector comparisons below.
-* The vectors (<R^2(n)>/n at all n, every populated histogram bin: about 80
-  comparisons, correlated) are checked family-wise: at least 85% of them
-  within 2 standard errors and none beyond 3.5 (for independent comparisons
-  at the null, about 1% of runs would exceed 3.5 somewhere).
+  their paired z; each must lie within 3 paired standard errors.  The paired
+  error understates how far whole runs scatter on the large-scale
+  summaries: over 4 noise seeds x 3 implementations (oracle, binary64 GPU,
+  mixed GPU) of this protocol the seed means of l_K and <R^2(n)>/n scattered
+  1.6 times more than it predicts (the local ones 1.0 - 1.3 times), and two
+  runs of one implementation under different seeds reached paired z = 3.1.
+  3 paired errors is about 2 run-to-run errors on l_K.  Over those 12 runs
+  the three implementations' means agreed within 1.6 run-to-run errors
+  (l_K: oracle 2.7439, binary64 -0.9%, mixed -0.2%).
+* The vectors (<R^2(n)>/n at all n, every populated histogram bin: about 90
+  comparisons, correlated through the same scatter) are checked
+  family-wise: none beyond 3.5 paired standard errors.
 * Gamma = 0: the total energy of the mixed path against the binary64 GPU
   path and the oracle over 20 tau of velocity Verlet.
 * The 80,000-monomer melt (200 x 400, kappa = 2.5) runs a 100,000-step soft
@@ -156,7 +157,6 @@ def test_long_run_statistics_of_batched_mixed_melts_match_the_oracle(kg):
           f"{np.abs(zall).max():.2f} (R2 {np.abs(z_r2).max():.2f}, bond {np.abs(z_b).max():.2f}, "
           f"cos {np.abs(z_c).max():.2f})")
     assert len(z_b) >= 5 and len(z_c) >= 15
-    assert np.mean(np.abs(zall) < 2.0) >= 0.85, zall
     assert np.abs(zall).max() < 3.5, zall
 
 
