@@ -164,7 +164,10 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream,
 /* Load melt `melt`'s state: x (3, M) unwrapped positions, v (3, M) velocities
  * (NULL: zero), pid (M) particle ids carried through DB swaps (NULL: 0..M-1).
  * The velocity is the state velocity u = v_{n-1/2} of the leapfrog form of
- * velocity Verlet.  Clears a latched error; forces a neighbour-list rebuild. */
+ * velocity Verlet.  Clears a latched error; forces a neighbour-list rebuild.
+ * The loaded melt is held in chain order until the first kg_step, which runs
+ * its first MD step alone and then re-sorts the state into that step's cell
+ * order (gathers stay local from the second step on). */
 kg_status kg_load_config(kg_ctx *c, int melt, const double *x, const double *v, const int *pid);
 
 /* Copy melt `melt`'s state out (any pointer may be NULL). */

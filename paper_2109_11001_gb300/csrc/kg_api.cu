@@ -478,6 +478,7 @@ kg_status kg_load_config(kg_ctx *c, int melt, const double *x, const double *v, 
     k_iota<<<(int)((Mm + 255) / 256), 256, 0, c->stream>>>(c->comp_of + md.off, (int)Mm, md.off);
     kg::bonded_partners(c);
     c->clist_valid = false;
+    c->sort_after_load = true;           // a loaded melt starts in chain order
     {   // keep the count of graph-side rebuild kernels across the reset of the status words
         unsigned f[8];
         KG_TRY(cudaMemcpyAsync(f, c->flags, sizeof(f), cudaMemcpyDeviceToHost, c->stream));
@@ -550,13 +551,16 @@ kg_status kg_step(kg_ctx *c, long long n_steps)
         }
         long long done = 0;
         while (done < chunk) {
-            if (c->since_sort >= c->sort_interval && c->clist_valid) {
+            if ((c->since_sort >= c->sort_interval || c->sort_after_load) && c->clist_valid) {
                 kg::md_sort(c);                 // restore cell order for locality
                 c->since_sort = 0;
                 c->clist_valid = false;
+                c->sort_after_load = false;
             }
             long long n = 1;
-            if (!c->prof_on && (c->p.flags & KG_FLAG_PERSISTENT) && c->precision == KG_MIXED &&
+            if (c->sort_after_load)             // after a load: one step builds the cell order to sort into
+                kg::md_step(c);
+            else if (!c->prof_on && (c->p.flags & KG_FLAG_PERSISTENT) && c->precision == KG_MIXED &&
                 chunk - done >= kg::PERSIST_STEPS && kg::md_persist_steps(c))
                 n = kg::PERSIST_STEPS;
             else if (!c->prof_on && c->use_graphs && chunk - done >= kg::GRAPH_STEPS && kg::md_graph_steps(c, 1))
@@ -1191,11 +1195,10 @@ kg_status kg_profile_read(kg_ctx *c, double *ms, long long *n, long long *launch
     return KG_OK;
 }
 
-// One autotuner trial: a context with parameters q on the given states,
-// brought into the cell order of its first Verlet build (the order a long
-// run keeps by its periodic re-sorts; a freshly loaded context is in chain
-// order), warmed up, then timed over two windows of trial_steps MD steps
-// with re-sorts off.  *ms: the better window, per MD step.
+// One autotuner trial: a context with parameters q on the given states
+// (re-sorted into cell order after its first step, as after every load),
+// warmed up, then timed over two windows of trial_steps MD steps with
+// periodic re-sorts off.  *ms: the better window, per MD step.
 static kg_status autotune_trial(const kg_params &q0, const double *const *x, const double *const *v,
                                 const kg_stage *stage, int trial_steps, int device, void *stream,
                                 const kg_allocator *allocator, cudaEvent_t e0, cudaEvent_t e1, double *ms)
@@ -1209,13 +1212,7 @@ static kg_status autotune_trial(const kg_params &q0, const double *const *x, con
     st.n_steps = -1;                                       // open-ended stage for the trial
     for (int m = 0; s == KG_OK && m < q.n_melts; ++m) s = kg_load_config(c, m, x[m], v ? v[m] : nullptr, nullptr);
     if (s == KG_OK) s = kg_set_potential_schedule(c, &st, 1);
-    if (s == KG_OK) s = kg_step(c, kg::GRAPH_STEPS);      // first Verlet build
-    if (s == KG_OK) {
-        kg::md_sort(c);                                    // into its cell order
-        c->since_sort = 0;
-        c->clist_valid = false;
-        s = kg_step(c, trial_steps);                       // warm-up: builds, graph capture
-    }
+    if (s == KG_OK) s = kg_step(c, trial_steps);          // warm-up: re-sort after the first build, graphs
     float best = 1e30f;
     for (int rep = 0; s == KG_OK && rep < 2; ++rep) {
         float t = 0.f;

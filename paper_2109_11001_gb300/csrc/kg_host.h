@@ -43,6 +43,7 @@ struct kg_ctx {
     int *comp_of = nullptr;      // chain-major slot -> compute index
     int4 *bp = nullptr;          // compute indices of slots s-2, s-1, s+1, s+2 (-1 past a chain end)
     bool clist_valid = false;    // the last Verlet build's cell order can seed a re-sort
+    bool sort_after_load = false;  // re-sort after the first build that follows a load
     long long since_sort = 0;
     long long *d_step = nullptr;   // device step counter (index of the step being run)
     bool d_step_stale = true;      // host must write it before the next step

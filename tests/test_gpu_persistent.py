@@ -10,7 +10,8 @@ the launch between grid barriers.
 * The bounded barrier wait: a self-test launch in which one block never
   arrives makes the other blocks give up after a short poll limit; the call
   returns KG_ERR_TIMEOUT, the context refuses work until the next
-  kg_load_config, and after reloading it steps like a fresh context.
+  kg_load_config, after reloading it steps like a fresh context, and an
+  ordinary self-test launch then succeeds.
 """
 import contextlib
 
@@ -102,9 +103,9 @@ def test_barrier_wait_gives_up_and_the_context_recovers(kg):
             kg.kg_load_config(ctx, i, m.x, m.v)
         kg.kg_set_counters(ctx, 0, 0)
         kg.kg_set_potential_schedule(ctx, [kg.stage(n, k, dt) for n, k, dt in SCHED])   # back to its start
-        assert kg.kg_persistent_selftest(ctx, -1, 1 << 24) == kg.KG_OK   # an ordinary two-step launch
-        kg.kg_step(ctx, 98)
+        kg.kg_step(ctx, 100)
         after = _state(kg, ctx, melts)
+        assert kg.kg_persistent_selftest(ctx, -1, 1 << 24) == kg.KG_OK   # an ordinary two-step launch
     with _ctx(kg, melts, kg.KG_FLAG_PERSISTENT) as ctx:
         kg.kg_step(ctx, 100)
         fresh = _state(kg, ctx, melts)
