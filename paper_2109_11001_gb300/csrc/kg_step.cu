@@ -17,9 +17,11 @@
 //    gets its own straight-line r^-n;
 //  * the pair loop runs to the warp's longest list with per-lane predicates
 //    (no divergent loop exits), ILP list entries in flight;
-//  * the image shift of an entry's stencil code q is read from a 27-entry
-//    shared-memory table of cell offsets (-1, 0, 1)^3 and scaled by the
-//    melt's cell side with one FMA per component.
+//  * the image shift of an entry's stencil code q is read from three
+//    shared-memory word tables of the cell offsets (-1, 0, 1), one per axis
+//    (entry q in bank q: conflict-free, three wavefronts where a float4
+//    table took about five; the L1 data pipe is this kernel's busiest unit)
+//    and scaled by the melt's cell side with one FMA per component;
 //  * latency is hidden by resident warps: the pair loop runs before the
 //    bonded terms and the noise, holding only its own state, so the kernel
 //    fits 32 registers at full occupancy.
@@ -206,7 +208,7 @@ constexpr int STEP_ILP = 4;      // Verlet-list entries in flight per lane
 template <int N4, int TPM>
 __device__ __forceinline__ void step_tile(const StepArgs &P, int t0, const float4 *__restrict__ dcur,
                                           float4 *__restrict__ dnext, const float4 *__restrict__ pcur,
-                                          float4 *__restrict__ pnext, long long step, const float4 *dk)
+                                          float4 *__restrict__ pnext, long long step, const float *dk)
 {
     const int lane = threadIdx.x & 31;
     const int t = t0 + threadIdx.x;
@@ -240,10 +242,10 @@ __device__ __forceinline__ void step_tile(const StepArgs &P, int t0, const float
         for (int i = 0; i < STEP_ILP; ++i) pj[i] = __ldg(pcur + (e[i] & IDX_MASK));
 #pragma unroll
         for (int i = 0; i < STEP_ILP; ++i) {
-            const float4 q = dk[e[i] >> IDX_BITS];
-            const float dx = fmaf(q.x, h, pj[i].x - pi.x);
-            const float dy = fmaf(q.y, h, pj[i].y - pi.y);
-            const float dz = fmaf(q.z, h, pj[i].z - pi.z);
+            const unsigned q = e[i] >> IDX_BITS;
+            const float dx = fmaf(dk[q], h, pj[i].x - pi.x);
+            const float dy = fmaf(dk[32 + q], h, pj[i].y - pi.y);
+            const float dz = fmaf(dk[64 + q], h, pj[i].z - pi.z);
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
             float fr = mlj_fr32<N4>(P, r2);
             fr = (k0 + i * TPM < cnt && r2 < rc2) ? fr : 0.0f;
@@ -289,12 +291,15 @@ __device__ __forceinline__ void step_tile(const StepArgs &P, int t0, const float
     if (err) atomicOr(P.flags, err);
 }
 
-// per-block setup of the step body: the 27-entry stencil table
-__device__ __forceinline__ void step_block_setup(float4 *dk)
+// per-block setup of the step body: the stencil offsets of the 27 codes,
+// one table per axis
+__device__ __forceinline__ void step_block_setup(float *dk)
 {
     if (threadIdx.x < 27) {
         const int q = threadIdx.x;
-        dk[q] = make_float4((float)(q % 3 - 1), (float)((q / 3) % 3 - 1), (float)(q / 9 - 1), 0.f);
+        dk[q] = (float)(q % 3 - 1);
+        dk[32 + q] = (float)((q / 3) % 3 - 1);
+        dk[64 + q] = (float)(q / 9 - 1);
     }
 }
 
@@ -306,7 +311,7 @@ __device__ __forceinline__ void step_block_setup(float4 *dk)
 template <int N4, int TPM>
 __global__ void __launch_bounds__(256, 8) k_step32(const __grid_constant__ StepArgs P)
 {
-    __shared__ float4 dk[27];
+    __shared__ float dk[96];
     __shared__ unsigned stop;
     step_block_setup(dk);
     if (threadIdx.x == 0) stop = *(volatile unsigned *)P.flags;    // a latched error stops the run
@@ -445,7 +450,7 @@ constexpr int PERSIST_BLOCK = 256;
 template <int N4>
 __global__ void __launch_bounds__(PERSIST_BLOCK, 5) k_persist(const __grid_constant__ PersistArgs A)
 {
-    __shared__ float4 dk[27];
+    __shared__ float dk[96];
     __shared__ unsigned ok_s;
     __shared__ uint2 snap_s;
     __shared__ int wsum[32];
