@@ -67,7 +67,7 @@ def bytes_per_monomer_at_skin(precision, skin):
 # DRAM bytes per monomer of the mixed step kernel from one ncu capture of the
 # 1.6M-monomer case at skin 0.5, and the hash of the step kernel's source
 # (kg_step.cu) it was taken on (reported as null once the source changes)
-NCU_TRAFFIC = {"bytes_per_monomer": 196.3, "src_sha1": "ee95d3b9332b36dc65395558ab04932d66ef1ff7"}
+NCU_TRAFFIC = {"bytes_per_monomer": 196.9, "src_sha1": "1ea5171a830ebd703a17b1e2a8f1b447c11522c2"}
 
 WORKLOADS = {
     "cfg5": dict(index=5, desc="1000 chains x N=1600 (1.6M monomers), kappa=3.5, rho=0.85"),
@@ -360,7 +360,7 @@ def run_ours(args, world, rank, local):
         xs, vs = np.zeros_like(m.x), np.zeros_like(m.v)
         kg.kg_get_config(ctx, 0, xs, vs)
         step0, sweep0 = kg.kg_get_counters(ctx)
-        best = kg.kg_autotune(params, [xs], [vs], kg.stage(12.0, -1, DT), 100, local, stream.cuda_stream,
+        best = kg.kg_autotune(params, [xs], [vs], kg.stage(12.0, -1, DT), 200, local, stream.cuda_stream,
                               kg.torch_allocator())
         tuning = {"skin": best.skin, "block_size": best.block_size,
                   "threads_per_monomer": best.threads_per_monomer, "cell_scale": best.cell_scale,

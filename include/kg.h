@@ -261,7 +261,9 @@ typedef struct {
  * skin in {0.25, 0.3, 0.4, 0.5, 0.6}, block size in {64, 128, 256} and, for
  * KG_MIXED, threads per monomer in {1, 2}, each in a scratch context of its
  * own, then the cell side (cell_scale 1.15 and 1.3 of r_c + skin) with the
- * best of those; return the fastest in *best.  The settings do
+ * best of those; return the fastest in *best (a later candidate must be
+ * faster by 0.5% to replace an earlier one, so near-ties keep the smaller
+ * skin, block and cell).  The settings do
  * not change results beyond floating-point summation order.  Synchronises. */
 kg_status kg_autotune(const kg_params *p, const double *const *x, const double *const *v,
                       const kg_stage *stage, int trial_steps, int device, void *stream,

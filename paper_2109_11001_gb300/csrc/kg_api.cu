@@ -1195,6 +1195,11 @@ kg_status kg_profile_read(kg_ctx *c, double *ms, long long *n, long long *launch
     return KG_OK;
 }
 
+// A candidate replaces the best so far only if it is faster by this
+// fraction: trials of nearly equal settings then keep the earlier one (the
+// smaller skin, block and cell) instead of following timing noise.
+constexpr double TUNE_MARGIN = 0.005;
+
 // One autotuner trial: a context with parameters q on the given states
 // (re-sorted into cell order after its first step, as after every load),
 // warmed up, then timed over two windows of trial_steps MD steps with
@@ -1255,7 +1260,7 @@ kg_status kg_autotune(const kg_params *p, const double *const *x, const double *
             if (s == KG_ERR_INVALID_ARG) continue;                 // this skin does not fit the box
             if (s != KG_OK) { out = s; break; }
             ++best->trials;
-            if (per < best->ms_per_step) {
+            if (per < best->ms_per_step * (1.0 - TUNE_MARGIN)) {   // earlier (smaller skin) wins ties
                 best->ms_per_step = per;
                 best->skin = skin;
                 best->block_size = q.block_size;
@@ -1276,7 +1281,7 @@ kg_status kg_autotune(const kg_params *p, const double *const *x, const double *
         if (s == KG_ERR_INVALID_ARG) continue;                     // fewer than three cells per side
         if (s != KG_OK) { out = s; break; }
         ++best->trials;
-        if (per < best->ms_per_step) {
+        if (per < best->ms_per_step * (1.0 - TUNE_MARGIN)) {
             best->ms_per_step = per;
             best->cell_scale = scales[k];
         }
