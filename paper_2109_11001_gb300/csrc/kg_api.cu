@@ -351,6 +351,7 @@ kg_status kg_create(kg_ctx **out, const kg_params *p, int device, void *stream, 
     c->ccount = (int *)A((size_t)c->ncell_md * sizeof(int));
     c->cstart = (int *)A(((size_t)c->ncell_md + 1) * sizeof(int));
     c->clist = (int *)A(Mp * sizeof(int));
+    c->ctmp = (int *)A(Mp * sizeof(int));
     const size_t nbs = (size_t)std::max(c->ncell_md, c->ncell_db) / 1024 + 2;
     c->bsum = (int *)A(nbs * sizeof(int));
     c->nl = (unsigned *)A((size_t)c->maxnb * Mp * sizeof(unsigned));
@@ -417,7 +418,7 @@ void kg_destroy(kg_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *bufs[] = {c->d_sim, c->d_stage, c->x, c->xb64, c->u, c->pid, c->recb, c->recs, c->shtab, c->dlt[0], c->dlt[1],
                     c->pg[0], c->pg[1], c->pos64[0],
-                    c->pos64[1], c->xb, c->cellid, c->rank, c->ccount, c->cstart, c->clist, c->bsum, c->nl,
+                    c->pos64[1], c->xb, c->cellid, c->rank, c->ccount, c->cstart, c->clist, c->ctmp, c->bsum, c->nl,
                     c->nn, c->dbcell, c->dbrank, c->dbcount, c->dbstart, c->dblist, c->dbrec, c->dbmark, c->chain_ver, c->dbround, c->att_ver, c->att,
                     c->koff, c->slot_of,
                     c->comp_of, c->bp, c->img, c->db_stats, c->scratch, c->flags, c->fout, c->partials,

@@ -221,8 +221,7 @@ __global__ void k_scan2(int *__restrict__ out, const int *__restrict__ bsum, int
                         const unsigned *__restrict__ flags);
 __global__ void k_scatter(const int *__restrict__ cellid, const int *__restrict__ rank,
                           const int *__restrict__ start, int *__restrict__ list, int M,
-                          const unsigned *__restrict__ flags, const float4 *__restrict__ recb,
-                          float4 *__restrict__ recs);
+                          const unsigned *__restrict__ flags);
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
@@ -241,8 +240,7 @@ void db_bin(kg_ctx *c, const std::vector<long long> &K)
     const int nb = nblk(c->ncell_db, 1024);
     k_scan1<<<nb, 1024, 0, st>>>(c->dbcount, c->dbstart, c->bsum, c->ncell_db, nullptr);
     k_scan2<<<nb, 1024, 0, st>>>(c->dbstart, c->bsum, c->ncell_db, nb, nullptr);
-    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->dbcell, c->dbrank, c->dbstart, c->dblist, c->M, nullptr,
-                                               nullptr, nullptr);
+    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->dbcell, c->dbrank, c->dbstart, c->dblist, c->M, nullptr);
 }
 
 void db_finish(kg_ctx *c, long long *host_stats)

@@ -70,6 +70,7 @@ struct kg_ctx {
     // Verlet list and its cell grid
     int ncell_md = 0;
     int *cellid = nullptr, *rank = nullptr, *ccount = nullptr, *cstart = nullptr, *clist = nullptr;
+    int *ctmp = nullptr;         // cell-ordered list before the in-cell ranking
     int *bsum = nullptr;         // scan block sums (shared by both grids)
     int maxnb = 0;
     unsigned *nl = nullptr;      // entries j | stencil code << IDX_BITS

@@ -431,22 +431,23 @@ __global__ void __launch_bounds__(1024) k_scan2(int *__restrict__ out, const int
 // contiguous run of single 16-byte loads
 __global__ void __launch_bounds__(256) k_scatter(const int *__restrict__ cellid, const int *__restrict__ rank,
                                                 const int *__restrict__ start, int *__restrict__ list, int M,
-                                                const unsigned *__restrict__ flags,
-                                                const float4 *__restrict__ recb, float4 *__restrict__ recs)
+                                                const unsigned *__restrict__ flags)
 {
     if (flags && (!flags[1] || flags[0])) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < M) scatter_one(s, cellid, rank, start, list, recb, recs);
+    if (s < M) scatter_one(s, cellid, rank, start, list);
 }
 
-// within-cell order by slot (deterministic lists), then clear the counts
-__global__ void __launch_bounds__(256) k_cellsort(const int *__restrict__ start, int *__restrict__ list,
-                                                 float4 *__restrict__ recs, int *__restrict__ count, int ncell,
-                                                 unsigned *__restrict__ flags)
+// within-cell order by compute index (deterministic lists), the records in
+// the same order, the counts cleared (cellrank_one, kg_rebuild.cuh)
+__global__ void __launch_bounds__(256) k_cellrank(const int *__restrict__ cellid, const int *__restrict__ start,
+                                                 const int *__restrict__ tmp, int *__restrict__ list,
+                                                 const float4 *__restrict__ recb, float4 *__restrict__ recs,
+                                                 int *__restrict__ count, int M, unsigned *__restrict__ flags)
 {
     if (!flags[1] || flags[0]) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < ncell && cellsort_one(c, start, list, recs, count)) atomicOr(flags, ERR_NL_CAPACITY);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < M && cellrank_one(p, cellid, start, tmp, list, recb, recs, count)) atomicOr(flags, ERR_NL_CAPACITY);
 }
 
 // Verlet-list build (the per-monomer work is nlist_one, kg_rebuild.cuh).
@@ -769,10 +770,9 @@ static void launch_rebuild(kg_ctx *c, cudaStream_t st)
     const int nb = nblk(c->ncell_md, 1024);
     k_scan1<<<nb, 1024, 0, st>>>(c->ccount, c->cstart, c->bsum, c->ncell_md, c->flags);
     k_scan2<<<nb, 1024, 0, st>>>(c->cstart, c->bsum, c->ncell_md, nb, c->flags);
-    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->cellid, c->rank, c->cstart, c->clist, c->M, c->flags, c->recb,
-                                               c->recs);
-    k_cellsort<<<nblk(c->ncell_md, 256), 256, 0, st>>>(c->cstart, c->clist, c->recs, c->ccount, c->ncell_md,
-                                                       c->flags);
+    k_scatter<<<nblk(c->M, 256), 256, 0, st>>>(c->cellid, c->rank, c->cstart, c->ctmp, c->M, c->flags);
+    k_cellrank<<<nblk(c->M, 256), 256, 0, st>>>(c->cellid, c->cstart, c->ctmp, c->clist, c->recb, c->recs, c->ccount,
+                                                c->M, c->flags);
     k_nlist<<<nblk(c->M, NL_BLOCK), NL_BLOCK, 0, st>>>(nl_args(c));
 }
 

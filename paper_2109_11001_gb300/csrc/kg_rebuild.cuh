@@ -78,39 +78,40 @@ __device__ __forceinline__ void bin_md_one(const SimDev &S, int s, double *__res
     rank[s] = base + __popc(grp & ((1u << lane) - 1u));
 }
 
-// Monomer s into cell order; its build record is copied into the same order
-// (recs, w = the compute index) so that a cell's candidates are one contiguous
-// run of single 16-byte loads.
+// Monomer s into its cell's segment of the cell-ordered list, at its
+// arrival rank (the in-cell order is fixed afterwards).
 __device__ __forceinline__ void scatter_one(int s, const int *__restrict__ cellid, const int *__restrict__ rank,
-                                            const int *__restrict__ start, int *__restrict__ list,
-                                            const float4 *__restrict__ recb, float4 *__restrict__ recs)
+                                            const int *__restrict__ start, int *__restrict__ list)
 {
-    const int pos = start[cellid[s]] + rank[s];
-    list[pos] = s;
-    if (recs) {
-        const float4 r = recb[s];
-        recs[pos] = make_float4(r.x, r.y, r.z, __int_as_float(s));
-    }
+    list[start[cellid[s]] + rank[s]] = s;
 }
 
-// Cell c: within-cell order by compute index (deterministic lists), then its
-// count cleared for the next build.  True if the cell holds more than
-// MAX_CELL_OCC monomers (left unsorted: an error).
-__device__ __forceinline__ bool cellsort_one(int c, const int *__restrict__ start, int *__restrict__ list,
-                                             float4 *__restrict__ recs, int *__restrict__ count)
+// Position p of the cell-ordered list: the monomer the scatter put there
+// (in atomic-arrival order within its cell, tmp) moves to its rank by
+// compute index among its cell's members, with its build record (w = the
+// compute index), so a cell's candidates form one contiguous run in a fixed
+// order (deterministic lists).  A cell's first position clears its count for
+// the next build.  True if the cell holds more than MAX_CELL_OCC monomers
+// (left in arrival order: an error).
+__device__ __forceinline__ bool cellrank_one(int p, const int *__restrict__ cellid, const int *__restrict__ start,
+                                             const int *__restrict__ tmp, int *__restrict__ list,
+                                             const float4 *__restrict__ recb, float4 *__restrict__ recs,
+                                             int *__restrict__ count)
 {
+    const int v = tmp[p];
+    const int c = cellid[v];
     const int a = start[c], b = start[c + 1];
-    count[c] = 0;
-    if (b - a > MAX_CELL_OCC) return true;         // bounded work: an over-full cell is an error
-    for (int k = a + 1; k < b; ++k) {
-        const int v = list[k];
-        const float4 rv = recs[k];
-        int j = k - 1;
-        while (j >= a && list[j] > v) { list[j + 1] = list[j]; recs[j + 1] = recs[j]; --j; }
-        list[j + 1] = v;
-        recs[j + 1] = rv;
+    if (p == a) count[c] = 0;
+    const bool over = b - a > MAX_CELL_OCC;
+    int r = p - a;
+    if (!over) {
+        r = 0;
+        for (int q = a; q < b; ++q) r += tmp[q] < v ? 1 : 0;
     }
-    return false;
+    list[a + r] = v;
+    const float4 rb = recb[v];
+    recs[a + r] = make_float4(rb.x, rb.y, rb.z, __int_as_float(v));
+    return over;
 }
 
 // ---------------------------------------------------------------------------

@@ -337,7 +337,7 @@ struct PersistArgs {
     float4 *dlt[2], *pg[2];      // displacement and gather buffers, ping-pong
     double *x, *xb64;
     float4 *recb, *recs;
-    int *cellid, *rank, *ccount, *cstart, *clist, *bsum;
+    int *cellid, *rank, *ccount, *cstart, *clist, *ctmp, *bsum;
     int ncell, cur0, K, skip_block;   // skip_block >= 0: that block never arrives (barrier self-test)
     unsigned *bar;               // [0] arrivals, [1] generation, [2] error word and [3] rebuild word at release
     unsigned spin;               // barrier polls before giving up
@@ -475,10 +475,11 @@ __global__ void __launch_bounds__(PERSIST_BLOCK, 5) k_persist(const __grid_const
             for (int g = blockIdx.x; g < nseg; g += gridDim.x) scan_fix(A, g, nseg, wsum);
             if (!grid_sync(A, &ok_s, &snap_s)) return;
             for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.M; s += nthreads)
-                scatter_one(s, A.cellid, A.rank, A.cstart, A.clist, A.recb, A.recs);
+                scatter_one(s, A.cellid, A.rank, A.cstart, A.ctmp);
             if (!grid_sync(A, &ok_s, &snap_s)) return;
-            for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < A.ncell; c += nthreads)
-                if (cellsort_one(c, A.cstart, A.clist, A.recs, A.ccount)) atomicOr(P.flags, ERR_NL_CAPACITY);
+            for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.M; p += nthreads)
+                if (cellrank_one(p, A.cellid, A.cstart, A.ctmp, A.clist, A.recb, A.recs, A.ccount))
+                    atomicOr(P.flags, ERR_NL_CAPACITY);
             if (!grid_sync(A, &ok_s, &snap_s)) return;
             for (int s0 = blockIdx.x * blockDim.x; s0 < P.Mp; s0 += nthreads) {    // whole warps
                 const unsigned err = nlist_one(A.nl, s0 + threadIdx.x);
@@ -628,6 +629,7 @@ cudaError_t persist_launch(kg_ctx *c, cudaStream_t st, int cur, int K, int skip_
     a.ccount = c->ccount;
     a.cstart = c->cstart;
     a.clist = c->clist;
+    a.ctmp = c->ctmp;
     a.bsum = c->bsum;
     a.ncell = c->ncell_md;
     a.cur0 = cur;
