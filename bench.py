@@ -64,10 +64,11 @@ def bytes_per_monomer_at_skin(precision, skin):
     return (48 + 24 + 32 if precision == "mixed" else 48 + 48 + 32) + 4 * nb_mean(skin)
 
 
-# DRAM bytes per monomer of the mixed step kernel from one ncu capture of the
-# 1.6M-monomer case at skin 0.5, and the hash of the step kernel's source
-# (kg_step.cu) it was taken on (reported as null once the source changes)
-NCU_TRAFFIC = {"bytes_per_monomer": 196.9, "src_sha1": "1ea5171a830ebd703a17b1e2a8f1b447c11522c2"}
+# DRAM bytes per monomer of the mixed step kernel from ncu captures of the
+# 1.6M-monomer case, by skin, and the hash of the step kernel's source
+# (kg_step.cu) they were taken on (reported as null for another skin or once
+# the source changes)
+NCU_TRAFFIC = {"bytes_per_monomer": {0.5: 196.8, 0.6: 213.9}, "src_sha1": "63835746348d748769c7622c82ff1331f3d77778"}
 
 WORKLOADS = {
     "cfg5": dict(index=5, desc="1000 chains x N=1600 (1.6M monomers), kappa=3.5, rho=0.85"),
@@ -482,9 +483,9 @@ def run_ours(args, world, rank, local):
     bpm_skin = bytes_per_monomer_at_skin(args.precision, run_skin)
     peak, src = peaks()
     traffic = None
-    if (NCU_TRAFFIC["bytes_per_monomer"] and NCU_TRAFFIC["src_sha1"] == src_sha1()
-            and args.precision == "mixed" and abs(run_skin - 0.5) < 1e-12):
-        traffic = NCU_TRAFFIC["bytes_per_monomer"] * m.M
+    bpm_ncu = {round(k, 6): v for k, v in NCU_TRAFFIC["bytes_per_monomer"].items()}.get(round(run_skin, 6))
+    if bpm_ncu and NCU_TRAFFIC["src_sha1"] == src_sha1() and args.precision == "mixed":
+        traffic = bpm_ncu * m.M
     # the oracle on the same state and stage as the timed region (n = 12,
     # dt = DT): one host core alone, then one process per host core at once
     log("oracle sample")
