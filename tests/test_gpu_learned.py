@@ -87,7 +87,9 @@ def test_forward_matches_bf16_network(kg, n):
     assert np.allclose(sd, ref_d, rtol=1e-6, atol=1e-6)
 
 
-@pytest.mark.parametrize("n", [16, 37, 1000])
+# 5000 rows: 313 row tiles, so the weight gradients sum 20 chunks of 256 rows,
+# the last one partial
+@pytest.mark.parametrize("n", [16, 37, 1000, 5000])
 def test_loss_gradient(kg, n):
     rng = np.random.default_rng(10 + n)
     F = rng.normal(size=(n, 24))
