@@ -68,7 +68,7 @@ def bytes_per_monomer_at_skin(precision, skin):
 # 1.6M-monomer case, by skin, and the hash of the step kernel's source
 # (kg_step.cu) they were taken on (reported as null for another skin or once
 # the source changes)
-NCU_TRAFFIC = {"bytes_per_monomer": {0.5: 196.8, 0.6: 213.9}, "src_sha1": "63835746348d748769c7622c82ff1331f3d77778"}
+NCU_TRAFFIC = {"bytes_per_monomer": {0.5: 196.8, 0.6: 213.9}, "src_sha1": "e627455da1f4382bbc2b14cf2e2c30d8d440a189"}
 
 WORKLOADS = {
     "cfg5": dict(index=5, desc="1000 chains x N=1600 (1.6M monomers), kappa=3.5, rho=0.85"),

@@ -1,5 +1,5 @@
 // kg_rebuild.cuh -- per-item work of the Verlet-list rebuild chain (binning,
-// scatter into cell order, in-cell sort, list build), shared by the
+// scatter into cell order, in-cell rank, list build), shared by the
 // standalone rebuild kernels and the persistent step kernel, so both run the
 // same arithmetic.
 #pragma once
@@ -68,7 +68,7 @@ __device__ __forceinline__ void bin_md_one(const SimDev &S, int s, double *__res
     const int c = md_cell(md, cell[0], cell[1], cell[2]);
     cellid[s] = c;
     // one atomic per cell and warp: monomers in cell order share cells with
-    // their lane neighbours (the in-cell order is fixed later by the sort)
+    // their lane neighbours (the in-cell order is fixed later by the rank pass)
     const unsigned act = __activemask();
     const unsigned grp = __match_any_sync(act, c);
     const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;

@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256, 8) k_step32(const __grid_constant__ StepA
 // blocks stay resident and walk the work in grid-stride loops; a grid barrier
 // separates the step of one timestep from the next and, when a step asked
 // for it, the phases of the Verlet rebuild (bin, scan of the cell counts in
-// two passes, scatter into cell order, in-cell sort, list).  The barrier's
+// two passes, scatter into cell order, in-cell rank, list).  The barrier's
 // last arriver snapshots the error and rebuild words, so every block takes
 // the same decisions.  Every barrier wait is bounded: a block that polls
 // longer than `spin` latches ERR_TIMEOUT and leaves the kernel.
