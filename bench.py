@@ -857,7 +857,7 @@ def learned_secondary(kg, torch, args, local):
     kg.kg_set_potential_schedule(ctx, [kg.stage(n, k, dt) for n, k, dt in LEARNED_STAGES])
     kg.kg_load_config(ctx, 0, m.x, m.v)
     kg.kg_step(ctx, 1200)
-    K = m.M // 20
+    K = m.M // 5                                  # ~0.3% of draws are admissible at N = 800: ~20 swaps a sweep
     lam = 0.1
     kg.kg_mlp_log(ctx, 4_000_000)
     ev = lambda: torch.cuda.Event(enable_timing=True)

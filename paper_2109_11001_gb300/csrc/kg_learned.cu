@@ -132,17 +132,22 @@ __device__ void move_features(const DBC &C, const V &v, int c, int b, const Cand
 }
 
 // Proposal weights of bond (c, b) in view v: wp.cand[0..n), wp.pi, and (when
-// `features` or the network is in use) wp.dE and wp.F.  log_att >= 0 writes the
+// `features` or the network is in use) wp.dE and wp.F; wp.s (the logits) when
+// the network ran (lambda < 1 and n > 1, or `logits`).  log_att >= 0 writes the
 // FP64 features and targets min(1, exp(-dE/T)) of every candidate to that
 // attempt's log rows.  Returns n (0: empty, -1: capacity error).
 template <class V>
 __device__ int proposal(const DBC &C, const V &v, const MlpSmem &W, WarpProp &wp, const LearnedArgs &la, int c,
-                        int b, bool features, long long log_att, unsigned &err)
+                        int b, bool features, long long log_att, unsigned &err, bool logits = false)
 {
     const int lane = threadIdx.x & 31;
     const int n = warp_partners<true>(C, v, c, b, wp, err);
     if (n <= 0) return n;
-    const bool net = la.lambda < 1.0;
+    // A one-entry list proposes its only swap with pi = (1 - lambda) + lambda
+    // whatever the logit (the softmax of one value is exactly 1, so pi has the
+    // same bits either way): unless the caller wants the logits, the network
+    // and, unless dE or the log needs them, the features are skipped
+    const bool net = la.lambda < 1.0 && (n > 1 || logits);
     if (net || features) {
         const int nr = (n + 15) & ~15;
         for (int j = lane; j < nr; j += 32) {
@@ -472,7 +477,7 @@ __global__ void __launch_bounds__(32) k_dbl_proposal(const SimDev *__restrict__ 
     la.logf = out_d;
     la.logt = out_d + CAND_CAP * 24;
     la.logn = out_i;
-    const int n = proposal(C, ViewMap{comp_of, slot_of}, W, wp, la, c, b, true, 0, err);
+    const int n = proposal(C, ViewMap{comp_of, slot_of}, W, wp, la, c, b, true, 0, err, true);
     const int lane = threadIdx.x;
     out_i[0] = n;                                  // every lane writes the same value
     for (int j = lane; j < (n > 0 ? n : 0); j += 32) {
