@@ -70,6 +70,30 @@ def test_nlist_bit_exact(kg, case, precision):
     assert np.array_equal(nbr, on)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_smallest_cell_grid(kg, precision):
+    """Three Verlet cells a side, the fewest the library accepts: a box just
+    above the 7 sigma minimum with skin 1.0 (r_c + skin = 2.12), so every
+    stencil of 27 cells covers the whole box and each neighbouring cell is
+    reached by exactly one image shift.  The list is bit-exact and 10 steps
+    follow the oracle."""
+    import torch
+    m = KI.random_walk_melt(16, 19, 0.85, 1.0, 7)              # M = 304, L = 7.10
+    rl = 2.0 ** (1 / 6) + 1.0
+    assert int(m.box // rl) == 3
+    dt = 0.002
+    with context(kg, [m], precision, schedule=[kg.stage(2.0, 100, dt)], skin=1.0) as ctx:
+        offs, nbr = kg.kg_get_nlist(ctx, 0, m.M)
+        kg.kg_step(ctx, 10)
+        x = np.zeros_like(m.x)
+        kg.kg_get_config(ctx, 0, x)
+    oo, on = O.nlist(oparams(m, 12), m.x, rl, use_cells=False)   # all pairs, minimum image
+    assert np.array_equal(offs, oo) and np.array_equal(nbr, on)
+    xo, uo = m.x.copy(), m.v.copy()
+    O.run(oparams(m, 2.0, dt=dt), xo, uo, 0, 10)
+    assert np.abs(x - xo).max() < (1e-9 if precision == 0 else 1e-4)
+
+
 def _force_err(F, Fo):
     n = np.linalg.norm(F - Fo, axis=0)
     ref = np.maximum(np.linalg.norm(Fo, axis=0), np.sqrt((Fo ** 2).sum(axis=0).mean()))
