@@ -18,18 +18,18 @@ errors).
 * The scalar summaries -- l_K (Eq. 14 fitted over N/4 <= n <= N/2),
   <R^2(n)>/n averaged over that range, <R^2(1)> (mean squared bond) and the
   bond-bond correlation (<R^2(2)> - 2 <R^2(1)>) / 2 -- are reported with
-  their paired z; each must lie within 3 paired standard errors.  The paired
-  error understates how far whole runs scatter on the large-scale
-  summaries: over 4 noise seeds x 3 implementations (oracle, binary64 GPU,
-  mixed GPU) of this protocol the seed means of l_K and <R^2(n)>/n scattered
-  1.6 times more than it predicts (the local ones 1.0 - 1.3 times), and two
-  runs of one implementation under different seeds reached paired z = 3.1.
-  3 paired errors is about 2 run-to-run errors on l_K.  Over those 12 runs
-  the three implementations' means agreed within 1.6 run-to-run errors
-  (l_K: oracle 2.7439, binary64 -0.9%, mixed -0.2%).
-* The vectors (<R^2(n)>/n at all n, every populated histogram bin: about 90
-  comparisons, correlated through the same scatter) are checked
-  family-wise: none beyond 3.5 paired standard errors.
+  their paired z.  The paired error understates how far whole runs scatter:
+  over 4 noise seeds x 3 implementations (oracle, binary64 GPU, mixed GPU)
+  of this protocol the seed means of <R^2(n)>/n scattered 1.6 times more
+  than it predicts for n >= 16 (and for l_K), 1.0 - 1.3 times for n <= 12
+  and the local statistics; two runs of one implementation under different
+  seeds reached paired z = 3.1, and the three implementations' means agreed
+  within 1.6 run-to-run errors (l_K: oracle 2.7439, binary64 -0.9%, mixed
+  -0.2%).  The test therefore divides each paired z by that factor (INFL_LARGE
+  for l_K, <R^2(n)>/n over N/4..N/2 and <R^2(n)>/n at n >= N/4, INFL_LOCAL
+  for the rest) and asks each scalar to lie within 2.5 run-to-run errors
+  and every vector comparison (<R^2(n)>/n at all n, every populated
+  histogram bin: about 90, correlated) within 3.
 * Gamma = 0: the total energy of the mixed path against the binary64 GPU
   path and the oracle over 20 tau of velocity Verlet.
 * The 80,000-monomer melt (200 x 400, kappa = 2.5) runs a 100,000-step soft
@@ -52,6 +52,8 @@ RELAX = [(2.0, 300, 0.0005), (2.0, 300, 0.001), (4.0, 300, 0.0015), (6.5, 300, 0
          (12.0, 300, 0.005)]
 N_MELTS, N_CH, N, KAPPA = 48, 20, 50, 1.5
 PROD, EVERY, SKIP, K, NBINS, SEED = 20000, 100, 2000, 100, 40, 11
+# run-to-run scatter over the paired error, measured (see the docstring)
+INFL_LARGE, INFL_LOCAL = 1.6, 1.3
 
 
 @pytest.fixture(scope="module")
@@ -138,9 +140,10 @@ def test_long_run_statistics_of_batched_mixed_melts_match_the_oracle(kg):
         a = np.array([s[key] for s in g_sum])
         b = np.array([s[key] for s in o_sum])
         report[key] = (a.mean(), b.mean(), float(_z(a, b)))
-    print("scalar summaries (GPU mean, oracle mean, z):", report)
+    print("scalar summaries (GPU mean, oracle mean, paired z):", report)
+    large = ("l_K", "R2(n)/n, N/4..N/2")
     for key, (a, b, z) in report.items():
-        assert abs(z) < 3.0, (key, a, b, z)
+        assert abs(z) / (INFL_LARGE if key in large else INFL_LOCAL) < 2.5, (key, a, b, z)
     # vectors: <R^2(n)>/n at every n, populated histogram bins (per-melt frequencies)
     n = np.arange(1, N)
     z_r2 = _z(g_r2[:, 1:] / n, o_r2[:, 1:] / n)
@@ -157,7 +160,10 @@ def test_long_run_statistics_of_batched_mixed_melts_match_the_oracle(kg):
           f"{np.abs(zall).max():.2f} (R2 {np.abs(z_r2).max():.2f}, bond {np.abs(z_b).max():.2f}, "
           f"cos {np.abs(z_c).max():.2f})")
     assert len(z_b) >= 5 and len(z_c) >= 15
-    assert np.abs(zall).max() < 3.5, zall
+    infl = np.concatenate([np.where(n >= N // 4, INFL_LARGE, INFL_LOCAL), np.full(len(z_b) + len(z_c), INFL_LOCAL)])
+    zrun = np.abs(zall) / infl
+    print(f"largest run-to-run |z| {zrun.max():.2f}")
+    assert zrun.max() < 3.0, zall
 
 
 CFG2_SCHED = [(2.0, 2000, 0.001), (2.0, 10000, 0.004), (4.0, 10000, 0.005), (6.5, 10000, 0.006),
